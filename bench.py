@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Benchmark of the CSPH hot path on GB300.
+
+Workload: the 3D plate impact (50^3 projector at 1 km/s onto a 200x200x25
+slab, 1,125,000 particles, cubic lattice 0.1 mm, stiffened gas rho0 = 2700,
+c0 = 5.3 km/s, gamma = 2, h = 1.3 spacing), FP32 pair fluxes with FP64
+positions, 64 Voronoi work units rebalanced every 10 steps.  A step is one
+full CSPH time step (CFL reduction, kick-drift, cell mesh and sort, operand
+packing, pair loop, kick) plus, every 10th step, balancing + reassignment +
+renumbering.  Inputs are synthetic (synth.plate_impact_full) and larger than
+L2 (the FP64 state is ~190 MB), so no L2 flush is needed.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CSPH particle-steps/s on 1 GB300 (plate impact, FP32 pair fluxes / FP64 positions)"
+UNIT = "particle-steps/s"
+WORKLOAD = "plate_impact_1125k"
+# named workloads: the plate impact of the benchmark and a smaller one of the
+# same shape for profiler captures
+WORKLOADS = {
+    "plate_impact_1125k": dict(proj=50, target=(200, 200, 25)),
+    "plate_impact_387k": dict(proj=30, target=(120, 120, 25)),
+}
+
+# Algorithmic FP32 work of the pair loop (counted from the formulas):
+#   per unique candidate pair (interaction test r^2 < (kappa h_ij)^2): 11 flops
+#   per interacting half pair (e^R, v^R, acoustic P*, v*, W', three rate terms for both ends): 70 flops
+FLOP_TEST = 11.0
+FLOP_PAIR = 70.0
+
+
+def fp32_peak_tflops() -> float:
+    """152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum SM clock."""
+    return 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(steps: int, warmup: int = 0):
+    """Time the FP64 CPU oracle on a bounded sample of the workload: the full
+    1.125M-particle plate for `steps` steps after `warmup` steps (first rate
+    evaluation included in warm-up).  Returns (particle-steps/s, seconds)."""
+    import oracle as O
+    import synth
+    prob = synth.plate_impact_full()
+    p, s = O.from_problem(prob)
+    O.eval_rates(p, s)
+    if warmup:
+        O.step(p, s, warmup, rates_valid=True)
+    t0 = time.perf_counter()
+    O.step(p, s, steps, rates_valid=True)
+    dt = time.perf_counter() - t0
+    return prob.n * steps / dt, dt, prob.n
+
+
+def run_reference(args, rank: int):
+    """--impl reference: the oracle on the host cores, one bounded sample per step."""
+    if rank != 0:
+        return None
+    import oracle as O
+    import synth
+    # per step: one oracle step of a 1/16 sample of the workload (same lattice,
+    # EOS and impact; 25^3 projector on a 50x50x25 slab = 78,125 particles)
+    prob = synth.plate_impact(25, (50, 50, 25))
+    p, s = O.from_problem(prob)
+    O.eval_rates(p, s)
+    for _ in range(args.warmup):
+        O.step(p, s, 1, rates_valid=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.step(p, s, 1, rates_valid=True)
+    dt = time.perf_counter() - t0
+    value = prob.n * args.steps / dt
+    sample = (f"oracle (plain FP64 C, single thread) on a 78,125-particle sample of the plate impact "
+              f"(25^3 projector, 50x50x25 slab), {args.steps} timed steps")
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_particles": prob.n}, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_gpu(args, rank: int, world: int, local_rank: int):
+    import torch
+    import synth
+    from paper_1805_05128_gb300 import Simulation, build
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    prob = synth.plate_impact(units=64, n_steps=500, **WORKLOADS[args.workload])
+    gen = synth.problem_generators(prob)
+    sim = Simulation(prob, precision=args.precision, generators=gen, n_upd=10, device=dev)
+    sim.assign()
+    sim.build_cells()
+    sim.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local_rank
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_index) as clk:
+        sim.profile(True)
+        e0.record()
+        for _ in range(args.steps):
+            sim.step(1)
+        e1.record()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    pair_ms, pair_launches, launches = sim.profile_read()
+    sim.profile(False)
+    half_pairs, candidates, fp64_checks = sim.pair_counts()
+    status = sim.read_status()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    n_total = prob.n * world
+    value = n_total * args.steps / (ms * 1e-3)
+
+    # ---- end to end: host state in pinned memory, copied in and out every step
+    e2e_value, e2e_steps, h2d, d2h = None, 0, 0, 0
+    fields = [k for k in ("x", "y", "z", "vx", "vy", "vz", "rho", "E", "m", "ax", "ay", "az", "drho", "dE")]
+    if not args.no_e2e:
+        host = {k: torch.empty(prob.n, dtype=torch.float64, pin_memory=True) for k in fields}
+        for k in fields:
+            host[k].copy_(sim.t[k])
+        torch.cuda.synchronize()
+        e2e_steps = max(1, min(args.steps, 20))
+        h2d = sum(host[k].numel() * 8 for k in fields)
+        d2h = h2d
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        f0.record()
+        for _ in range(e2e_steps):
+            for k in fields:
+                sim.t[k].copy_(host[k], non_blocking=True)
+            sim.step(1)
+            for k in fields:
+                host[k].copy_(sim.t[k], non_blocking=True)
+        f1.record()
+        torch.cuda.synchronize()
+        e2e_ms = f0.elapsed_time(f1)
+        if dist:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e_value = n_total * e2e_steps / (e2e_ms * 1e-3)
+
+    if rank != 0:
+        return None
+    # ---- roofline of the dominant kernel (pair loop, FP32 ALU)
+    pair_ms_avg = pair_ms / max(pair_launches, 1)
+    flops = FLOP_PAIR * half_pairs + FLOP_TEST * candidates / 2.0
+    achieved = flops / (pair_ms_avg * 1e-3) / 1e12
+    peak = fp32_peak_tflops()
+    traffic = None
+    prof_path = os.path.join(ROOT, "profiles", "pair_traffic.json")
+    if os.path.exists(prof_path):
+        try:
+            pt = json.load(open(prof_path))
+            if pt.get("precision") == args.precision and pt.get("kernel_rev") == kernel_rev():
+                traffic = pt["bytes_per_launch_full"]
+        except (ValueError, KeyError):
+            traffic = None
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+           "data": "synthetic",
+           "config": {"workload": args.workload, "particles": prob.n, "precision": args.precision, "units": 64,
+                      "rebalance_every": 10, "l2": "inputs larger than L2 (no flush)",
+                      "parallelism": f"replicas{world}" if world > 1 else "single"},
+           "pair_interactions_per_s": half_pairs * world * args.steps / (ms * 1e-3),
+           "half_pairs_per_step": half_pairs, "candidates_per_step": candidates,
+           "fp64_pair_checks_per_step": fp64_checks,
+           "roofline": {"kernel": "k_pair", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": traffic,
+                        "peak_note": "FP32 152 SM x 128 lanes x 2 x 2.07 GHz (derived from unit counts and clock)",
+                        "pair_ms_per_launch": pair_ms_avg, "pair_share": pair_ms / ms},
+           "clocks": clk.summary(), "gpu_launches": launches, "device_status": status,
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "steps": e2e_steps}}
+    if world == 1 and not args.no_cpu_baseline:
+        cval, csec, cn = oracle_sample(args.cpu_steps)
+        out["cpu_baseline"] = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"plain FP64 C oracle, single thread, full {cn}-particle plate impact, "
+                                         f"{args.cpu_steps} steps after one rate evaluation ({csec:.1f} s)"}
+    return out
+
+
+def kernel_rev() -> str:
+    """Identifier of the pair-kernel source the stored ncu traffic belongs to."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1805_05128_gb300", "csrc", "k_pair.cu")
+    return hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="csph", choices=["csph", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        out = run_gpu(args, rank, world, local_rank)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * csph.h -- C ABI of the GB300 contact-SPH (CSPH) hot path with Voronoi
+ * dynamic domain decomposition (VD3), arXiv 1805.05128.
+ *
+ * Conventions for every entry point:
+ *  - All functions are extern "C", return an int status (SPH_OK = 0 or an
+ *    SPH_ERR_* code) and never throw.  sph_last_error() gives a message.
+ *  - Array arguments are DEVICE pointers owned by the caller unless a comment
+ *    says "host".  Arrays are dense, contiguous, one element per particle (or
+ *    per generator), 8-byte aligned for doubles.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are asynchronous on that stream: they enqueue work and return.
+ *    Only sph_read_status() synchronises.  Errors found on the host (bad
+ *    arguments) are returned at once; errors found on the device (capacity,
+ *    non-finite values, bounded-wait timeouts) are latched in a device status
+ *    word and reported by sph_read_status().
+ *  - A handle owns only workspace (cell lists, packed operands, work-unit
+ *    lists, reduction buffers), allocated in sph_init and freed in
+ *    sph_destroy.  A handle is used from one host thread at a time.
+ */
+#ifndef CSPH_H
+#define CSPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SPH_OK 0
+#define SPH_ERR_INVALID 1    /* bad argument or unsupported combination */
+#define SPH_ERR_CAPACITY 2   /* more particles / cells / pairs than the workspace holds */
+#define SPH_ERR_NONFINITE 3  /* NaN or Inf found in the particle state */
+#define SPH_ERR_CUDA 4       /* a CUDA runtime call failed */
+#define SPH_ERR_TIMEOUT 5    /* a bounded device-side wait gave up */
+
+/* ---- enumerations ---- */
+#define SPH_KERNEL_CUBIC 0        /* cubic spline M4, support 2h */
+#define SPH_KERNEL_WENDLAND_C2 1  /* Wendland C2, support kappa h (paper: kappa = 1.936, Sec. 4.1) */
+
+#define SPH_EOS_IDEAL 0          /* P = (gamma-1) rho e */
+#define SPH_EOS_STIFFENED 1      /* P = (gamma-1) rho e - gamma P_inf */
+#define SPH_EOS_TAIT 2           /* P = rho0 c0^2/gamma [(rho/rho0)^gamma - 1] */
+#define SPH_EOS_MIE_GRUNEISEN 3  /* eqs. (mie_gruneisen_eos), (mie_gruneisen_reference), Sec. 7 */
+
+#define SPH_PREC_FP64 0   /* every pair flux in FP64 */
+#define SPH_PREC_MIXED 1  /* FP32 pair fluxes on local-origin offsets, Kahan-compensated
+                             per-particle sums; FP64 positions, time, integration */
+
+#define SPH_MAX_MAT 4
+#define SPH_MAX_UNITS 256
+
+typedef struct sph_material {
+  int32_t eos;     /* SPH_EOS_* */
+  int32_t pad_;
+  double gamma;    /* ideal/stiffened: adiabatic index; Tait: exponent; MG: Grueneisen Gamma */
+  double rho0;     /* reference density (stiffened: informative; Tait, MG: used) */
+  double c0;       /* reference sound speed (Tait); MG: c_a */
+  double p_inf;    /* stiffened gas P_inf */
+  double s_a;      /* MG: Hugoniot slope */
+} sph_material;
+
+typedef struct sph_params {
+  int32_t dim;        /* spatial dimension of the particles: 1, 2 or 3 */
+  int32_t kernel;     /* SPH_KERNEL_* */
+  int32_t precision;  /* SPH_PREC_* */
+  int32_t n_mat;      /* materials used (1..SPH_MAX_MAT) */
+  double kappa;       /* kernel support in units of h */
+  double eta;         /* h_ij = eta (d_i + d_j)/2, eq. (SmoothingLengthDef) times eta */
+  double cfl;         /* dt = cfl min_i eta d_i / (c_i + |v_i|) */
+  double cell_beta;   /* beta of eq. (Dcell); 0 = cells rebuilt every step */
+  int64_t cell_cap;   /* maximum cells of the dense mesh over all instances */
+  sph_material mat[SPH_MAX_MAT];
+  /* Voronoi work units (VD3).  n_units = 0 disables them. */
+  int32_t n_units;    /* K <= SPH_MAX_UNITS */
+  int32_t unit_dim;   /* dimension of the decomposition: 1, 2 or 3 (<= dim) */
+  int32_t n_upd;      /* sph_step rebalances every n_upd steps (0 = never) */
+  int32_t pad_;
+  double theta;       /* eq. (TotalOffset) */
+  double sigma;       /* eq. (BalancingOffsetPlusRot) */
+  double gamma_b;     /* gamma of eq. (TotalOffset) */
+  double beta_sh;     /* buffer beta of R^hrz used in D^sh, eq. (Horizon) */
+  double* generators; /* device, K x unit_dim, read and updated by sph_step's rebalancing */
+} sph_params;
+
+/* Particle state: structure of arrays in device memory, n elements each.
+ * For dim < 3 the unused components (y, z, vy, vz, ay, az) may be NULL. */
+typedef struct sph_state {
+  int64_t n;
+  double *x, *y, *z;            /* position (FP64) */
+  double *vx, *vy, *vz;         /* velocity */
+  double *rho, *E, *m;          /* density, specific total energy e + v^2/2, mass */
+  int32_t* mat;                 /* material index, or NULL for material 0 */
+  double *ax, *ay, *az, *drho, *dE; /* rates at this state (written by the library) */
+  double *d, *P, *c;            /* particle size, pressure, sound speed (written) */
+  int64_t* id;                  /* caller's particle identity, permuted along; may be NULL */
+  int32_t* unit;                /* work unit of each particle (written by voronoi_assign); may be
+                                   NULL when n_units = 0 */
+} sph_state;
+
+typedef struct sph_balance_params {
+  double theta, sigma, gamma_b, beta_sh;
+} sph_balance_params;
+
+typedef struct sph_handle sph_handle;
+
+/* Create a handle for `s->n` particles split into n_instances independent
+ * simulations; instance b owns particles [inst_offsets[b], inst_offsets[b+1])
+ * (host array of n_instances+1 entries, inst_offsets[0] = 0,
+ * inst_offsets[n_instances] = s->n).  Checks the parameters, allocates the
+ * workspace and checks the state for non-finite values (this one call
+ * synchronises the stream).  Problem statement: particles with mass,
+ * position, velocity, density and energy interacting through pair Riemann
+ * fluxes within kappa h_ij (Sec. 4.1).  Errors: SPH_ERR_INVALID for bad
+ * parameters, SPH_ERR_NONFINITE, SPH_ERR_CUDA.  On error *h is NULL. */
+int sph_init(sph_handle** h, const sph_params* p, int n_instances, const int64_t* inst_offsets,
+             const sph_state* s, void* stream);
+
+/* Derive d_i = (m_i/rho_i)^(1/dim), P_i and c_i, build the cell mesh of
+ * eq. (Dcell) and renumber the particles so that each cell's particles are
+ * contiguous and cells follow each other in mesh order (the locality
+ * renumbering of Sec. 4.2).  Every array of `s` (including id, unit, mat and
+ * the rates) is permuted in place, within each instance. */
+int sph_build_cells(sph_handle* h, sph_state* s, void* stream);
+
+/* Evaluate the CSPH rates of eqs. (SPH:Conti), (SPH:Pulse), (SPH:Energy) at
+ * the current state: d, P, c, cell mesh, pair search within kappa h_ij,
+ * acoustic pair Riemann fluxes, per-particle sums.  Writes ax, ay, az, drho,
+ * dE, d, P, c.  Does not move particles or permute arrays.  When work units
+ * are enabled it adds this evaluation's pair counts and unit adjacency to the
+ * balancing accumulators. */
+int sph_eval_rates(sph_handle* h, sph_state* s, void* stream);
+
+/* Advance every instance by n_steps kick-drift-kick steps (Alg. 1, loop
+ * "renew particle positions and states and make global synchronization of
+ * SPH time step"): dt from the CFL condition reduced on the device, half
+ * kick with the rates held in `s`, drift, rates at the predicted state, half
+ * kick.  t_dev (device, n_instances doubles, may be NULL) accumulates time.
+ * If the rates in `s` were not produced by this handle they are evaluated
+ * first.  With work units and n_upd > 0, every n_upd steps it runs
+ * voronoi_balance on p->generators, voronoi_assign and the renumbering of
+ * sph_build_cells (Alg. 1, outer loop). */
+int sph_step(sph_handle* h, sph_state* s, int n_steps, double* t_dev, void* stream);
+
+/* Assign every particle to its nearest generator, eq. (VoronoiDefinition),
+ * ties to the smaller index (Sec. 3.1), in the first `dim` coordinates.
+ * gen: device, K x dim doubles.  unit_out: device, n int32 (may be s->unit).
+ * unit_offsets: device, K+1 int32, or NULL: start of each unit in the
+ * handle's unit-ordered particle list.  Resets the balancing accumulators.
+ * Requires one instance.  Errors: SPH_ERR_INVALID (K, dim, instances). */
+int voronoi_assign(sph_handle* h, const sph_state* s, const double* gen, int K, int dim,
+                   int32_t* unit_out, int32_t* unit_offsets, void* stream);
+
+/* One balancing update of the generators (Secs. 3.2-3.4): loads L_k (device
+ * `load`, K doubles, or NULL for the accumulated pair counts, a pair that
+ * crosses units counting 1/2 to each), adjacency from the accumulated
+ * interacting pairs, D^sh_kl of eq. (Horizon), two-body eq.
+ * (BalancingOffset), three-body eq. (BalancingOffsetRot) for dim = 2 limited
+ * to max_l D^sh_kl, combination eq. (BalancingOffsetPlusRot) and cumulative
+ * movement eq. (TotalOffset) toward the current centroid of each unit's
+ * particles.  gen (device, K x dim) is updated in place; shift_sum_out
+ * (device double, may be NULL) receives sum_k |g^_k - g_k|, eq. (VDConvergence).
+ * Uses s->unit, positions and d, and the neighbour statistics of the last
+ * rate evaluation; resets the accumulators. */
+int voronoi_balance(sph_handle* h, const sph_state* s, double* gen, int K, int dim, const double* load,
+                    const sph_balance_params* bp, double* shift_sum_out, void* stream);
+
+/* FP64 totals per instance: out (device, n_instances x 5 doubles) receives
+ * mass, momentum x/y/z and total energy sum m E, summed in a fixed order. */
+int sph_conservation(sph_handle* h, const sph_state* s, double* out, void* stream);
+
+/* Host-side copy of the balancing accumulators (for inspection and tests):
+ * load_out (host, K doubles, pair counts with 1/2 per crossing end) and
+ * adj_out (host, K*K bytes, 0/1).  Synchronises the stream. */
+int sph_unit_stats(sph_handle* h, double* load_out, uint8_t* adj_out, void* stream);
+
+/* Synchronise the handle's last stream and report the device status word
+ * (SPH_OK or the first SPH_ERR_* latched by a kernel) in *device_status;
+ * the return value is SPH_OK unless the synchronisation itself failed.
+ * Clears the status word. */
+int sph_read_status(sph_handle* h, int* device_status);
+
+/* Message for the last host-side error on this handle ("" if none);
+ * sph_last_error(NULL) gives the message of the last failed sph_init. */
+const char* sph_last_error(const sph_handle* h);
+
+/* Counters of the last call: accepted half pairs (i < j) of the last rate
+ * evaluation, candidates tested, and pairs decided by the FP64 fallback. */
+int sph_pair_counts(sph_handle* h, int64_t* half_pairs, int64_t* candidates, int64_t* fp64_checks,
+                    void* stream);
+
+/* Inspection of the neighbour search (Sec. 4.2) at the current state,
+ * for verification: derives d, builds the cell mesh of eq. (Dcell) and
+ * writes, per particle in the state's order, the linear cell index
+ * cx + nx (cy + ny cz) local to its instance (cell_out, device, n int32).
+ * grid_out (host, may be NULL) receives per instance 8 doubles:
+ * x0[3], D^c, nx, ny, nz, ncells.  Synchronises the stream. */
+int sph_cell_index(sph_handle* h, const sph_state* s, int32_t* cell_out, double* grid_out, void* stream);
+
+/* Inspection of the interacting pairs (Sec. 4.1-4.2) at the current state:
+ * runs the rate evaluation of sph_eval_rates and also writes every
+ * interacting unordered pair once as (i, j) particle indices with i < j
+ * into pi_out/pj_out (device, cap int32 each, unordered).  *count_out
+ * (host) receives the number of pairs; when it exceeds cap only cap pairs
+ * are written and SPH_ERR_CAPACITY is returned.  Synchronises the stream. */
+int sph_pair_list(sph_handle* h, sph_state* s, int64_t cap, int32_t* pi_out, int32_t* pj_out,
+                  int64_t* count_out, void* stream);
+
+/* Measurement support.  sph_profile(h, 1) starts recording CUDA events
+ * around every launch of the pair kernel on the caller's stream and counts
+ * every kernel launch of the library; sph_profile(h, 0) stops.  Resets the
+ * records either way. */
+int sph_profile(sph_handle* h, int enable);
+
+/* Synchronise and report, since the last sph_profile/sph_profile_read: the
+ * summed device duration of the pair-kernel launches in ms (pair_ms), their
+ * number, and the number of kernel launches of the library.  Resets them. */
+int sph_profile_read(sph_handle* h, double* pair_ms, int64_t* pair_launches, int64_t* kernel_launches);
+
+void sph_destroy(sph_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSPH_H */

@@ -1,0 +1,469 @@
+// csph_api.cu -- the C ABI of include/csph.h: argument checks, workspace
+// ownership and the orchestration of the kernels of one CSPH step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "csph_internal.cuh"
+
+using namespace csph;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+int fail(sph_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg; else g_init_error = msg;
+  return code;
+}
+
+int cuda_fail(sph_handle* h, const char* what, cudaError_t e) {
+  return fail(h, SPH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                           \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail((h), #call, e_);  \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count);
+}
+
+void free_all(sph_handle* h) {
+  void* ptrs[] = {h->blk_inst, h->blk_start, h->blk_end, h->inst_blk, h->inst_off, h->part, h->grid, h->dt,
+                  h->inst_cap, h->total_cells, h->cell_count, h->cell_start, h->scan_sums, h->cell_of, h->rank,
+                  h->perm, h->slot_cell, h->slot_unit, h->packA, h->packB, h->packC, h->rho_slot, h->dmax_nbr,
+                  h->load_acc, h->adj_bits, h->unit_off, h->unit_list, h->unit_work, h->unit_total, h->unit_stats,
+                  h->status, h->counters, h->scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+int check_state(sph_handle* h, const sph_state* s, int dim) {
+  if (!s) return fail(h, SPH_ERR_INVALID, "state is NULL");
+  if (!s->x || !s->vx || !s->rho || !s->E || !s->m || !s->ax || !s->drho || !s->dE || !s->d || !s->P || !s->c)
+    return fail(h, SPH_ERR_INVALID, "state: a required array is NULL");
+  if (dim >= 2 && (!s->y || !s->vy || !s->ay)) return fail(h, SPH_ERR_INVALID, "state: y/vy/ay NULL for dim >= 2");
+  if (dim >= 3 && (!s->z || !s->vz || !s->az)) return fail(h, SPH_ERR_INVALID, "state: z/vz/az NULL for dim 3");
+  return SPH_OK;
+}
+
+int check_handle_state(sph_handle* h, const sph_state* s) {
+  if (!h) return SPH_ERR_INVALID;
+  int rc = check_state(h, s, h->dp.dim);
+  if (rc) return rc;
+  if (s->n != h->n) return fail(h, SPH_ERR_INVALID, "state size differs from the handle's");
+  if (h->K > 0 && !s->unit) return fail(h, SPH_ERR_INVALID, "state: unit array NULL with work units enabled");
+  return SPH_OK;
+}
+
+int eval_rates_impl(sph_handle* h, sph_state* s, cudaStream_t st) {
+  CK(h, launch_derive_dt(h, *s, true, st));
+  CK(h, launch_build_grid(h, *s, st));
+  CK(h, launch_pack(h, *s, false, st));
+  CK(h, launch_pair(h, *s, st));
+  h->rates_valid = true;
+  return SPH_OK;
+}
+
+int balance_impl(sph_handle* h, sph_state* s, double* gen, int K, int dim, const double* load,
+                 const sph_balance_params& bp, double* shift_out, cudaStream_t st) {
+  CK(h, launch_balance(h, *s, gen, K, dim, load, bp, shift_out, st));
+  return SPH_OK;
+}
+
+int assign_impl(sph_handle* h, const sph_state* s, const double* gen, int K, int dim, int32_t* unit_out,
+                int32_t* unit_offsets, cudaStream_t st) {
+  CK(h, launch_assign(h, *s, gen, K, dim, unit_out, st));
+  CK(h, launch_unit_lists(h, unit_out, unit_offsets, st));
+  CK(h, cudaMemsetAsync(h->load_acc, 0, sizeof(unsigned long long) * K, st));
+  CK(h, cudaMemsetAsync(h->adj_bits, 0, sizeof(uint32_t) * K * ((K + 31) / 32), st));
+  return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64_t* inst_offsets,
+             const sph_state* s, void* stream) {
+  if (!out) return fail(nullptr, SPH_ERR_INVALID, "handle pointer is NULL");
+  *out = nullptr;
+  if (!p) return fail(nullptr, SPH_ERR_INVALID, "params is NULL");
+  if (p->dim < 1 || p->dim > 3) return fail(nullptr, SPH_ERR_INVALID, "dim must be 1, 2 or 3");
+  if (p->kernel != SPH_KERNEL_CUBIC && p->kernel != SPH_KERNEL_WENDLAND_C2)
+    return fail(nullptr, SPH_ERR_INVALID, "unknown kernel");
+  if (p->precision != SPH_PREC_FP64 && p->precision != SPH_PREC_MIXED)
+    return fail(nullptr, SPH_ERR_INVALID, "unknown precision");
+  if (p->n_mat < 1 || p->n_mat > SPH_MAX_MAT) return fail(nullptr, SPH_ERR_INVALID, "n_mat out of range");
+  for (int k = 0; k < p->n_mat; ++k)
+    if (p->mat[k].eos < SPH_EOS_IDEAL || p->mat[k].eos > SPH_EOS_MIE_GRUNEISEN)
+      return fail(nullptr, SPH_ERR_INVALID, "unknown EOS");
+  if (!(p->kappa > 0) || !(p->eta > 0) || !(p->cfl > 0) || !(p->cell_beta >= 0))
+    return fail(nullptr, SPH_ERR_INVALID, "kappa, eta, cfl must be > 0 and cell_beta >= 0");
+  if (n_instances < 1 || !inst_offsets) return fail(nullptr, SPH_ERR_INVALID, "need n_instances >= 1 and offsets");
+  int rc = check_state(nullptr, s, p->dim);
+  if (rc) return rc;
+  if (s->n < 1) return fail(nullptr, SPH_ERR_INVALID, "no particles");
+  if (s->n >= (int64_t(1) << 26)) return fail(nullptr, SPH_ERR_CAPACITY, "at most 2^26 - 1 particles per handle");
+  if (inst_offsets[0] != 0 || inst_offsets[n_instances] != s->n)
+    return fail(nullptr, SPH_ERR_INVALID, "instance offsets must start at 0 and end at n");
+  for (int b = 0; b < n_instances; ++b)
+    if (inst_offsets[b + 1] <= inst_offsets[b]) return fail(nullptr, SPH_ERR_INVALID, "empty or unordered instance");
+  if (p->cell_cap < n_instances || p->cell_cap > (int64_t(1) << 31) - 2)
+    return fail(nullptr, SPH_ERR_INVALID, "cell_cap must be in [n_instances, 2^31 - 2]");
+  if (p->n_units < 0 || p->n_units > SPH_MAX_UNITS) return fail(nullptr, SPH_ERR_INVALID, "n_units out of range");
+  if (p->n_units > 0) {
+    if (n_instances != 1) return fail(nullptr, SPH_ERR_INVALID, "work units need a single instance");
+    if (p->unit_dim < 1 || p->unit_dim > p->dim) return fail(nullptr, SPH_ERR_INVALID, "unit_dim out of range");
+    if (!s->unit) return fail(nullptr, SPH_ERR_INVALID, "work units need state.unit");
+    if (p->n_upd > 0 && !p->generators) return fail(nullptr, SPH_ERR_INVALID, "n_upd > 0 needs generators");
+  }
+
+  sph_handle* h = new sph_handle();
+  h->p = *p;
+  h->n = s->n;
+  h->n_inst = n_instances;
+  h->inst_off_h.assign(inst_offsets, inst_offsets + n_instances + 1);
+  h->last_stream = (cudaStream_t)stream;
+  DevParams& dp = h->dp;
+  dp.dim = p->dim; dp.kernel = p->kernel; dp.precision = p->precision; dp.n_mat = p->n_mat;
+  dp.kappa = p->kappa; dp.eta = p->eta; dp.cfl = p->cfl; dp.cell_beta = p->cell_beta;
+  dp.kh = (0.5 * p->kappa) * p->eta;
+  for (int k = 0; k < SPH_MAX_MAT; ++k) {
+    const sph_material& m = p->mat[k < p->n_mat ? k : 0];
+    dp.mat[k] = Mat{m.eos, m.gamma, m.rho0, m.c0, m.p_inf, m.s_a};
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  auto bail = [&](int code) {
+    g_init_error = h->err;
+    free_all(h);
+    delete h;
+    return code;
+  };
+#define CKI(call)                                                         \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess) { cuda_fail(h, #call, e_); return bail(SPH_ERR_CUDA); } \
+  } while (0)
+
+  // segmented blocks
+  std::vector<int32_t> bi;
+  std::vector<int64_t> bs, be;
+  h->inst_blk_h.clear();
+  for (int b = 0; b < n_instances; ++b) {
+    h->inst_blk_h.push_back((int32_t)bi.size());
+    for (int64_t q = inst_offsets[b]; q < inst_offsets[b + 1]; q += kBlock) {
+      bi.push_back(b);
+      bs.push_back(q);
+      be.push_back(std::min(q + kBlock, inst_offsets[b + 1]));
+    }
+  }
+  h->inst_blk_h.push_back((int32_t)bi.size());
+  h->nblk = (int)bi.size();
+  const int64_t n = h->n;
+  CKI(dalloc(&h->blk_inst, h->nblk));
+  CKI(dalloc(&h->blk_start, h->nblk));
+  CKI(dalloc(&h->blk_end, h->nblk));
+  CKI(dalloc(&h->inst_blk, n_instances + 1));
+  CKI(dalloc(&h->inst_off, n_instances + 1));
+  CKI(cudaMemcpy(h->blk_inst, bi.data(), sizeof(int32_t) * bi.size(), cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(h->blk_start, bs.data(), sizeof(int64_t) * bs.size(), cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(h->blk_end, be.data(), sizeof(int64_t) * be.size(), cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(h->inst_blk, h->inst_blk_h.data(), sizeof(int32_t) * (n_instances + 1), cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(h->inst_off, inst_offsets, sizeof(int64_t) * (n_instances + 1), cudaMemcpyHostToDevice));
+
+  CKI(dalloc(&h->part, h->nblk));
+  CKI(dalloc(&h->grid, n_instances));
+  CKI(dalloc(&h->dt, n_instances));
+  CKI(dalloc(&h->inst_cap, n_instances));
+  CKI(dalloc(&h->total_cells, 1));
+  std::vector<int64_t> caps(n_instances);
+  for (int b = 0; b < n_instances; ++b) {
+    int64_t nb = inst_offsets[b + 1] - inst_offsets[b];
+    // share of the cell capacity: 1 + floor((cap - n_inst) n_b / n); the shares sum to <= cap
+    // and a single instance gets the whole capacity
+    caps[b] = n_instances == 1 ? p->cell_cap
+                               : 1 + (int64_t)((double)(p->cell_cap - n_instances) * (double)nb / (double)n);
+  }
+  CKI(cudaMemcpy(h->inst_cap, caps.data(), sizeof(int64_t) * n_instances, cudaMemcpyHostToDevice));
+
+  h->cell_cap = p->cell_cap;
+  CKI(dalloc(&h->cell_count, h->cell_cap));
+  CKI(cudaMemset(h->cell_count, 0, sizeof(int32_t) * h->cell_cap));
+  CKI(dalloc(&h->cell_start, h->cell_cap + 1));
+  CKI(dalloc(&h->scan_sums, h->cell_cap / 1024 + 2));
+  CKI(dalloc(&h->cell_of, n));
+  CKI(dalloc(&h->rank, n));
+  CKI(dalloc(&h->perm, n));
+  CKI(dalloc(&h->slot_cell, n));
+  CKI(dalloc(&h->slot_unit, n));
+  if (p->precision == SPH_PREC_MIXED) {
+    CKI(dalloc(reinterpret_cast<float4**>(&h->packA), n));
+    CKI(dalloc(reinterpret_cast<float4**>(&h->packB), n));
+    CKI(dalloc(reinterpret_cast<float2**>(&h->packC), n));
+  } else {
+    CKI(dalloc(reinterpret_cast<D4**>(&h->packA), n));
+    CKI(dalloc(reinterpret_cast<D4**>(&h->packB), n));
+    CKI(dalloc(reinterpret_cast<D2**>(&h->packC), n));
+  }
+  CKI(dalloc(&h->rho_slot, n));
+  CKI(dalloc(&h->dmax_nbr, n));
+  CKI(dalloc(&h->status, 1));
+  CKI(cudaMemset(h->status, 0, sizeof(int)));
+  CKI(dalloc(&h->counters, 5));
+  CKI(cudaMemset(h->counters, 0, 5 * sizeof(unsigned long long)));
+  h->scratch_bytes = (size_t)n * (18 * 8 + 8 + 4 + 4);
+  CKI(cudaMalloc(&h->scratch, h->scratch_bytes));
+
+  h->K = p->n_units;
+  h->gdim = p->unit_dim;
+  if (h->K > 0) {
+    int K = h->K;
+    int nb = grid_for(n, 1024);
+    h->unit_work_total = (int64_t)K * nb;
+    CKI(dalloc(&h->load_acc, K));
+    CKI(cudaMemset(h->load_acc, 0, sizeof(unsigned long long) * K));
+    CKI(dalloc(&h->adj_bits, (size_t)K * ((K + 31) / 32)));
+    CKI(cudaMemset(h->adj_bits, 0, sizeof(uint32_t) * K * ((K + 31) / 32)));
+    CKI(dalloc(&h->unit_off, K + 1));
+    CKI(dalloc(&h->unit_list, n));
+    CKI(dalloc(&h->unit_work, 2 * h->unit_work_total + h->unit_work_total / 1024 + 4));
+    CKI(cudaMemset(h->unit_work, 0, sizeof(int32_t) * (2 * h->unit_work_total + h->unit_work_total / 1024 + 4)));
+    CKI(dalloc(&h->unit_total, 1));
+    CKI(cudaMemcpy(h->unit_total, &h->unit_work_total, sizeof(int64_t), cudaMemcpyHostToDevice));
+    CKI(dalloc(&h->unit_stats, (size_t)K * 5));
+  }
+
+  CKI(launch_check_finite(h, *s, st));
+  int status = 0;
+  CKI(cudaStreamSynchronize(st));
+  CKI(cudaMemcpy(&status, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status != 0) {
+    fail(h, SPH_ERR_NONFINITE, "state holds a non-finite or non-positive value");
+    return bail(SPH_ERR_NONFINITE);
+  }
+#undef CKI
+  *out = h;
+  return SPH_OK;
+}
+
+int sph_build_cells(sph_handle* h, sph_state* s, void* stream) {
+  int rc = check_handle_state(h, s);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  CK(h, launch_derive_dt(h, *s, true, st));
+  CK(h, launch_build_grid(h, *s, st));
+  CK(h, launch_renumber(h, *s, st));
+  return SPH_OK;
+}
+
+int sph_eval_rates(sph_handle* h, sph_state* s, void* stream) {
+  int rc = check_handle_state(h, s);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  return eval_rates_impl(h, s, st);
+}
+
+int sph_step(sph_handle* h, sph_state* s, int n_steps, double* t_dev, void* stream) {
+  int rc = check_handle_state(h, s);
+  if (rc) return rc;
+  if (n_steps < 0) return fail(h, SPH_ERR_INVALID, "n_steps < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  if (!h->rates_valid) {
+    rc = eval_rates_impl(h, s, st);
+    if (rc) return rc;
+  }
+  const bool vd3 = h->K > 0 && h->p.n_upd > 0;
+  sph_balance_params bp{h->p.theta, h->p.sigma, h->p.gamma_b, h->p.beta_sh};
+  for (int k = 0; k < n_steps; ++k) {
+    CK(h, launch_derive_dt(h, *s, false, st));
+    CK(h, launch_reduce_dt(h, st));
+    CK(h, launch_kick_drift(h, *s, st));
+    CK(h, launch_build_grid(h, *s, st));
+    CK(h, launch_pack(h, *s, true, st));
+    // unit adjacency is needed only from the evaluation that precedes a rebalance
+    h->collect_adj = !vd3 || h->steps_since_balance + 1 >= h->p.n_upd;
+    CK(h, launch_pair(h, *s, st));
+    h->collect_adj = true;
+    CK(h, launch_kick2(h, *s, t_dev, st));
+    if (vd3 && ++h->steps_since_balance >= h->p.n_upd) {
+      // Alg. 1 outer loop: shift generators, reassign, renumber
+      h->steps_since_balance = 0;
+      rc = balance_impl(h, s, h->p.generators, h->K, h->gdim, nullptr, bp, nullptr, st);
+      if (rc) return rc;
+      rc = assign_impl(h, s, h->p.generators, h->K, h->gdim, s->unit, nullptr, st);
+      if (rc) return rc;
+      CK(h, launch_renumber(h, *s, st));
+    }
+  }
+  return SPH_OK;
+}
+
+int voronoi_assign(sph_handle* h, const sph_state* s, const double* gen, int K, int dim, int32_t* unit_out,
+                   int32_t* unit_offsets, void* stream) {
+  int rc = check_handle_state(h, s);
+  if (rc) return rc;
+  if (h->K == 0 || K != h->K) return fail(h, SPH_ERR_INVALID, "K must equal the handle's n_units (> 0)");
+  if (dim != h->gdim) return fail(h, SPH_ERR_INVALID, "dim must equal the handle's unit_dim");
+  if (!gen || !unit_out) return fail(h, SPH_ERR_INVALID, "gen and unit_out are required");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  return assign_impl(h, s, gen, K, dim, unit_out, unit_offsets, st);
+}
+
+int voronoi_balance(sph_handle* h, const sph_state* s, double* gen, int K, int dim, const double* load,
+                    const sph_balance_params* bp, double* shift_sum_out, void* stream) {
+  int rc = check_handle_state(h, s);
+  if (rc) return rc;
+  if (h->K == 0 || K != h->K) return fail(h, SPH_ERR_INVALID, "K must equal the handle's n_units (> 0)");
+  if (dim != h->gdim) return fail(h, SPH_ERR_INVALID, "dim must equal the handle's unit_dim");
+  if (!gen || !bp) return fail(h, SPH_ERR_INVALID, "gen and balance params are required");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  return balance_impl(h, const_cast<sph_state*>(s), gen, K, dim, load, *bp, shift_sum_out, st);
+}
+
+int sph_conservation(sph_handle* h, const sph_state* s, double* out, void* stream) {
+  int rc = check_handle_state(h, s);
+  if (rc) return rc;
+  if (!out) return fail(h, SPH_ERR_INVALID, "out is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  CK(h, launch_conservation(h, *s, out, st));
+  return SPH_OK;
+}
+
+int sph_unit_stats(sph_handle* h, double* load_out, uint8_t* adj_out, void* stream) {
+  if (!h) return SPH_ERR_INVALID;
+  if (h->K == 0) return fail(h, SPH_ERR_INVALID, "work units are disabled");
+  cudaStream_t st = (cudaStream_t)stream;
+  int K = h->K, words = (K + 31) / 32;
+  std::vector<unsigned long long> acc(K);
+  std::vector<uint32_t> bits((size_t)K * words);
+  CK(h, cudaMemcpyAsync(acc.data(), h->load_acc, sizeof(unsigned long long) * K, cudaMemcpyDeviceToHost, st));
+  CK(h, cudaMemcpyAsync(bits.data(), h->adj_bits, sizeof(uint32_t) * bits.size(), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  for (int k = 0; k < K; ++k) {
+    if (load_out) load_out[k] = 0.5 * (double)acc[k];
+    if (adj_out)
+      for (int l = 0; l < K; ++l) adj_out[k * K + l] = (bits[(size_t)k * words + (l >> 5)] >> (l & 31)) & 1u;
+  }
+  return SPH_OK;
+}
+
+int sph_read_status(sph_handle* h, int* device_status) {
+  if (!h || !device_status) return SPH_ERR_INVALID;
+  CK(h, cudaStreamSynchronize(h->last_stream));
+  CK(h, cudaMemcpy(device_status, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(h, cudaMemset(h->status, 0, sizeof(int)));
+  return SPH_OK;
+}
+
+const char* sph_last_error(const sph_handle* h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+
+int sph_pair_counts(sph_handle* h, int64_t* half_pairs, int64_t* candidates, int64_t* fp64_checks, void* stream) {
+  if (!h) return SPH_ERR_INVALID;
+  unsigned long long c[4];
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(h, cudaMemcpyAsync(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  if (half_pairs) *half_pairs = (int64_t)(c[0] / 2);
+  if (candidates) *candidates = (int64_t)c[1];
+  if (fp64_checks) *fp64_checks = (int64_t)c[2];
+  return SPH_OK;
+}
+
+int sph_cell_index(sph_handle* h, const sph_state* s, int32_t* cell_out, double* grid_out, void* stream) {
+  int rc = check_handle_state(h, s);
+  if (rc) return rc;
+  if (!cell_out) return fail(h, SPH_ERR_INVALID, "cell_out is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  sph_state tmp = *s;
+  CK(h, launch_derive_dt(h, tmp, true, st));
+  CK(h, launch_build_grid(h, tmp, st));
+  std::vector<GridInfo> g(h->n_inst);
+  CK(h, cudaMemcpyAsync(g.data(), h->grid, sizeof(GridInfo) * h->n_inst, cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  std::vector<int32_t> cells(h->n);
+  CK(h, cudaMemcpy(cells.data(), h->cell_of, sizeof(int32_t) * h->n, cudaMemcpyDeviceToHost));
+  for (int b = 0; b < h->n_inst; ++b) {
+    for (int64_t q = h->inst_off_h[b]; q < h->inst_off_h[b + 1]; ++q) cells[q] -= (int32_t)g[b].cell_off;
+    if (grid_out) {
+      double* o = grid_out + 8 * b;
+      for (int a = 0; a < 3; ++a) o[a] = g[b].x0[a];
+      o[3] = g[b].dc;
+      for (int a = 0; a < 3; ++a) o[4 + a] = (double)g[b].dims[a];
+      o[7] = (double)g[b].ncells;
+    }
+  }
+  CK(h, cudaMemcpy(cell_out, cells.data(), sizeof(int32_t) * h->n, cudaMemcpyHostToDevice));
+  return SPH_OK;
+}
+
+int sph_pair_list(sph_handle* h, sph_state* s, int64_t cap, int32_t* pi_out, int32_t* pj_out, int64_t* count_out,
+                  void* stream) {
+  int rc = check_handle_state(h, s);
+  if (rc) return rc;
+  if (!pi_out || !pj_out || !count_out || cap < 0) return fail(h, SPH_ERR_INVALID, "bad pair output arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  h->pair_out_i = pi_out;
+  h->pair_out_j = pj_out;
+  h->pair_out_cap = cap;
+  rc = eval_rates_impl(h, s, st);
+  h->pair_out_i = h->pair_out_j = nullptr;
+  h->pair_out_cap = 0;
+  if (rc) return rc;
+  unsigned long long c = 0;
+  CK(h, cudaMemcpyAsync(&c, &h->counters[4], sizeof(c), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  *count_out = (int64_t)c;
+  if ((int64_t)c > cap) return fail(h, SPH_ERR_CAPACITY, "more pairs than cap");
+  return SPH_OK;
+}
+
+int sph_profile(sph_handle* h, int enable) {
+  if (!h) return SPH_ERR_INVALID;
+  h->profiling = enable != 0;
+  h->prof_used = 0;
+  h->launches = 0;
+  return SPH_OK;
+}
+
+int sph_profile_read(sph_handle* h, double* pair_ms, int64_t* pair_launches, int64_t* kernel_launches) {
+  if (!h) return SPH_ERR_INVALID;
+  CK(h, cudaStreamSynchronize(h->last_stream));
+  double tot = 0.0;
+  for (size_t k = 0; k + 1 < h->prof_used; k += 2) {
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, h->prof_events[k], h->prof_events[k + 1]));
+    tot += ms;
+  }
+  if (pair_ms) *pair_ms = tot;
+  if (pair_launches) *pair_launches = (int64_t)(h->prof_used / 2);
+  if (kernel_launches) *kernel_launches = h->launches;
+  h->prof_used = 0;
+  h->launches = 0;
+  return SPH_OK;
+}
+
+void sph_destroy(sph_handle* h) {
+  if (!h) return;
+  for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

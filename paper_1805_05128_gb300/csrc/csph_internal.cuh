@@ -1,0 +1,234 @@
+// csph_internal.cuh -- shared declarations of the CUDA implementation of the
+// CSPH hot path (arXiv 1805.05128) for sm_103a.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "csph.h"
+
+namespace csph {
+
+constexpr int kBlock = 256;          // threads of the per-particle kernels
+constexpr int kPairBlock = 128;      // threads of the pair kernel
+constexpr int kListCap = 128;        // per-thread neighbour list capacity (16-bit entries, shared memory)
+constexpr double kCellMargin = 1.0 + 0x1p-20;  // relative safety margin of D^c
+
+// Per-instance cell mesh of eq. (Dcell) on the dense grid.
+struct GridInfo {
+  double x0[3];      // componentwise minimum of the positions
+  double hi[3];      // componentwise maximum of the positions
+  double dc;         // cell edge D^c
+  double inv_dc;     // 1 / D^c
+  double dmax1, dmax2;  // the two largest particle sizes
+  int32_t dims[3];   // cells per axis
+  int32_t pad;
+  int64_t cell_off;  // first global cell of this instance
+  int64_t ncells;
+  float dc_f;        // D^c rounded to FP32 (offset shifts of the mixed kernel)
+  float pad2;
+};
+
+// Per-block partial reductions of the segmented per-particle kernels.
+// Values are order-preserving integer keys of the doubles (see k_step.cu).
+struct BlockPart {
+  long long lo[3], hi[3];  // bounding box
+  long long d1, d2;        // two largest particle sizes
+  long long dtmin;         // min_i eta d_i / (c_i + |v_i|)
+  long long pad;
+};
+
+// Material constants on the device.
+struct Mat {
+  int eos;
+  double gamma, rho0, c0, p_inf, s_a;
+};
+
+struct DevParams {
+  int dim, kernel, precision, n_mat;
+  double kappa, eta, cfl, cell_beta, kh;  // kh = (0.5 kappa) eta
+  Mat mat[SPH_MAX_MAT];
+};
+
+// FP64 packed pair operands (slot order).
+struct alignas(32) D4 { double x, y, z, w; };
+struct alignas(16) D2 { double x, y; };
+
+}  // namespace csph
+
+struct sph_handle {
+  sph_params p;
+  csph::DevParams dp;
+  int n_inst = 0;
+  int64_t n = 0;
+  std::vector<int64_t> inst_off_h;
+  std::vector<int32_t> inst_blk_h;   // first segmented block of each instance (+ total)
+  std::string err;
+  cudaStream_t last_stream = nullptr;
+  bool rates_valid = false;
+  int steps_since_balance = 0;
+
+  // segmented blocks: block b covers particles [blk_start[b], blk_end[b]) of instance blk_inst[b]
+  int nblk = 0;
+  int32_t* blk_inst = nullptr;
+  int64_t* blk_start = nullptr;
+  int64_t* blk_end = nullptr;
+  int32_t* inst_blk = nullptr;   // [n_inst + 1]
+  int64_t* inst_off = nullptr;   // [n_inst + 1]
+
+  csph::BlockPart* part = nullptr;   // [nblk]
+  csph::GridInfo* grid = nullptr;    // [n_inst]
+  double* dt = nullptr;              // [n_inst]
+  int64_t* inst_cap = nullptr;       // [n_inst] cell capacity share of each instance
+  int64_t* total_cells = nullptr;    // device scalar
+
+  // cell lists
+  int64_t cell_cap = 0;
+  int32_t* cell_count = nullptr;     // [cell_cap], kept zero between uses
+  int32_t* cell_start = nullptr;     // [cell_cap + 1]
+  int32_t* scan_sums = nullptr;      // block sums of the scan
+  int32_t* cell_of = nullptr;        // [n] global cell of particle p
+  int32_t* rank = nullptr;           // [n] arrival rank within the cell
+  int32_t* perm = nullptr;           // [n] slot -> particle
+  int32_t* slot_cell = nullptr;      // [n] global cell of slot s
+  int32_t* slot_unit = nullptr;      // [n] work unit of slot s
+
+  // packed operands in slot order (FP32 or FP64 by precision)
+  void* packA = nullptr;
+  void* packB = nullptr;
+  void* packC = nullptr;
+  double* rho_slot = nullptr;        // [n] density of slot s (FP64)
+
+  double* dmax_nbr = nullptr;        // [n] largest neighbour size of particle p (last evaluation)
+
+  // Voronoi work units
+  int K = 0;
+  int gdim = 0;
+  unsigned long long* load_acc = nullptr;  // [K] accumulated full-list pair counts
+  uint32_t* adj_bits = nullptr;            // [K * K/32 rounded up]
+  int32_t* unit_off = nullptr;             // [K + 1]
+  int32_t* unit_list = nullptr;            // [n]
+  int32_t* unit_work = nullptr;            // partition scratch: counts, starts, scan sums
+  int64_t* unit_total = nullptr;           // device scalar K * nb
+  int64_t unit_work_total = 0;             // K * nb on the host
+  double* unit_stats = nullptr;            // [K x 5] centroid, count, max R^hrz
+
+  // optional pair output of the pair kernel (sph_pair_list)
+  bool collect_adj = true;                  // record unit adjacency in the next pair evaluation
+  int32_t* pair_out_i = nullptr;
+  int32_t* pair_out_j = nullptr;
+  int64_t pair_out_cap = 0;
+
+  // profiling: kernel launch count and CUDA events around each pair-kernel launch
+  int64_t launches = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_events;     // pool, used in (start, stop) pairs
+  size_t prof_used = 0;
+
+  int* status = nullptr;                    // device status word
+  unsigned long long* counters = nullptr;   // [5] full-list pairs, candidates, fp64 checks, assign FP64
+                                            // re-evaluations, listed pairs
+
+  // renumbering scratch
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+};
+
+namespace csph {
+
+// --------------------------------------------------------------------------
+// Device closure: EOS, kernel derivative, acoustic solver
+// --------------------------------------------------------------------------
+
+// Returns P and c of material m at (rho, e).  A negative c^2 yields c = 0.
+__device__ __forceinline__ void eos(const Mat& m, double rho, double e, double& P, double& c) {
+  double c2;
+  if (m.eos == SPH_EOS_IDEAL) {
+    P = (m.gamma - 1.0) * rho * e;
+    c2 = m.gamma * P / rho;
+  } else if (m.eos == SPH_EOS_STIFFENED) {
+    P = (m.gamma - 1.0) * rho * e - m.gamma * m.p_inf;
+    c2 = m.gamma * (P + m.p_inf) / rho;
+  } else if (m.eos == SPH_EOS_TAIT) {
+    double B = m.rho0 * m.c0 * m.c0 / m.gamma;
+    double r = rho / m.rho0;
+    P = B * (pow(r, m.gamma) - 1.0);
+    c2 = m.c0 * m.c0 * pow(r, m.gamma - 1.0);
+  } else {  // Mie-Grueneisen with the linear u_s-u_p Hugoniot reference curves
+    double G = m.gamma, ca = m.c0, sa = m.s_a;
+    double x = m.rho0 / rho;
+    double u = 1.0 - x;
+    double D = 1.0 - sa * u;
+    double iD2 = 1.0 / (D * D);
+    double Pr = m.rho0 * ca * ca * u * iD2;
+    double er = 0.5 * ca * ca * u * u * iD2;
+    double du = x / rho;
+    double dPr = m.rho0 * ca * ca * (1.0 + sa * u) * iD2 / D * du;
+    double der = ca * ca * u * iD2 / D * du;
+    P = Pr + G * rho * (e - er);
+    c2 = dPr + G * (e - er) - G * rho * der + G * P / rho;
+  }
+  c = c2 > 0.0 ? sqrt(c2) : 0.0;
+}
+
+// dW/dr of the cubic spline (support 2h) or the Wendland C2 kernel (support
+// kappa h), for dimension DIM.
+template <typename T, int DIM>
+__device__ __forceinline__ T kernel_dw(int kernel, T kappa, T r, T h) {
+  const T pi = T(3.14159265358979323846);
+  if (kernel == SPH_KERNEL_CUBIC) {
+    T ih = T(1) / h;
+    T q = r * ih;
+    T norm;
+    if (DIM == 1) norm = T(2.0 / 3.0) * ih * ih;
+    else if (DIM == 2) norm = T(10) / (T(7) * pi) * ih * ih * ih;
+    else norm = ih * ih * ih * ih / pi;
+    T f;
+    if (q < T(1)) f = q * (T(2.25) * q - T(3));
+    else if (q < T(2)) { T t = T(2) - q; f = T(-0.75) * t * t; }
+    else f = T(0);
+    return norm * f;
+  } else {
+    T H = kappa * h;
+    T iH = T(1) / H;
+    T s = r * iH;
+    if (s >= T(1)) return T(0);
+    T t = T(1) - s;
+    if (DIM == 1) return T(1.25) * iH * iH * (T(-12) * s * t * t);
+    T norm = (DIM == 2) ? T(7) / pi * iH * iH * iH : T(21) / (T(2) * pi) * iH * iH * iH * iH;
+    return norm * (T(-20) * s * t * t * t);
+  }
+}
+
+// --------------------------------------------------------------------------
+// Host helpers shared by the translation units
+// --------------------------------------------------------------------------
+inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+// Launchers (defined in k_step.cu, k_pair.cu, k_vd3.cu).  They enqueue on
+// `st` and return the launch status.
+cudaError_t launch_derive_dt(sph_handle* h, const sph_state& s, bool with_bbox, cudaStream_t st);
+cudaError_t launch_reduce_dt(sph_handle* h, cudaStream_t st);
+cudaError_t launch_kick_drift(sph_handle* h, const sph_state& s, cudaStream_t st);
+cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st);
+cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st);
+cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st);
+cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st);
+// Exclusive scan of cnt[0, *total) into start[0, *total], start[*total] = n_total;
+// cnt is zeroed; launched for up to `cap` elements.
+cudaError_t launch_exclusive_scan(int32_t* cnt, const int64_t* total, int32_t* sums, int32_t* start,
+                                  int64_t n_total, int64_t cap, cudaStream_t st);
+cudaError_t launch_conservation(sph_handle* h, const sph_state& s, double* out, cudaStream_t st);
+cudaError_t launch_check_finite(sph_handle* h, const sph_state& s, cudaStream_t st);
+cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st);
+cudaError_t launch_assign(sph_handle* h, const sph_state& s, const double* gen, int K, int dim,
+                          int32_t* unit_out, cudaStream_t st);
+cudaError_t launch_unit_lists(sph_handle* h, const int32_t* unit, int32_t* unit_offsets, cudaStream_t st);
+cudaError_t launch_balance(sph_handle* h, const sph_state& s, double* gen, int K, int dim,
+                           const double* load, const sph_balance_params& bp, double* shift_out,
+                           cudaStream_t st);
+
+}  // namespace csph

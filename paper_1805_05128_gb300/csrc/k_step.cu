@@ -1,0 +1,618 @@
+// k_step.cu -- per-particle kernels of the CSPH step (HBM-bound): CFL time
+// step, kick-drift-kick updates, the cell mesh of eq. (Dcell) with a
+// counting sort into cells, operand packing for the pair kernel, the
+// renumbering of Sec. 4.2 and the FP64 conservation sums.
+//
+// Every per-particle kernel runs on "segmented" blocks: block b covers the
+// particles [blk_start[b], blk_end[b]) of one instance, so per-instance
+// reductions are fixed-order reductions over whole blocks (no atomics).
+#include <cfloat>
+#include <climits>
+
+#include "csph_internal.cuh"
+
+namespace csph {
+
+namespace {
+
+__device__ __forceinline__ double ld(const double* a, int64_t i) { return a ? a[i] : 0.0; }
+
+__device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+// Reductions run on order-preserving 64-bit integer keys of the doubles
+// (integer ALU instead of the narrow FP64 pipe): key(x) = bits(x) for x >= 0,
+// bits(x) ^ 0x7fff...f for x < 0, so key order is numeric order.
+__device__ __forceinline__ long long dkey(double x) {
+  long long b = __double_as_longlong(x);
+  return b < 0 ? b ^ 0x7fffffffffffffffLL : b;
+}
+__device__ __forceinline__ double dunkey(long long k) {
+  return __longlong_as_double(k < 0 ? k ^ 0x7fffffffffffffffLL : k);
+}
+
+// Merge the top-2 multisets (a1 >= a2) and (b1 >= b2).
+__device__ __forceinline__ void top2_merge(long long& a1, long long& a2, long long b1, long long b2) {
+  if (a1 >= b1) { a2 = a2 > b1 ? a2 : b1; }
+  else { a2 = b2 > a1 ? b2 : a1; a1 = b1; }
+}
+
+struct Red {
+  long long lo[3], hi[3], d1, d2, dtmin;
+};
+
+__device__ __forceinline__ void red_init(Red& r) {
+  for (int a = 0; a < 3; ++a) { r.lo[a] = LLONG_MAX; r.hi[a] = LLONG_MIN; }
+  r.d1 = 0; r.d2 = 0; r.dtmin = LLONG_MAX;
+}
+
+__device__ __forceinline__ void red_merge(Red& a, const Red& b) {
+  for (int k = 0; k < 3; ++k) {
+    a.lo[k] = a.lo[k] < b.lo[k] ? a.lo[k] : b.lo[k];
+    a.hi[k] = a.hi[k] > b.hi[k] ? a.hi[k] : b.hi[k];
+  }
+  top2_merge(a.d1, a.d2, b.d1, b.d2);
+  a.dtmin = a.dtmin < b.dtmin ? a.dtmin : b.dtmin;
+}
+
+// Block-wide reduction of Red through shared memory; result in thread 0.
+__device__ void block_reduce(Red& r) {
+  __shared__ Red sh[kBlock];
+  int t = threadIdx.x;
+  sh[t] = r;
+  __syncthreads();
+  for (int w = kBlock / 2; w > 0; w >>= 1) {
+    if (t < w) red_merge(sh[t], sh[t + w]);
+    __syncthreads();
+  }
+  if (t == 0) r = sh[0];
+}
+
+__device__ __forceinline__ void write_part(BlockPart* part, const Red& r) {
+  BlockPart& b = part[blockIdx.x];
+  for (int a = 0; a < 3; ++a) { b.lo[a] = r.lo[a]; b.hi[a] = r.hi[a]; }
+  b.d1 = r.d1; b.d2 = r.d2; b.dtmin = r.dtmin;
+}
+
+// Cube root in FP64 with little FP64 work: the FP32 cube root as seed, then
+// two Newton steps on y^3 - x = 0 whose derivative reciprocal 1/(3 y^2) is
+// taken in FP32 (a ~1e-7 relative error in the slope only scales each
+// correction, so the error falls ~1e-7-fold per step to rounding level).
+__device__ __forceinline__ double cbrt_fast(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return cbrt(x);   // outside the FP32 seed's comfortable range
+  double y = (double)cbrtf((float)x);
+  const double r = (double)__frcp_rn((float)(3.0 * y * y));
+  y = y - (y * y * y - x) * r;
+  y = y - (y * y * y - x) * r;
+  return y;
+}
+
+__device__ __forceinline__ double size_of(int dim, double m, double rho) {
+  double vol = m / rho;
+  return dim == 1 ? vol : (dim == 2 ? sqrt(vol) : cbrt_fast(vol));
+}
+
+// ---------------------------------------------------------------------------
+// d, P, c at the current state, dt_i = eta d_i / (c_i + |v_i|), optional bbox.
+// ---------------------------------------------------------------------------
+__global__ void k_derive(DevParams P, sph_state s, const int64_t* __restrict__ blk_start,
+                         const int64_t* __restrict__ blk_end, BlockPart* part, int write_derived,
+                         int with_bbox) {
+  int64_t p = blk_start[blockIdx.x] + threadIdx.x;
+  Red r;
+  red_init(r);
+  if (p < blk_end[blockIdx.x]) {
+    double vx = ld(s.vx, p), vy = ld(s.vy, p), vz = ld(s.vz, p);
+    double v2 = vx * vx + vy * vy + vz * vz;
+    double e = s.E[p] - 0.5 * v2;
+    int mi = s.mat ? s.mat[p] : 0;
+    double Pp, cp;
+    eos(P.mat[mi], s.rho[p], e, Pp, cp);
+    double d = size_of(P.dim, s.m[p], s.rho[p]);
+    if (write_derived) { s.d[p] = d; s.P[p] = Pp; s.c[p] = cp; }
+    r.dtmin = dkey((P.eta * d) / (cp + sqrt(v2)));
+    if (with_bbox) {
+      r.lo[0] = r.hi[0] = dkey(s.x[p]);
+      if (P.dim >= 2) r.lo[1] = r.hi[1] = dkey(s.y[p]);
+      if (P.dim >= 3) r.lo[2] = r.hi[2] = dkey(s.z[p]);
+      r.d1 = dkey(d);
+    }
+  }
+  block_reduce(r);
+  if (threadIdx.x == 0) write_part(part, r);
+}
+
+// One block per instance: reduce the block partials of the instance.
+// mode 1: dt = cfl * min; mode 2: bounding box and sizes into the grid record.
+__global__ void k_reduce_inst(const int32_t* __restrict__ inst_blk, const BlockPart* __restrict__ part,
+                              double cfl, double* dt, GridInfo* grid, int mode) {
+  int b = blockIdx.x;
+  Red r;
+  red_init(r);
+  for (int k = inst_blk[b] + threadIdx.x; k < inst_blk[b + 1]; k += blockDim.x) {
+    Red q;
+    for (int a = 0; a < 3; ++a) { q.lo[a] = part[k].lo[a]; q.hi[a] = part[k].hi[a]; }
+    q.d1 = part[k].d1; q.d2 = part[k].d2; q.dtmin = part[k].dtmin;
+    red_merge(r, q);
+  }
+  block_reduce(r);
+  if (threadIdx.x == 0) {
+    if (mode == 1) dt[b] = cfl * dunkey(r.dtmin);
+    if (mode == 2) {
+      GridInfo& g = grid[b];
+      for (int a = 0; a < 3; ++a) { g.x0[a] = dunkey(r.lo[a]); g.hi[a] = dunkey(r.hi[a]); }
+      g.dmax1 = dunkey(r.d1);
+      g.dmax2 = dunkey(r.d2);
+    }
+  }
+}
+
+// Cell mesh per instance (single block): D^c of eq. (Dcell) with the safety
+// margin, doubled until the instance's share of the cell capacity holds the
+// mesh; dims per axis; global cell offsets.  Matches the oracle bit for bit.
+__global__ void k_grid_setup(DevParams P, int n_inst, const int64_t* __restrict__ inst_off,
+                             const int64_t* __restrict__ inst_cap, GridInfo* grid, int64_t* total_cells,
+                             int* status) {
+  if (threadIdx.x != 0) return;
+  int64_t off = 0;
+  for (int b = 0; b < n_inst; ++b) {
+    GridInfo& g = grid[b];
+    double hi[3];
+    for (int a = 0; a < 3; ++a) hi[a] = g.hi[a];
+    for (int a = P.dim; a < 3; ++a) { g.x0[a] = 0.0; g.hi[a] = 0.0; hi[a] = 0.0; }
+    double d1 = g.dmax1, d2 = g.dmax2;
+    if (inst_off[b + 1] - inst_off[b] < 2) d2 = d1;
+    double dc = __dmul_rn(P.kh, __dadd_rn(d1, d2));
+    dc = __dmul_rn(dc, 1.0 + P.cell_beta);
+    dc = __dmul_rn(dc, kCellMargin);
+    if (!(dc > 0.0) || !isfinite(dc)) { set_status(status, SPH_ERR_NONFINITE); dc = 1.0; }
+    int64_t tot;
+    double inv;
+    int64_t dims[3];
+    for (int iter = 0; iter < 2100; ++iter) {
+      inv = 1.0 / dc;
+      tot = 1;
+      for (int a = 0; a < 3; ++a) {
+        dims[a] = (a < P.dim) ? (int64_t)floor(__dmul_rn(__dsub_rn(hi[a], g.x0[a]), inv)) + 1 : 1;
+        tot *= dims[a];
+      }
+      if (tot <= inst_cap[b]) break;
+      dc = dc * 2.0;
+    }
+    g.dc = dc;
+    g.inv_dc = inv;
+    for (int a = 0; a < 3; ++a) g.dims[a] = (int32_t)dims[a];
+    g.ncells = tot;
+    g.cell_off = off;
+    g.dc_f = (float)dc;
+    off += tot;
+  }
+  *total_cells = off;
+}
+
+__device__ __forceinline__ int64_t local_cell(const GridInfo& g, int dim, double x, double y, double z,
+                                              int32_t c[3]) {
+  c[0] = (int32_t)floor(__dmul_rn(__dsub_rn(x, g.x0[0]), g.inv_dc));
+  c[1] = dim >= 2 ? (int32_t)floor(__dmul_rn(__dsub_rn(y, g.x0[1]), g.inv_dc)) : 0;
+  c[2] = dim >= 3 ? (int32_t)floor(__dmul_rn(__dsub_rn(z, g.x0[2]), g.inv_dc)) : 0;
+  return (int64_t)c[0] + (int64_t)g.dims[0] * ((int64_t)c[1] + (int64_t)g.dims[1] * c[2]);
+}
+
+__global__ void k_cell_count(int dim, sph_state s, const int64_t* __restrict__ blk_start,
+                             const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst,
+                             const GridInfo* __restrict__ grid, int32_t* cell_count, int32_t* cell_of,
+                             int32_t* rank, int* status) {
+  int64_t p = blk_start[blockIdx.x] + threadIdx.x;
+  if (p >= blk_end[blockIdx.x]) return;
+  const GridInfo& g = grid[blk_inst[blockIdx.x]];
+  int32_t c[3];
+  int64_t lc = local_cell(g, dim, s.x[p], dim >= 2 ? s.y[p] : 0.0, dim >= 3 ? s.z[p] : 0.0, c);
+  bool ok = true;
+  for (int a = 0; a < 3; ++a) ok = ok && c[a] >= 0 && c[a] < g.dims[a];
+  if (!ok) {  // only a non-finite position can leave the mesh: latch it, stay in bounds
+    set_status(status, SPH_ERR_NONFINITE);
+    lc = 0;
+  }
+  int32_t gc = (int32_t)(g.cell_off + lc);
+  cell_of[p] = gc;
+  rank[p] = atomicAdd(&cell_count[gc], 1);
+}
+
+// Exclusive scan of cell_count[0, total) into cell_start, 1024 cells per tile.
+constexpr int kScanTile = 1024;
+
+__global__ void k_scan_reduce(const int32_t* __restrict__ cnt, const int64_t* __restrict__ total,
+                              int32_t* sums) {
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t tot = *total;
+  if (base >= tot) return;
+  int v = 0;
+  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+    int64_t c = base + k;
+    if (c < tot) v += cnt[c];
+  }
+  __shared__ int sh[kBlock];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = kBlock / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = sh[0];
+}
+
+// Single block: exclusive scan of the tile sums in place.
+__global__ void k_scan_sums(int32_t* sums, const int64_t* __restrict__ total) {
+  int64_t ntiles = (*total + kScanTile - 1) / kScanTile;
+  __shared__ int carry;
+  __shared__ int sh[1024];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < ntiles; base += blockDim.x) {
+    int64_t i = base + threadIdx.x;
+    int v = (i < ntiles) ? sums[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+      int add = threadIdx.x >= (unsigned)off ? sh[threadIdx.x - off] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < ntiles) sums[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += sh[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+// Per tile: exclusive scan plus tile offset; zero the counts for the next use.
+__global__ void k_scan_down(int32_t* cnt, const int64_t* __restrict__ total, const int32_t* __restrict__ sums,
+                            int32_t* start, int64_t n_total) {
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t tot = *total;
+  if (base >= tot) return;
+  constexpr int per = kScanTile / kBlock;  // 4 cells per thread
+  int vals[per];
+  int run = 0;
+  for (int k = 0; k < per; ++k) {
+    int64_t c = base + threadIdx.x * per + k;
+    vals[k] = (c < tot) ? cnt[c] : 0;
+    run += vals[k];
+  }
+  __shared__ int sh[kBlock];
+  sh[threadIdx.x] = run;
+  __syncthreads();
+  for (int off = 1; off < kBlock; off <<= 1) {
+    int add = threadIdx.x >= (unsigned)off ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += add;
+    __syncthreads();
+  }
+  int acc = sums[blockIdx.x] + sh[threadIdx.x] - run;
+  for (int k = 0; k < per; ++k) {
+    int64_t c = base + threadIdx.x * per + k;
+    if (c < tot) {
+      start[c] = acc;
+      acc += vals[k];
+      cnt[c] = 0;
+    }
+  }
+  if (base + kScanTile >= tot && threadIdx.x == 0) start[tot] = (int32_t)n_total;
+}
+
+__global__ void k_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of, const int32_t* __restrict__ rank,
+                               const int32_t* __restrict__ start, int32_t* perm) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  perm[start[cell_of[p]] + rank[p]] = (int32_t)p;
+}
+
+// Within each cell, order the particles by index (the atomic arrival order is
+// not reproducible; this makes the slot order a function of the state only).
+__global__ void k_cell_sort(const int64_t* __restrict__ total, const int32_t* __restrict__ start, int32_t* perm) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= *total) return;
+  int b = start[c], e = start[c + 1];
+  for (int i = b + 1; i < e; ++i) {
+    int32_t v = perm[i];
+    int j = i - 1;
+    while (j >= b && perm[j] > v) { perm[j + 1] = perm[j]; --j; }
+    perm[j + 1] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kick-drift: v <- v + dt/2 a, x <- x + dt v, rho, E half kicks; predicted
+// size d~ from rho~ = rho^h + dt/2 drho; bounding box and sizes for the mesh.
+// ---------------------------------------------------------------------------
+__global__ void k_kick_drift(DevParams P, sph_state s, const int64_t* __restrict__ blk_start,
+                             const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst,
+                             const double* __restrict__ dt, BlockPart* part, int* status) {
+  int64_t p = blk_start[blockIdx.x] + threadIdx.x;
+  Red r;
+  red_init(r);
+  if (p < blk_end[blockIdx.x]) {
+    double h = dt[blk_inst[blockIdx.x]];
+    double hdt = 0.5 * h;
+    double* X[3] = {s.x, s.y, s.z};
+    double* V[3] = {s.vx, s.vy, s.vz};
+    double* A[3] = {s.ax, s.ay, s.az};
+    bool finite = true;
+    for (int a = 0; a < P.dim; ++a) {
+      double vh = __dadd_rn(V[a][p], __dmul_rn(hdt, A[a][p]));
+      double xn = __dadd_rn(X[a][p], __dmul_rn(h, vh));
+      V[a][p] = vh;
+      X[a][p] = xn;
+      r.lo[a] = r.hi[a] = dkey(xn);
+      finite = finite && isfinite(xn);
+    }
+    double rh = __dadd_rn(s.rho[p], __dmul_rn(hdt, s.drho[p]));
+    s.rho[p] = rh;
+    s.E[p] = __dadd_rn(s.E[p], __dmul_rn(hdt, s.dE[p]));
+    double rp = __dadd_rn(rh, __dmul_rn(hdt, s.drho[p]));
+    double d = size_of(P.dim, s.m[p], rp);
+    s.d[p] = d;
+    r.d1 = dkey(d);
+    if (!finite || !isfinite(d)) set_status(status, SPH_ERR_NONFINITE);
+  }
+  block_reduce(r);
+  if (threadIdx.x == 0) write_part(part, r);
+}
+
+// Second half kick with the rates of the predicted state; instance time.
+__global__ void k_kick2(int dim, sph_state s, const int64_t* __restrict__ blk_start,
+                        const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst,
+                        const int32_t* __restrict__ inst_blk, const double* __restrict__ dt, double* t_dev) {
+  int64_t p = blk_start[blockIdx.x] + threadIdx.x;
+  int b = blk_inst[blockIdx.x];
+  if (t_dev && threadIdx.x == 0 && inst_blk[b] == (int)blockIdx.x) t_dev[b] += dt[b];
+  if (p >= blk_end[blockIdx.x]) return;
+  double hdt = 0.5 * dt[b];
+  double* V[3] = {s.vx, s.vy, s.vz};
+  double* A[3] = {s.ax, s.ay, s.az};
+  for (int a = 0; a < dim; ++a) V[a][p] = __dadd_rn(V[a][p], __dmul_rn(hdt, A[a][p]));
+  s.rho[p] = __dadd_rn(s.rho[p], __dmul_rn(hdt, s.drho[p]));
+  s.E[p] = __dadd_rn(s.E[p], __dmul_rn(hdt, s.dE[p]));
+}
+
+// ---------------------------------------------------------------------------
+// Pack the pair operands in slot order.  With predict, the state holds the
+// half-step values q^h and the rates q' of the previous evaluation and the
+// operands are the predicted q~ = q^h + dt/2 q'.  P and c of the packed state
+// are written back to the particle arrays.
+//   mixed: A = {x - o, y - o, z - o, d} (FP32 offsets from the particle's own
+//          cell origin o, the local-origin idea of Sec. 3.1), B = {v, m/rho},
+//          C = {P, rho c}
+//   fp64 : A = {x, y, z, d} (global positions), B, C in FP64
+// ---------------------------------------------------------------------------
+template <bool MIXED>
+__global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk_start,
+                       const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst,
+                       const GridInfo* __restrict__ grid, const double* __restrict__ dt, int predict,
+                       const int32_t* __restrict__ perm, const int32_t* __restrict__ cell_of,
+                       void* packA, void* packB, void* packC, double* rho_slot, int32_t* slot_cell,
+                       int32_t* slot_unit, int n_units, int* status) {
+  int64_t sl = blk_start[blockIdx.x] + threadIdx.x;
+  if (sl >= blk_end[blockIdx.x]) return;
+  int b = blk_inst[blockIdx.x];
+  int64_t p = perm[sl];
+  double hdt = predict ? 0.5 * dt[b] : 0.0;
+  double v[3] = {ld(s.vx, p), ld(s.vy, p), ld(s.vz, p)};
+  if (predict) {
+    v[0] = __dadd_rn(v[0], __dmul_rn(hdt, s.ax[p]));
+    if (P.dim >= 2) v[1] = __dadd_rn(v[1], __dmul_rn(hdt, s.ay[p]));
+    if (P.dim >= 3) v[2] = __dadd_rn(v[2], __dmul_rn(hdt, s.az[p]));
+  }
+  double rho = predict ? __dadd_rn(s.rho[p], __dmul_rn(hdt, s.drho[p])) : s.rho[p];
+  double E = predict ? __dadd_rn(s.E[p], __dmul_rn(hdt, s.dE[p])) : s.E[p];
+  double e = E - 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  int mi = s.mat ? s.mat[p] : 0;
+  double Pp, cp;
+  eos(P.mat[mi], rho, e, Pp, cp);
+  s.P[p] = Pp;
+  s.c[p] = cp;
+  double d = s.d[p];
+  double m = s.m[p];
+  double X[3] = {s.x[p], P.dim >= 2 ? s.y[p] : 0.0, P.dim >= 3 ? s.z[p] : 0.0};
+  int32_t gc = cell_of[p];
+  slot_cell[sl] = gc;
+  int32_t u = s.unit ? s.unit[p] : 0;
+  if (u < 0 || u >= n_units) { if (n_units > 0) set_status(status, SPH_ERR_INVALID); u = 0; }
+  slot_unit[sl] = u;
+  rho_slot[sl] = rho;
+  if (MIXED) {
+    const GridInfo& g = grid[b];
+    int64_t lc = gc - g.cell_off;
+    int64_t c0 = lc % g.dims[0];
+    int64_t c1 = (lc / g.dims[0]) % g.dims[1];
+    int64_t c2 = lc / ((int64_t)g.dims[0] * g.dims[1]);
+    int64_t cc[3] = {c0, c1, c2};
+    float off[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < P.dim; ++a) off[a] = (float)(X[a] - (g.x0[a] + (double)cc[a] * g.dc));
+    reinterpret_cast<float4*>(packA)[sl] = make_float4(off[0], off[1], off[2], (float)d);
+    reinterpret_cast<float4*>(packB)[sl] =
+        make_float4((float)v[0], (float)v[1], (float)v[2], (float)(m / rho));
+    reinterpret_cast<float2*>(packC)[sl] = make_float2((float)Pp, (float)(rho * cp));
+  } else {
+    reinterpret_cast<D4*>(packA)[sl] = D4{X[0], X[1], X[2], d};
+    reinterpret_cast<D4*>(packB)[sl] = D4{v[0], v[1], v[2], m / rho};
+    reinterpret_cast<D2*>(packC)[sl] = D2{Pp, rho * cp};
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Renumbering: gather every per-particle array through perm, copy back.
+// ---------------------------------------------------------------------------
+constexpr int kMaxPermArrays = 24;
+struct PermArrays {
+  void* ptr[kMaxPermArrays];
+  int bytes[kMaxPermArrays];   // element size: 4 or 8
+  int count;
+};
+
+__global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, PermArrays a, char* scratch) {
+  int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= n) return;
+  int64_t p = perm[sl];
+  size_t off = 0;
+  for (int k = 0; k < a.count; ++k) {
+    if (a.bytes[k] == 8) reinterpret_cast<uint64_t*>(scratch + off)[sl] = reinterpret_cast<const uint64_t*>(a.ptr[k])[p];
+    else reinterpret_cast<uint32_t*>(scratch + off)[sl] = reinterpret_cast<const uint32_t*>(a.ptr[k])[p];
+    off += (size_t)a.bytes[k] * n;
+  }
+}
+
+__global__ void k_scatter_back(int64_t n, PermArrays a, const char* scratch) {
+  int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= n) return;
+  size_t off = 0;
+  for (int k = 0; k < a.count; ++k) {
+    if (a.bytes[k] == 8) reinterpret_cast<uint64_t*>(a.ptr[k])[sl] = reinterpret_cast<const uint64_t*>(scratch + off)[sl];
+    else reinterpret_cast<uint32_t*>(a.ptr[k])[sl] = reinterpret_cast<const uint32_t*>(scratch + off)[sl];
+    off += (size_t)a.bytes[k] * n;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 conservation sums per instance, fixed order: thread t sums particles
+// t, t + blockDim, ...; then a tree over threads.
+// ---------------------------------------------------------------------------
+__global__ void k_conservation(sph_state s, const int64_t* __restrict__ inst_off, double* out) {
+  int b = blockIdx.x;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int64_t p = inst_off[b] + threadIdx.x; p < inst_off[b + 1]; p += blockDim.x) {
+    double m = s.m[p];
+    acc[0] += m;
+    acc[1] += m * ld(s.vx, p);
+    acc[2] += m * ld(s.vy, p);
+    acc[3] += m * ld(s.vz, p);
+    acc[4] += m * s.E[p];
+  }
+  __shared__ double sh[5][kBlock];
+  for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = kBlock / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 5; ++k) out[b * 5 + k] = sh[k][0];
+}
+
+__global__ void k_check_finite(int dim, sph_state s, int64_t n, int* status) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  bool ok = isfinite(s.x[p]) && isfinite(s.vx[p]) && isfinite(s.rho[p]) && isfinite(s.E[p]) &&
+            isfinite(s.m[p]) && s.rho[p] > 0.0 && s.m[p] > 0.0;
+  if (dim >= 2) ok = ok && isfinite(s.y[p]) && isfinite(s.vy[p]);
+  if (dim >= 3) ok = ok && isfinite(s.z[p]) && isfinite(s.vz[p]);
+  if (!ok) set_status(status, SPH_ERR_NONFINITE);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_derive_dt(sph_handle* h, const sph_state& s, bool with_bbox, cudaStream_t st) {
+  k_derive<<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->part, with_bbox ? 1 : 0,
+                                       with_bbox ? 1 : 0);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_dt(sph_handle* h, cudaStream_t st) {
+  k_reduce_inst<<<h->n_inst, kBlock, 0, st>>>(h->inst_blk, h->part, h->dp.cfl, h->dt, h->grid, 1);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kick_drift(sph_handle* h, const sph_state& s, cudaStream_t st) {
+  k_kick_drift<<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->dt, h->part,
+                                           h->status);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+// Mesh from the block partials left by k_derive(with_bbox) or k_kick_drift,
+// then the counting sort of particles into cells.
+cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st) {
+  k_reduce_inst<<<h->n_inst, kBlock, 0, st>>>(h->inst_blk, h->part, h->dp.cfl, h->dt, h->grid, 2);
+  k_grid_setup<<<1, 32, 0, st>>>(h->dp, h->n_inst, h->inst_off, h->inst_cap, h->grid, h->total_cells,
+                                 h->status);
+  k_cell_count<<<h->nblk, kBlock, 0, st>>>(h->dp.dim, s, h->blk_start, h->blk_end, h->blk_inst, h->grid,
+                                           h->cell_count, h->cell_of, h->rank, h->status);
+  int tiles = grid_for(h->cell_cap, kScanTile);
+  k_scan_reduce<<<tiles, kBlock, 0, st>>>(h->cell_count, h->total_cells, h->scan_sums);
+  k_scan_sums<<<1, 1024, 0, st>>>(h->scan_sums, h->total_cells);
+  k_scan_down<<<tiles, kBlock, 0, st>>>(h->cell_count, h->total_cells, h->scan_sums, h->cell_start, h->n);
+  k_cell_scatter<<<grid_for(h->n, kBlock), kBlock, 0, st>>>(h->n, h->cell_of, h->rank, h->cell_start, h->perm);
+  k_cell_sort<<<grid_for(h->cell_cap, kBlock), kBlock, 0, st>>>(h->total_cells, h->cell_start, h->perm);
+  h->launches += 8;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st) {
+  if (h->dp.precision == SPH_PREC_MIXED)
+    k_pack<true><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->grid, h->dt,
+                                             predict ? 1 : 0, h->perm, h->cell_of, h->packA, h->packB, h->packC,
+                                             h->rho_slot, h->slot_cell, h->slot_unit, h->K, h->status);
+  else
+    k_pack<false><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->grid, h->dt,
+                                              predict ? 1 : 0, h->perm, h->cell_of, h->packA, h->packB, h->packC,
+                                              h->rho_slot, h->slot_cell, h->slot_unit, h->K, h->status);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st) {
+  k_kick2<<<h->nblk, kBlock, 0, st>>>(h->dp.dim, s, h->blk_start, h->blk_end, h->blk_inst, h->inst_blk, h->dt,
+                                      t_dev);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st) {
+  PermArrays a;
+  a.count = 0;
+  auto add = [&](void* ptr, int bytes) {
+    if (ptr) { a.ptr[a.count] = ptr; a.bytes[a.count] = bytes; ++a.count; }
+  };
+  add(s.x, 8); add(s.y, 8); add(s.z, 8);
+  add(s.vx, 8); add(s.vy, 8); add(s.vz, 8);
+  add(s.rho, 8); add(s.E, 8); add(s.m, 8);
+  add(s.ax, 8); add(s.ay, 8); add(s.az, 8); add(s.drho, 8); add(s.dE, 8);
+  add(s.d, 8); add(s.P, 8); add(s.c, 8);
+  add(s.id, 8);
+  add(s.mat, 4); add(s.unit, 4);
+  int g = grid_for(h->n, kBlock);
+  k_gather<<<g, kBlock, 0, st>>>(h->n, h->perm, a, reinterpret_cast<char*>(h->scratch));
+  k_scatter_back<<<g, kBlock, 0, st>>>(h->n, a, reinterpret_cast<const char*>(h->scratch));
+  h->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exclusive_scan(int32_t* cnt, const int64_t* total, int32_t* sums, int32_t* start,
+                                  int64_t n_total, int64_t cap, cudaStream_t st) {
+  int tiles = grid_for(cap, kScanTile);
+  k_scan_reduce<<<tiles, kBlock, 0, st>>>(cnt, total, sums);
+  k_scan_sums<<<1, 1024, 0, st>>>(sums, total);
+  k_scan_down<<<tiles, kBlock, 0, st>>>(cnt, total, sums, start, n_total);
+  return cudaGetLastError();
+}
+// (launch_exclusive_scan's three kernels are counted by its callers)
+
+cudaError_t launch_conservation(sph_handle* h, const sph_state& s, double* out, cudaStream_t st) {
+  k_conservation<<<h->n_inst, kBlock, 0, st>>>(s, h->inst_off, out);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(sph_handle* h, const sph_state& s, cudaStream_t st) {
+  k_check_finite<<<grid_for(h->n, kBlock), kBlock, 0, st>>>(h->dp.dim, s, h->n, h->status);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace csph

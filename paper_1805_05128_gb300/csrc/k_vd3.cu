@@ -1,0 +1,372 @@
+// k_vd3.cu -- Voronoi dynamic decomposition recast as the work-unit
+// partition of one GPU (Secs. 3.1-3.4, 4.3): nearest-generator assignment,
+// stable per-unit particle lists, per-unit statistics (centroid, D^sh) and
+// the balancing update of the generators.
+#include <cfloat>
+
+#include "csph_internal.cuh"
+
+namespace csph {
+
+namespace {
+
+constexpr int kUnitBlock = 1024;   // particles per block of the unit partition kernels
+
+// ---------------------------------------------------------------------------
+// Nearest generator, eq. (VoronoiDefinition), ties to the smaller index.
+// FP32 pass on offsets from the generators' mean o: with M = max(|x - o|_inf,
+// max_k |g_k - o|_inf) each squared distance carries an error below
+// dim M^2 2^-19; every k within 3 such bounds of the FP32 minimum is then
+// re-evaluated in FP64 with the oracle's operation order (dx = x - g,
+// squares summed in axis order), the smallest with strict < winning.
+// ---------------------------------------------------------------------------
+__global__ void k_assign(int64_t n, int dim, const double* __restrict__ x, const double* __restrict__ y,
+                         const double* __restrict__ z, const double* __restrict__ gen, int K,
+                         int32_t* unit, unsigned long long* n_exact) {
+  __shared__ double gd[SPH_MAX_UNITS * 3];
+  __shared__ float gf[SPH_MAX_UNITS * 3];
+  __shared__ double org[3];
+  __shared__ float gmax;
+  for (int k = threadIdx.x; k < K * dim; k += blockDim.x) gd[k] = gen[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int a = 0; a < dim; ++a) {
+      double s = 0.0;
+      for (int k = 0; k < K; ++k) s += gd[k * dim + a];
+      org[a] = s / K;
+    }
+    float gm = 0.f;
+    for (int k = 0; k < K; ++k)
+      for (int a = 0; a < dim; ++a) {
+        float v = (float)(gd[k * dim + a] - org[a]);
+        gf[k * dim + a] = v;
+        gm = fmaxf(gm, fabsf(v));
+      }
+    gmax = gm;
+  }
+  __syncthreads();
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const double* X[3] = {x, y, z};
+  float xf[3] = {0.f, 0.f, 0.f};
+  float M = gmax;
+  for (int a = 0; a < dim; ++a) {
+    xf[a] = (float)(X[a][p] - org[a]);
+    M = fmaxf(M, fabsf(xf[a]));
+  }
+  // inflate M by a relative 2^-20 for the rounding of M itself
+  M = M * (1.0f + 0x1p-20f);
+  const float B = (float)dim * M * M * 0x1p-19f;
+  float best = FLT_MAX;
+  for (int k = 0; k < K; ++k) {
+    float d2 = 0.f;
+    for (int a = 0; a < dim; ++a) {
+      float t = xf[a] - gf[k * dim + a];
+      d2 = fmaf(t, t, d2);
+    }
+    best = fminf(best, d2);
+  }
+  const float lim = best + 3.0f * B;
+  int first = -1, ncand = 0;
+  for (int k = 0; k < K; ++k) {
+    float d2 = 0.f;
+    for (int a = 0; a < dim; ++a) {
+      float t = xf[a] - gf[k * dim + a];
+      d2 = fmaf(t, t, d2);
+    }
+    if (d2 <= lim) {
+      if (first < 0) first = k;
+      ++ncand;
+    }
+  }
+  int win = first;
+  if (ncand > 1) {
+    atomicAdd(n_exact, 1ull);
+    double bd = DBL_MAX;
+    for (int k = first; k < K; ++k) {
+      float d2f = 0.f;
+      for (int a = 0; a < dim; ++a) {
+        float t = xf[a] - gf[k * dim + a];
+        d2f = fmaf(t, t, d2f);
+      }
+      if (d2f > lim) continue;
+      double dx = __dsub_rn(X[0][p], gd[k * dim + 0]);
+      double d2 = __dmul_rn(dx, dx);
+      if (dim >= 2) { double dy = __dsub_rn(X[1][p], gd[k * dim + 1]); d2 = __dadd_rn(d2, __dmul_rn(dy, dy)); }
+      if (dim >= 3) { double dz = __dsub_rn(X[2][p], gd[k * dim + 2]); d2 = __dadd_rn(d2, __dmul_rn(dz, dz)); }
+      if (d2 < bd) { bd = d2; win = k; }
+    }
+  }
+  unit[p] = win < 0 ? 0 : win;   // no candidate only for non-finite input (latched elsewhere)
+}
+
+// ---------------------------------------------------------------------------
+// Stable partition of the particles by unit.  Block b of kUnitBlock
+// particles counts each unit per warp; counts[u * nb + b] feed an exclusive
+// scan; the scatter ranks each particle by (warp, lane) inside its block, so
+// each unit's list keeps ascending particle order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void warp_unit_counts(const int32_t* unit, int64_t n, int K, int* wcnt,
+                                                 int& my_unit, int& rank_in_warp) {
+  // wcnt: [32 warps][K] in shared memory, zeroed by the caller
+  int64_t p = (int64_t)blockIdx.x * kUnitBlock + threadIdx.x;
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  my_unit = (p < n) ? unit[p] : -1;
+  if (p < n && (my_unit < 0 || my_unit >= K)) my_unit = 0;   // stays in bounds; k_pack latches the error
+  unsigned same = __match_any_sync(0xffffffffu, my_unit);
+  rank_in_warp = __popc(same & ((1u << lane) - 1u));
+  if (my_unit >= 0 && rank_in_warp == 0) wcnt[w * K + my_unit] = __popc(same);
+}
+
+__global__ void k_unit_hist(const int32_t* __restrict__ unit, int64_t n, int K, int nb, int32_t* counts) {
+  extern __shared__ int wcnt[];
+  for (int k = threadIdx.x; k < 32 * K; k += blockDim.x) wcnt[k] = 0;
+  __syncthreads();
+  int u, r;
+  warp_unit_counts(unit, n, K, wcnt, u, r);
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    int s = 0;
+    for (int w = 0; w < 32; ++w) s += wcnt[w * K + k];
+    counts[(int64_t)k * nb + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_unit_scatter(const int32_t* __restrict__ unit, int64_t n, int K, int nb,
+                               const int32_t* __restrict__ start, int32_t* list) {
+  extern __shared__ int wcnt[];
+  for (int k = threadIdx.x; k < 32 * K; k += blockDim.x) wcnt[k] = 0;
+  __syncthreads();
+  int u, r;
+  warp_unit_counts(unit, n, K, wcnt, u, r);
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {  // exclusive prefix over warps
+    int s = 0;
+    for (int w = 0; w < 32; ++w) { int c = wcnt[w * K + k]; wcnt[w * K + k] = s; s += c; }
+  }
+  __syncthreads();
+  int64_t p = (int64_t)blockIdx.x * kUnitBlock + threadIdx.x;
+  if (p < n) {
+    int w = threadIdx.x >> 5;
+    list[start[(int64_t)u * nb + blockIdx.x] + wcnt[w * K + u] + r] = (int32_t)p;
+  }
+}
+
+__global__ void k_unit_offsets(const int32_t* __restrict__ start, int K, int nb, int64_t n, int32_t* unit_off,
+                               int32_t* out_copy) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > K) return;
+  int32_t v = (k < K) ? start[(int64_t)k * nb] : (int32_t)n;
+  unit_off[k] = v;
+  if (out_copy) out_copy[k] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Per-unit statistics, one block per unit, fixed summation order:
+// centroid (eq. VoronoiGeomCenters over the current positions), count, and
+// max_{i in k} R^hrz_i with R^hrz_i = (1 + beta)(kh (d_i + max_j d_j)).
+// ---------------------------------------------------------------------------
+__global__ void k_unit_stats(const int32_t* __restrict__ unit_off, const int32_t* __restrict__ list,
+                             const double* __restrict__ x, const double* __restrict__ y,
+                             const double* __restrict__ z, const double* __restrict__ d,
+                             const double* __restrict__ dmax_nbr, int gdim, double kh, double beta,
+                             double* out /* K x 5: cx, cy, cz, count, rmax */) {
+  int k = blockIdx.x;
+  int b = unit_off[k], e = unit_off[k + 1];
+  double acc[3] = {0, 0, 0};
+  double rmax = 0.0;
+  const double* X[3] = {x, y, z};
+  for (int q = b + threadIdx.x; q < e; q += blockDim.x) {
+    int64_t p = list[q];
+    for (int a = 0; a < gdim; ++a) acc[a] += X[a][p];
+    double dm = dmax_nbr[p] < 0.0 ? d[p] : dmax_nbr[p];
+    double r = (1.0 + beta) * (kh * (d[p] + dm));
+    rmax = fmax(rmax, r);
+  }
+  __shared__ double sh[4][kBlock];
+  for (int a = 0; a < 3; ++a) sh[a][threadIdx.x] = acc[a];
+  sh[3][threadIdx.x] = rmax;
+  __syncthreads();
+  for (int w = kBlock / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      for (int a = 0; a < 3; ++a) sh[a][threadIdx.x] += sh[a][threadIdx.x + w];
+      sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int cnt = e - b;
+    for (int a = 0; a < 3; ++a) out[k * 5 + a] = cnt > 0 ? sh[a][0] / (double)cnt : 0.0;
+    out[k * 5 + 3] = (double)cnt;
+    out[k * 5 + 4] = sh[3][0];
+  }
+}
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ void rotate3(const double ax[3], double alpha, const double v[3], double out[3]) {
+  double na = sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
+  if (na == 0.0) { out[0] = v[0]; out[1] = v[1]; out[2] = v[2]; return; }
+  double u[3] = {ax[0] / na, ax[1] / na, ax[2] / na};
+  double c = cos(alpha), s = sin(alpha);
+  double uxv[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+  double udv = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+  for (int q = 0; q < 3; ++q) out[q] = v[q] * c + uxv[q] * s + u[q] * udv * (1.0 - c);
+}
+
+// ---------------------------------------------------------------------------
+// Balancing update (single block, thread k = generator k):
+//   eq. (BalancingOffset)       two-body, g_kl = g_k - g_l
+//   eq. (BalancingOffsetRot)    three-body for 2D decompositions, each
+//                               triangle of mutually adjacent units once,
+//                               length limited to max_l D^sh_kl
+//   eq. (BalancingOffsetPlusRot), eq. (TotalOffset)
+// D^sh_kl = max(rmax_k, rmax_l) (eq. Horizon).  Loads: caller's, else half
+// the accumulated full-list pair counts.  Resets the accumulators.
+// ---------------------------------------------------------------------------
+__global__ void k_balance(int K, int gdim, double* gen, const double* __restrict__ load_in,
+                          unsigned long long* load_acc, uint32_t* adj_bits, int adj_words,
+                          const double* __restrict__ stats, double theta, double sigma, double gamma_b,
+                          double* shift_out) {
+  __shared__ double L[SPH_MAX_UNITS];
+  __shared__ double G[SPH_MAX_UNITS * 3];
+  __shared__ double NG[SPH_MAX_UNITS * 3];
+  __shared__ double SH[SPH_MAX_UNITS];
+  const double pi = 3.14159265358979323846;
+  int k = threadIdx.x;
+  if (k < K) {
+    L[k] = load_in ? load_in[k] : 0.5 * (double)load_acc[k];
+    for (int a = 0; a < 3; ++a) G[k * 3 + a] = a < gdim ? gen[k * gdim + a] : 0.0;
+  }
+  __syncthreads();
+  double sig = (gdim == 2) ? sigma : 0.0;
+  auto adj = [&](int r, int c) -> bool { return (adj_bits[r * adj_words + (c >> 5)] >> (c & 31)) & 1u; };
+  auto dsh = [&](int r, int c) -> double {
+    double a = stats[r * 5 + 4], b = stats[c * 5 + 4];
+    return a > b ? a : b;
+  };
+  if (k < K) {
+    const double* gk = &G[k * 3];
+    double dg2[3] = {0, 0, 0}, dg3[3] = {0, 0, 0};
+    double maxd = 0.0;
+    for (int l = 0; l < K; ++l) {
+      if (l == k || !adj(k, l)) continue;
+      double D = dsh(k, l);
+      if (D > maxd) maxd = D;
+      double den = L[k] + L[l];
+      if (!(den > 0.0)) continue;
+      double gkl[3] = {gk[0] - G[l * 3], gk[1] - G[l * 3 + 1], gk[2] - G[l * 3 + 2]};
+      double nrm = sqrt(gkl[0] * gkl[0] + gkl[1] * gkl[1] + gkl[2] * gkl[2]);
+      if (nrm == 0.0) continue;
+      double f = D * ((L[k] - L[l]) / den) / nrm;
+      for (int a = 0; a < 3; ++a) dg2[a] += f * gkl[a];
+    }
+    if (sig != 0.0) {
+      for (int l = 0; l < K; ++l) {
+        if (l == k || !adj(k, l)) continue;
+        for (int m = l + 1; m < K; ++m) {
+          if (m == k || !adj(k, m) || !adj(l, m)) continue;
+          const double* gl = &G[l * 3];
+          const double* gm = &G[m * 3];
+          double ax = gl[0] - gk[0], ay = gl[1] - gk[1];
+          double bx = gm[0] - gk[0], by = gm[1] - gk[1];
+          double a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
+          double crs = ax * by - ay * bx;
+          double scale2 = a2 > b2 ? a2 : b2;
+          if (fabs(crs) < 1e-12 * scale2) continue;
+          double Dd = 2.0 * crs;
+          double ox = gk[0] + (by * a2 - ay * b2) / Dd;
+          double oy = gk[1] + (ax * b2 - bx * a2) / Dd;
+          double Ls = L[k] + L[l] + L[m];
+          if (!(Ls > 0.0)) continue;
+          double al = pi / 3.0 * (L[l] - L[k]) / Ls;
+          double am = pi / 3.0 * (L[m] - L[k]) / Ls;
+          double ck[3] = {gk[0] - ox, gk[1] - oy, 0.0};
+          double cl[3] = {gl[0] - ox, gl[1] - oy, 0.0};
+          double cm[3] = {gm[0] - ox, gm[1] - oy, 0.0};
+          double axl[3], axm[3], r1[3], r2[3];
+          cross3(ck, cl, axl);
+          cross3(ck, cm, axm);
+          rotate3(axl, al, ck, r1);
+          rotate3(axm, am, r1, r2);
+          for (int a = 0; a < 3; ++a) dg3[a] += r2[a] - ck[a];
+        }
+      }
+      double n3 = sqrt(dg3[0] * dg3[0] + dg3[1] * dg3[1] + dg3[2] * dg3[2]);
+      if (n3 > maxd && n3 > 0.0) {
+        double f = maxd / n3;
+        for (int a = 0; a < 3; ++a) dg3[a] *= f;
+      }
+    }
+    double cnt = stats[k * 5 + 3];
+    double dist2 = 0.0;
+    for (int a = 0; a < gdim; ++a) {
+      double dg = (1.0 - sig) * dg2[a] + sig * dg3[a];
+      double rc = cnt > 0.0 ? stats[k * 5 + a] : gk[a];
+      double ng = (1.0 - theta) * (gk[a] + gamma_b * dg) + theta * rc;
+      NG[k * 3 + a] = ng;
+      dist2 += (ng - gk[a]) * (ng - gk[a]);
+    }
+    SH[k] = sqrt(dist2);
+  }
+  __syncthreads();
+  if (k < K)
+    for (int a = 0; a < gdim; ++a) gen[k * gdim + a] = NG[k * 3 + a];
+  if (k == 0) {
+    double s = 0.0;
+    for (int q = 0; q < K; ++q) s += SH[q];
+    if (shift_out) *shift_out = s;
+  }
+  __syncthreads();
+  if (k < K) {
+    load_acc[k] = 0ull;
+    for (int w = 0; w < adj_words; ++w) adj_bits[k * adj_words + w] = 0u;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_assign(sph_handle* h, const sph_state& s, const double* gen, int K, int dim,
+                          int32_t* unit_out, cudaStream_t st) {
+  k_assign<<<grid_for(h->n, kBlock), kBlock, 0, st>>>(h->n, dim, s.x, s.y, s.z, gen, K, unit_out,
+                                                      &h->counters[3]);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unit_lists(sph_handle* h, const int32_t* unit, int32_t* unit_offsets, cudaStream_t st) {
+  int K = h->K;
+  int nb = grid_for(h->n, kUnitBlock);
+  size_t smem = sizeof(int) * 32 * K;
+  int32_t* counts = h->unit_work;                 // [K * nb]
+  int32_t* starts = counts + (size_t)K * nb;       // [K * nb + 1]
+  int32_t* sums = starts + (size_t)K * nb + 1;     // [K * nb / 1024 + 1]
+  int64_t tot = h->unit_work_total;                // = K * nb, also in h->unit_total
+  cudaError_t e;
+  k_unit_hist<<<nb, kUnitBlock, smem, st>>>(unit, h->n, K, nb, counts);
+  e = launch_exclusive_scan(counts, h->unit_total, sums, starts, h->n, tot, st);
+  if (e != cudaSuccess) return e;
+  k_unit_scatter<<<nb, kUnitBlock, smem, st>>>(unit, h->n, K, nb, starts, h->unit_list);
+  k_unit_offsets<<<grid_for(K + 1, kBlock), kBlock, 0, st>>>(starts, K, nb, h->n, h->unit_off, unit_offsets);
+  h->launches += 6;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_balance(sph_handle* h, const sph_state& s, double* gen, int K, int dim, const double* load,
+                           const sph_balance_params& bp, double* shift_out, cudaStream_t st) {
+  cudaError_t e = launch_unit_lists(h, s.unit, nullptr, st);
+  if (e != cudaSuccess) return e;
+  double* stats = h->unit_stats;
+  k_unit_stats<<<K, kBlock, 0, st>>>(h->unit_off, h->unit_list, s.x, s.y, s.z, s.d, h->dmax_nbr, dim, h->dp.kh,
+                                     bp.beta_sh, stats);
+  k_balance<<<1, SPH_MAX_UNITS, 0, st>>>(K, dim, gen, load, h->load_acc, h->adj_bits, (K + 31) / 32, stats,
+                                         bp.theta, bp.sigma, bp.gamma_b, shift_out);
+  h->launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace csph

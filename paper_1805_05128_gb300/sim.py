@@ -1,0 +1,177 @@
+"""Simulation: torch device tensors for the particle state plus a libcsph
+handle.  Torch provides device memory and the stream; every step of the hot
+path runs in the CUDA kernels behind the C ABI."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import abi
+
+_EOS = {"ideal": abi.SPH_EOS_IDEAL, "stiffened": abi.SPH_EOS_STIFFENED, "tait": abi.SPH_EOS_TAIT,
+        "mie_gruneisen": abi.SPH_EOS_MIE_GRUNEISEN}
+_KERNEL = {"cubic": abi.SPH_KERNEL_CUBIC, "wendland_c2": abi.SPH_KERNEL_WENDLAND_C2}
+_PREC = {"fp64": abi.SPH_PREC_FP64, "mixed": abi.SPH_PREC_MIXED}
+
+
+def _stream_ptr() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Simulation:
+    """One or more independent CSPH instances on one GPU.
+
+    ``problems``: objects with the attributes of ``synth.Problem`` (dim,
+    arrays, materials, mat, kernel, kappa, eta, cfl, units, unit_dim, n_upd);
+    several problems become instances of one handle (same parameters)."""
+
+    def __init__(self, problems, precision: str = "mixed", units: int | None = None,
+                 generators=None, n_upd: int | None = None, theta: float = 0.25, sigma: float = 0.5,
+                 gamma_b: float = 1.0, beta_sh: float = 0.45, cell_cap: int = 1 << 24,
+                 device: str | torch.device = "cuda:0"):
+        if not isinstance(problems, (list, tuple)):
+            problems = [problems]
+        self.device = torch.device(device)
+        p0 = problems[0]
+        self.dim = p0.dim
+        self.n_inst = len(problems)
+        sizes = [len(q.arrays["x"]) for q in problems]
+        self.inst_offsets = [0] + list(np.cumsum(sizes))
+        self.n = int(self.inst_offsets[-1])
+        dev = self.device
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.t = {}
+        for k in abi.STATE_F64 + abi.STATE_RATES + abi.STATE_DERIVED:
+            axis = "xyz".index(k[-1]) if k in ("y", "z", "vy", "vz", "ay", "az") else -1
+            if axis >= self.dim:
+                self.t[k] = None
+                continue
+            if k in abi.STATE_F64:
+                vals = [np.asarray(q.arrays.get(k, np.zeros(len(q.arrays["x"]))), dtype=np.float64) for q in problems]
+                self.t[k] = torch.from_numpy(np.concatenate(vals)).to(**f64).contiguous()
+            else:
+                self.t[k] = torch.zeros(self.n, **f64)
+        mats = [q.mat if q.mat is not None else np.zeros(len(q.arrays["x"]), dtype=np.int32) for q in problems]
+        self.t["mat"] = torch.from_numpy(np.concatenate(mats).astype(np.int32)).to(dev)
+        self.t["id"] = torch.arange(self.n, dtype=torch.int64, device=dev)
+        K = p0.units if units is None else units
+        self.K = int(K) if self.n_inst == 1 else 0
+        self.unit_dim = p0.unit_dim
+        self.t["unit"] = torch.zeros(self.n, dtype=torch.int32, device=dev)
+        self.gen = None
+        if self.K > 0:
+            if generators is None:
+                raise ValueError("work units need initial generators")
+            self.gen = torch.as_tensor(np.asarray(generators, dtype=np.float64), device=dev).contiguous()
+            assert self.gen.shape == (self.K, self.unit_dim)
+        self.time = torch.zeros(self.n_inst, **f64)
+
+        prm = abi.sph_params()
+        prm.dim, prm.kernel, prm.precision = self.dim, _KERNEL[p0.kernel], _PREC[precision]
+        prm.n_mat = len(p0.materials)
+        prm.kappa, prm.eta, prm.cfl, prm.cell_beta, prm.cell_cap = p0.kappa, p0.eta, p0.cfl, 0.0, cell_cap
+        for i, m in enumerate(p0.materials):
+            prm.mat[i].eos, prm.mat[i].gamma, prm.mat[i].rho0 = _EOS[m.eos], m.gamma, m.rho0
+            prm.mat[i].c0, prm.mat[i].p_inf, prm.mat[i].s_a = m.c0, m.p_inf, m.s_a
+        prm.n_units, prm.unit_dim = self.K, self.unit_dim
+        prm.n_upd = (p0.n_upd if n_upd is None else n_upd) if self.K > 0 else 0
+        prm.theta, prm.sigma, prm.gamma_b, prm.beta_sh = theta, sigma, gamma_b, beta_sh
+        prm.generators = self.gen.data_ptr() if self.gen is not None else None
+        self.params = prm
+        self.precision = precision
+        self.handle = abi.sph_init(prm, self.n_inst, [int(v) for v in self.inst_offsets], self.state(),
+                                   _stream_ptr())
+
+    # ---------------------------------------------------------------- state
+    def state(self) -> abi.sph_state:
+        s = abi.sph_state()
+        s.n = self.n
+        for k in abi.STATE_F64 + abi.STATE_RATES + abi.STATE_DERIVED + ("mat", "id", "unit"):
+            v = self.t[k]
+            setattr(s, k, v.data_ptr() if v is not None else None)
+        return s
+
+    def numpy(self) -> dict:
+        torch.cuda.synchronize(self.device)
+        return {k: v.cpu().numpy() for k, v in self.t.items() if v is not None}
+
+    # ---------------------------------------------------------------- calls
+    def build_cells(self):
+        abi.sph_build_cells(self.handle, self.state(), _stream_ptr())
+
+    def eval_rates(self):
+        abi.sph_eval_rates(self.handle, self.state(), _stream_ptr())
+
+    def step(self, n_steps: int = 1):
+        abi.sph_step(self.handle, self.state(), n_steps, self.time.data_ptr(), _stream_ptr())
+
+    def assign(self, gen=None) -> torch.Tensor:
+        g = self.gen if gen is None else gen
+        offs = torch.zeros(self.K + 1, dtype=torch.int32, device=self.device)
+        abi.voronoi_assign(self.handle, self.state(), g.data_ptr(), self.K, self.unit_dim,
+                           self.t["unit"].data_ptr(), offs.data_ptr(), _stream_ptr())
+        return offs
+
+    def balance(self, gen=None, load=None, theta=0.25, sigma=0.5, gamma_b=1.0, beta_sh=0.45) -> torch.Tensor:
+        g = self.gen if gen is None else gen
+        bp = abi.sph_balance_params(theta, sigma, gamma_b, beta_sh)
+        shift = torch.zeros(1, dtype=torch.float64, device=self.device)
+        abi.voronoi_balance(self.handle, self.state(), g.data_ptr(), self.K, self.unit_dim,
+                            None if load is None else load.data_ptr(), bp, shift.data_ptr(), _stream_ptr())
+        return shift
+
+    def conservation(self) -> torch.Tensor:
+        out = torch.zeros(self.n_inst, 5, dtype=torch.float64, device=self.device)
+        abi.sph_conservation(self.handle, self.state(), out.data_ptr(), _stream_ptr())
+        return out
+
+    def unit_stats(self):
+        load = np.zeros(self.K)
+        adj = np.zeros((self.K, self.K), dtype=np.uint8)
+        abi.sph_unit_stats(self.handle, load.ctypes.data_as(C.POINTER(C.c_double)),
+                           adj.ctypes.data_as(C.POINTER(C.c_uint8)), _stream_ptr())
+        return load, adj
+
+    def cell_index(self):
+        cells = torch.zeros(self.n, dtype=torch.int32, device=self.device)
+        grid = np.zeros(8 * self.n_inst)
+        abi.sph_cell_index(self.handle, self.state(), cells.data_ptr(),
+                           grid.ctypes.data_as(C.POINTER(C.c_double)), _stream_ptr())
+        return cells.cpu().numpy(), grid.reshape(self.n_inst, 8)
+
+    def pair_list(self, cap: int | None = None):
+        """Interacting pairs (i < j, particle indices), sorted; also evaluates the rates."""
+        cap = cap or max(64, 64 * self.n)
+        pi = torch.zeros(cap, dtype=torch.int32, device=self.device)
+        pj = torch.zeros(cap, dtype=torch.int32, device=self.device)
+        cnt = abi.sph_pair_list(self.handle, self.state(), cap, pi.data_ptr(), pj.data_ptr(), _stream_ptr())
+        a, b = pi[:cnt].cpu().numpy(), pj[:cnt].cpu().numpy()
+        o = np.lexsort((b, a))
+        return a[o], b[o]
+
+    def profile(self, enable: bool = True):
+        abi.sph_profile(self.handle, enable)
+
+    def profile_read(self):
+        """(pair-kernel ms summed, pair launches, kernel launches) since the last call."""
+        return abi.sph_profile_read(self.handle)
+
+    def read_status(self) -> int:
+        return abi.sph_read_status(self.handle)
+
+    def pair_counts(self):
+        return abi.sph_pair_counts(self.handle, _stream_ptr())
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            torch.cuda.synchronize(self.device)
+            abi.sph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
