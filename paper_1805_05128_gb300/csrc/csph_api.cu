@@ -112,6 +112,7 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   int rc = check_state(nullptr, s, p->dim);
   if (rc) return rc;
   if (s->n < 1) return fail(nullptr, SPH_ERR_INVALID, "no particles");
+  // pair-list entries hold a slot index in 26 bits
   if (s->n >= (int64_t(1) << 26)) return fail(nullptr, SPH_ERR_CAPACITY, "at most 2^26 - 1 particles per handle");
   if (inst_offsets[0] != 0 || inst_offsets[n_instances] != s->n)
     return fail(nullptr, SPH_ERR_INVALID, "instance offsets must start at 0 and end at n");
@@ -218,8 +219,8 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   CKI(dalloc(&h->dmax_nbr, n));
   CKI(dalloc(&h->status, 1));
   CKI(cudaMemset(h->status, 0, sizeof(int)));
-  CKI(dalloc(&h->counters, 5));
-  CKI(cudaMemset(h->counters, 0, 5 * sizeof(unsigned long long)));
+  CKI(dalloc(&h->counters, 8));
+  CKI(cudaMemset(h->counters, 0, 8 * sizeof(unsigned long long)));
   h->scratch_bytes = (size_t)n * (18 * 8 + 8 + 4 + 4);
   CKI(cudaMalloc(&h->scratch, h->scratch_bytes));
 

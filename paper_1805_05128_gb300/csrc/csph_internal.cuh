@@ -14,7 +14,7 @@ namespace csph {
 
 constexpr int kBlock = 256;          // threads of the per-particle kernels
 constexpr int kPairBlock = 128;      // threads of the pair kernel
-constexpr int kListCap = 128;        // per-thread neighbour list capacity (16-bit entries, shared memory)
+constexpr int kListCap = 128;        // per-particle neighbour list capacity of the pair kernel (shared memory)
 constexpr double kCellMargin = 1.0 + 0x1p-20;  // relative safety margin of D^c
 
 // Per-instance cell mesh of eq. (Dcell) on the dense grid.
@@ -129,8 +129,8 @@ struct sph_handle {
   size_t prof_used = 0;
 
   int* status = nullptr;                    // device status word
-  unsigned long long* counters = nullptr;   // [5] full-list pairs, candidates, fp64 checks, assign FP64
-                                            // re-evaluations, listed pairs
+  unsigned long long* counters = nullptr;   // [8] full-list pairs, candidates, fp64 checks, assign FP64
+                                            // re-evaluations, listed pairs, pair-kernel work counter
 
   // renumbering scratch
   void* scratch = nullptr;

@@ -2,14 +2,12 @@
 // 3^dim cells of the block B_i, acoustic pair Riemann solver, and the
 // per-particle sums of eqs. (SPH:Conti), (SPH:Pulse), (SPH:Energy).
 //
-// One thread owns one slot i (slots are particles in cell order).  The
-// thread scans the candidate slots of its neighbour cells, keeps the
-// interacting ones in a private list in shared memory (16-bit entries stored
-// transposed so the lanes of a warp hit distinct banks), and evaluates the
-// fluxes over that list after the scan, so the flux arithmetic runs on dense,
-// converged lanes instead of under the ~17% acceptance of the candidate
-// test.  The list holds 128 entries; only a particle with more interacting
-// neighbours flushes it early.
+// A warp handles one home cell at a time, one lane per home particle (see
+// k_pair below): candidates are staged in shared memory row by row, tested
+// against every lane's particle, and the interacting ones are kept in a
+// per-lane list; the fluxes are evaluated over the lists, so the flux
+// arithmetic runs on converged lanes instead of under the ~17% acceptance
+// of the candidate test.
 //
 // Antisymmetry: every pair flux is evaluated in the canonical orientation
 // lo -> hi (lo = the smaller slot) with the same instruction sequence from
@@ -32,6 +30,8 @@ namespace {
 
 struct PairArgs {
   int64_t n;
+  const int64_t* total_cells_dev;
+  int64_t total_cells;   // read from total_cells_dev by the kernel
   int n_inst;
   const int64_t* inst_off;
   const GridInfo* grid;
@@ -55,6 +55,8 @@ struct PairArgs {
   uint32_t* adj_bits;
   int adj_words;  // 32-bit words per row
   unsigned long long* counters;
+  int* status;
+  unsigned long long* work_counter;   // next cell for the persistent warps (zeroed per launch)
   int collect_adj;   // record unit adjacency in this evaluation
   int32_t* pair_i;   // optional unordered pair output (particle indices, i < j)
   int32_t* pair_j;
@@ -106,6 +108,8 @@ __device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
+
+__device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
 // Exact FP64 interaction test on the global positions, operation order of the oracle.
 __device__ __forceinline__ bool exact_accept(const PairArgs& a, int dim, int64_t pi, int64_t pj) {
@@ -183,232 +187,295 @@ struct Pair {
   }
 };
 
+// One warp per home cell, lane l owning home particle start_c + chunk + l.
+// Candidate test, transposed: for each neighbour row (the 3 x-consecutive
+// cells at (oy, oz), contiguous in slot order) the warp takes 32 candidates
+// at a time, one per lane (position relative to the home cell origin in
+// mixed mode, global in FP64), and loops over the home particles, whose data
+// is broadcast from shared memory.  Each lane tests its candidate against
+// home particle hp; a ballot collects the accepted lanes and each writes its
+// entry at the next free positions of hp's list (prefix popcount), so the
+// 32 lanes are busy in every test and consecutive tests are independent.
+// A list entry is 16 bits: the neighbour-cell code (ox+1) + 3 (oy+1) +
+// 9 (oz+1) and the offset inside that cell.  Lists are rows of padded
+// stride in shared memory; after the scan (or when some list could overflow
+// during the next chunk) each lane evaluates the fluxes of its own row.
+constexpr int kWarps = kPairBlock / 32;
+constexpr int kRow = kListCap + 2;   // padded row stride (16-bit entries): lane rows fall in distinct banks
+
 template <bool MIXED, int DIM>
-__global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair(PairArgs a) {
+__global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair(PairArgs a) {
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
   using V4 = typename P::V4;
   using V2 = typename P::V2;
-  // Per-thread neighbour list, 16-bit entries: 5-bit neighbour-cell code
-  // (ox, oy, oz in {-1,0,1}^3) and 11-bit offset inside that cell.
-  __shared__ uint16_t list[kListCap * kPairBlock];
+  __shared__ uint16_t list[kWarps][32][kRow];               // [warp][home particle][entry]
+  __shared__ V4 home[kWarps][32];                            // home particles: x, y, z, kh d (mixed) or d (FP64)
+  __shared__ int32_t nb_start[kWarps][27];                   // start slot of each neighbour cell
 
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t total = *a.total_cells_dev;
   const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
   const V4* __restrict__ B = reinterpret_cast<const V4*>(a.B);
   const V2* __restrict__ C = reinterpret_cast<const V2*>(a.C);
+  // Persistent warps: each takes the next cell from a global counter, so the
+  // work spreads evenly whatever the mix of empty and crowded cells.
+  for (;;) {
+  int64_t cell_g = 0;
+  if (lane == 0) cell_g = (int64_t)atomicAdd(a.work_counter, 1ull);
+  cell_g = __shfl_sync(0xffffffffu, cell_g, 0);
+  if (cell_g >= total) break;
+  const int hs = a.cell_start[cell_g], he = a.cell_start[cell_g + 1];
+  if (hs == he) continue;                                    // empty cell (warp-uniform)
 
   int b = 0;
-  if (a.n_inst > 1) {  // instance of slot i: binary search of the slot offsets
+  if (a.n_inst > 1) {  // instance of this cell: binary search of the slot offsets
     int lo = 0, hi = a.n_inst;
     while (hi - lo > 1) {
       int mid = (lo + hi) >> 1;
-      if (a.inst_off[mid] <= i) lo = mid; else hi = mid;
+      if (a.inst_off[mid] <= hs) lo = mid; else hi = mid;
     }
     b = lo;
   }
   const GridInfo& g = a.grid[b];
   const int nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
-  const int64_t lc = (int64_t)a.slot_cell[i] - g.cell_off;
+  const int64_t lc = cell_g - g.cell_off;
   const int cx = (int)(lc % nx), cy = (int)((lc / nx) % ny), cz = (int)(lc / ((int64_t)nx * ny));
   const T dcs = MIXED ? (T)g.dc_f : T(0);
   const float band = MIXED ? 0x1p-12f * g.dc_f * g.dc_f : 0.f;
 
-  const V4 Ai = A[i];
-  const V4 Bi = B[i];
-  const V2 Ci = C[i];
-  const T khdi = MIXED ? (T)a.kh_f * Ai.w : T(0);
-  const int lane_base = threadIdx.x;
-  int cnt = 0;
-  unsigned nfull = 0, ncand = 0, nexact = 0;
-  T dmax = T(0);
-  const int ui = a.K > 0 ? a.slot_unit[i] : 0;
-  int last_adj = -1;
-  Kahan<T> s_rho, s_fx, s_fy, s_fz, s_q;
+  // starts of the 27 neighbour cells (index (ox+1) + 3 (oy+1) + 9 (oz+1)); -1 outside the mesh
+  if (lane < 27) {
+    const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
+    const int xx = cx + ox, yy = cy + oy, zz = cz + oz;
+    const bool in = xx >= 0 && xx < nx && yy >= 0 && yy < ny && zz >= 0 && zz < nz;
+    nb_start[warp][lane] = in ? a.cell_start[g.cell_off + xx + (int64_t)nx * (yy + (int64_t)ny * zz)] : -1;
+  }
 
-  // Flux of the interacting pair (i, j), evaluated in the canonical
-  // orientation lo -> hi, applied to i with i's sign.
-  auto pair_flux = [&](int64_t j, int ox, int oy, int oz) {
-    if (j == i) return;       // the scan keeps the self pair (r = 0); it has no flux
-    const V4 Aj = A[j];
-    const V4 Bj = B[j];
-    const V2 Cj = C[j];
-    const bool ilo = i < j;
-    T dx, dy, dz;
-    P::sep(ilo, Ai, Aj, ox * dcs, oy * dcs, oz * dcs, dx, dy, dz);
-    const T r2 = P::r2_of(dx, dy, dz);
-    dmax = Aj.w > dmax ? Aj.w : dmax;
-    if (!(r2 > T(0))) return;  // coincident particles: no direction, no flux
-    const T ir = rsqrt_(r2);
-    const T r = r2 * ir;
-    const T ex = dx * ir, ey = dy * ir, ez = dz * ir;
-    const V4& Bl = ilo ? Bi : Bj;
-    const V4& Bh = ilo ? Bj : Bi;
-    const V2& Cl = ilo ? Ci : Cj;
-    const V2& Ch = ilo ? Cj : Ci;
-    T vl = Bl.x * ex, vh = Bh.x * ex;
-    if (DIM >= 2) { vl += Bl.y * ey; vh += Bh.y * ey; }
-    if (DIM >= 3) { vl += Bl.z * ez; vh += Bh.z * ez; }
-    const T Zl = Cl.y, Zh = Ch.y, Pl = Cl.x, Ph = Ch.x;
-    const T zs = Zl + Zh;
-    T Ps, vs;
-    if (zs > T(0)) {
-      const T izs = rcp_(zs);
-      Ps = (Zh * Pl + Zl * Ph + Zl * Zh * (vl - vh)) * izs;
-      vs = (Zl * vl + Zh * vh + Pl - Ph) * izs;
-    } else {
-      Ps = T(0.5) * (Pl + Ph);
-      vs = T(0.5) * (vl + vh);
+  for (int h0 = hs; h0 < he; h0 += 32) {
+    const int i = h0 + lane;
+    const bool act = i < he;
+    const int nh = min(32, he - h0);
+    const int ii = act ? i : hs;
+    const V4 Ai = A[ii];
+    const T khdi = MIXED ? (T)a.kh_f * Ai.w : T(0);
+    {
+      V4 hv = Ai;
+      if (MIXED) hv.w = khdi;
+      home[warp][lane] = hv;
     }
-    const V4& Al = ilo ? Ai : Aj;
-    const V4& Ah = ilo ? Aj : Ai;
-    const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * (Al.w + Ah.w);
-    const T dW = MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij)
-                       : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij);
-    const T F = T(2) * (Bl.w * Bh.w) * Ps * dW;   // momentum flux lo <- hi along e
-    const T Q = F * vs;                            // energy flux
-    if (ilo) {
-      s_rho.add(Bj.w * (vl - vs) * (-dW));
-      s_fx.add(F * ex);
-      if (DIM >= 2) s_fy.add(F * ey);
-      if (DIM >= 3) s_fz.add(F * ez);
-      s_q.add(Q);
-    } else {
-      s_rho.add(Bj.w * (vs - vh) * (-dW));
-      s_fx.add(-(F * ex));
-      if (DIM >= 2) s_fy.add(-(F * ey));
-      if (DIM >= 3) s_fz.add(-(F * ez));
-      s_q.add(-Q);
-    }
-    if (a.pair_i) {
-      const int32_t pi = a.perm[i], pj = a.perm[j];
-      if (pi < pj) {
-        const unsigned long long q = atomicAdd(&a.counters[4], 1ull);
-        if ((int64_t)q < a.pair_cap) { a.pair_i[q] = pi; a.pair_j[q] = pj; }
+    __syncwarp();
+    int cnt = 0;
+    unsigned nfull = 0, ncand = 0, nexact = 0;
+    T dmax = T(0);
+    const int ui = a.K > 0 ? a.slot_unit[ii] : 0;
+    int last_adj = -1;
+    Kahan<T> s_rho, s_fx, s_fy, s_fz, s_q;
+    const V4 Bi = B[ii];
+    const V2 Ci = C[ii];
+
+    // Flux of the interacting pair (i, j), evaluated in the canonical
+    // orientation lo -> hi, applied to i with i's sign.
+    auto pair_flux = [&](int64_t j, int ox, int oy, int oz) {
+      if (j == i) return;       // the scan keeps the self pair (r = 0); it has no flux
+      const V4 Aj = A[j];
+      const V4 Bj = B[j];
+      const V2 Cj = C[j];
+      const bool ilo = i < j;
+      T dx, dy, dz;
+      P::sep(ilo, Ai, Aj, ox * dcs, oy * dcs, oz * dcs, dx, dy, dz);
+      const T r2 = P::r2_of(dx, dy, dz);
+      dmax = Aj.w > dmax ? Aj.w : dmax;
+      if (!(r2 > T(0))) return;  // coincident particles: no direction, no flux
+      const T ir = rsqrt_(r2);
+      const T r = r2 * ir;
+      const T ex = dx * ir, ey = dy * ir, ez = dz * ir;
+      const V4& Bl = ilo ? Bi : Bj;
+      const V4& Bh = ilo ? Bj : Bi;
+      const V2& Cl = ilo ? Ci : Cj;
+      const V2& Ch = ilo ? Cj : Ci;
+      T vl = Bl.x * ex, vh = Bh.x * ex;
+      if (DIM >= 2) { vl += Bl.y * ey; vh += Bh.y * ey; }
+      if (DIM >= 3) { vl += Bl.z * ez; vh += Bh.z * ez; }
+      const T Zl = Cl.y, Zh = Ch.y, Pl = Cl.x, Ph = Ch.x;
+      const T zs = Zl + Zh;
+      T Ps, vs;
+      if (zs > T(0)) {
+        const T izs = rcp_(zs);
+        Ps = (Zh * Pl + Zl * Ph + Zl * Zh * (vl - vh)) * izs;
+        vs = (Zl * vl + Zh * vh + Pl - Ph) * izs;
+      } else {
+        Ps = T(0.5) * (Pl + Ph);
+        vs = T(0.5) * (vl + vh);
       }
-    }
-    if (a.collect_adj) {
-      const int uj = a.slot_unit[j];
-      if (uj != ui && uj != last_adj) {
-        atomicOr(&a.adj_bits[ui * a.adj_words + (uj >> 5)], 1u << (uj & 31));
-        last_adj = uj;
+      const V4& Al = ilo ? Ai : Aj;
+      const V4& Ah = ilo ? Aj : Ai;
+      const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * (Al.w + Ah.w);
+      const T dW = MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij)
+                         : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij);
+      const T F = T(2) * (Bl.w * Bh.w) * Ps * dW;   // momentum flux lo <- hi along e
+      const T Q = F * vs;                            // energy flux
+      if (ilo) {
+        s_rho.add(Bj.w * (vl - vs) * (-dW));
+        s_fx.add(F * ex);
+        if (DIM >= 2) s_fy.add(F * ey);
+        if (DIM >= 3) s_fz.add(F * ez);
+        s_q.add(Q);
+      } else {
+        s_rho.add(Bj.w * (vs - vh) * (-dW));
+        s_fx.add(-(F * ex));
+        if (DIM >= 2) s_fy.add(-(F * ey));
+        if (DIM >= 3) s_fz.add(-(F * ez));
+        s_q.add(-Q);
       }
-    }
-  };
+      if (a.pair_i) {
+        const int32_t pi = a.perm[i], pj = a.perm[j];
+        if (pi < pj) {
+          const unsigned long long q = atomicAdd(&a.counters[4], 1ull);
+          if ((int64_t)q < a.pair_cap) { a.pair_i[q] = pi; a.pair_j[q] = pj; }
+        }
+      }
+      if (a.collect_adj) {
+        const int uj = a.slot_unit[j];
+        if (uj != ui && uj != last_adj) {
+          atomicOr(&a.adj_bits[ui * a.adj_words + (uj >> 5)], 1u << (uj & 31));
+          last_adj = uj;
+        }
+      }
+    };
 
-  auto rare = [&](int64_t j, int ox, int oy, int oz) {
-    ++nfull;
-    pair_flux(j, ox, oy, oz);
-  };
+    auto flush = [&]() {
+      nfull += (unsigned)cnt;
+      for (int k = 0; k < cnt; ++k) {
+        const unsigned ent = list[warp][lane][k];
+        const int code = ent >> 11;
+        const int oz = code / 9, oy = (code - 9 * oz) / 3, ox = code - 9 * oz - 3 * oy;
+        pair_flux((int64_t)nb_start[warp][code] + (ent & 2047u), ox - 1, oy - 1, oz - 1);
+      }
+      cnt = 0;
+    };
 
-  auto flush = [&]() {
-    nfull += (unsigned)cnt;
-    for (int k = 0; k < cnt; ++k) {
-      const unsigned ent = list[k * kPairBlock + lane_base];
-      const int code = ent >> 11;
-      const int ox = code % 3 - 1, oy = (code / 3) % 3 - 1, oz = code / 9 - 1;
-      const int64_t c = g.cell_off + (cx + ox) + (int64_t)nx * ((cy + oy) + (int64_t)ny * (cz + oz));
-      pair_flux((int64_t)a.cell_start[c] + (ent & 2047u), ox, oy, oz);
-    }
-    cnt = 0;
-  };
-
-  for (int oz = (DIM >= 3 ? -1 : 0); oz <= (DIM >= 3 ? 1 : 0); ++oz) {
-    const int zz = cz + oz;
-    if (zz < 0 || zz >= nz) continue;
-    for (int oy = (DIM >= 2 ? -1 : 0); oy <= (DIM >= 2 ? 1 : 0); ++oy) {
-      const int yy = cy + oy;
-      if (yy < 0 || yy >= ny) continue;
-      for (int ox = -1; ox <= 1; ++ox) {
-        const int xx = cx + ox;
-        if (xx < 0 || xx >= nx) continue;
-        const int64_t c = g.cell_off + xx + (int64_t)nx * (yy + (int64_t)ny * zz);
-        const int s0 = a.cell_start[c], s1 = a.cell_start[c + 1];
-        const int code = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
-        ncand += (unsigned)(s1 - s0);
-        // j's offset relative to i's cell origin minus i's offset: q + off_j
-        const T qx = ox * dcs - Ai.x, qy = oy * dcs - Ai.y, qz = oz * dcs - Ai.z;
-        for (int j = s0; j < s1; ++j) {
-          const V4 Aj = A[j];
-          bool acc;
-          if (MIXED) {
-            // Not the canonical orientation: the band makes the decision the
-            // exact FP64 one from either side, so the set stays symmetric.
-            const T dx = Aj.x + qx;
-            const T dy = DIM >= 2 ? Aj.y + qy : T(0);
-            const T dz = DIM >= 3 ? Aj.z + qz : T(0);
-            const T r2 = P::r2_of(dx, dy, dz);
-            const T R = fmaf((T)a.kh_f, Aj.w, khdi);
-            const T diff = fmaf(-R, R, r2);            // r^2 - R^2
-            if (fabsf(diff) > band) acc = diff < T(0);
-            else {
-              ++nexact;
-              acc = (j == i) || exact_accept(a, DIM, a.perm[i], a.perm[j]);
-            }
-          } else {
-            T dx, dy, dz;
-            P::sep(true, Ai, Aj, T(0), T(0), T(0), dx, dy, dz);
-            const T r2 = P::r2_of(dx, dy, dz);
-            const double R = __dmul_rn(a.kh, __dadd_rn(Ai.w, Aj.w));
-            acc = r2 < __dmul_rn(R, R);
+    for (int oz = (DIM >= 3 ? -1 : 0); oz <= (DIM >= 3 ? 1 : 0); ++oz) {
+      for (int oy = (DIM >= 2 ? -1 : 0); oy <= (DIM >= 2 ? 1 : 0); ++oy) {
+        const int rc = 3 * (oy + 1) + 9 * (oz + 1);     // index of the row's ox = -1 cell
+        const int s_m = nb_start[warp][rc], s_0 = nb_start[warp][rc + 1], s_p = nb_start[warp][rc + 2];
+        if (s_0 < 0) continue;                           // row outside the mesh
+        // contiguous slot range of the row: from the first existing cell to the end of the last
+        const int r0 = s_m >= 0 ? s_m : s_0;
+        const int xe = s_p >= 0 ? cx + 2 : cx + 1;       // one past the last existing cell in x
+        const int64_t rowc = g.cell_off + (int64_t)nx * ((cy + oy) + (int64_t)ny * (cz + oz));
+        const int r1 = a.cell_start[rowc + xe];
+        const int b1 = a.cell_start[rowc + cx + 1];      // end of the ox = 0 cell
+        ncand += act ? (unsigned)(r1 - r0) : 0u;
+        for (int base = r0; base < r1; base += 32) {
+          // a chunk adds at most 32 entries to a list: flush first if one could overflow
+          if (__any_sync(0xffffffffu, cnt > kListCap - 32)) {
+            if (act) flush();
           }
-          if (acc) {
-            const int off = j - s0;
-            if (off < 2048) {
-              list[cnt * kPairBlock + lane_base] = (uint16_t)((code << 11) | off);
-              if (++cnt == kListCap) flush();
+          const int j = base + lane;
+          const bool jv = j < r1;
+          V4 S = A[jv ? j : r0];
+          uint32_t ent = 0;
+          if (jv) {
+            const int ox = j < s_0 ? -1 : (j < b1 ? 0 : 1);
+            if (MIXED) { S.x += ox * dcs; S.y += oy * dcs; S.z += oz * dcs; }
+            const int off = j - (ox < 0 ? s_m : (ox == 0 ? s_0 : b1));
+            if (off > 2047) set_status(a.status, SPH_ERR_CAPACITY);   // cell over 2047 particles
+            ent = ((uint32_t)(rc + ox + 1) << 11) | (uint32_t)(off & 2047);
+          }
+#pragma unroll 4
+          for (int hp = 0; hp < nh; ++hp) {
+            const V4 H = home[warp][hp];
+            bool acc;
+            if (MIXED) {
+              const T dx = S.x - H.x;
+              const T dy = DIM >= 2 ? S.y - H.y : T(0);
+              const T dz = DIM >= 3 ? S.z - H.z : T(0);
+              const T r2 = P::r2_of(dx, dy, dz);
+              const T R = fmaf((T)a.kh_f, S.w, H.w);
+              const T diff = fmaf(-R, R, r2);          // r^2 - R^2
+              acc = diff < T(0);
+              if (fabsf(diff) <= band && jv) {          // too close to call in FP32: FP64 decides
+                ++nexact;
+                acc = (j == h0 + hp) || exact_accept(a, DIM, a.perm[h0 + hp], a.perm[j]);
+              }
             } else {
-              rare(j, ox, oy, oz);   // cell of more than 2047 particles: no list entry
+              T dx, dy, dz;
+              P::sep(true, H, S, T(0), T(0), T(0), dx, dy, dz);   // x_j - x_i, oracle order
+              const T r2 = P::r2_of(dx, dy, dz);
+              const double R = __dmul_rn(a.kh, __dadd_rn(H.w, S.w));
+              acc = r2 < __dmul_rn(R, R);
+            }
+            acc = acc && jv;
+            const unsigned mask = __ballot_sync(0xffffffffu, acc);
+            if (mask) {
+              const int c = __shfl_sync(0xffffffffu, cnt, hp);
+              if (acc) list[warp][hp][c + __popc(mask & lt)] = (uint16_t)ent;
+              if (lane == hp) cnt += __popc(mask);
             }
           }
         }
       }
     }
-  }
-  flush();
-  nfull -= 1;   // the self pair
+    if (act) flush();
 
-  const int64_t p = a.perm[i];
-  a.drho[p] = 2.0 * a.rho_slot[i] * (double)s_rho.s;
-  const double im = 1.0 / a.m[p];
-  a.ax[p] = (double)s_fx.s * im;
-  if (DIM >= 2) a.ay[p] = (double)s_fy.s * im;
-  if (DIM >= 3) a.az[p] = (double)s_fz.s * im;
-  a.dE[p] = (double)s_q.s * im;
-  a.dmax_nbr[p] = nfull ? (double)dmax : -1.0;
-
-  // counters and work-unit loads, aggregated per warp
-  const unsigned mask = __activemask();
-  const int leader = __ffs(mask) - 1;
-  const int lane = threadIdx.x & 31;
-  unsigned tf = __reduce_add_sync(mask, nfull);
-  unsigned tc = __reduce_add_sync(mask, ncand);
-  unsigned te = __reduce_add_sync(mask, nexact);
-  if (lane == leader) {
-    atomicAdd(&a.counters[0], (unsigned long long)tf);
-    atomicAdd(&a.counters[1], (unsigned long long)tc);
-    atomicAdd(&a.counters[2], (unsigned long long)te);
-  }
-  if (a.K > 0) {
-    const int u0 = __shfl_sync(mask, ui, leader);
-    if (__all_sync(mask, ui == u0)) {
-      if (lane == leader) atomicAdd(&a.load_acc[u0], (unsigned long long)tf);
-    } else {
-      atomicAdd(&a.load_acc[ui], (unsigned long long)nfull);
+    if (act) {
+      nfull -= 1;   // the self pair
+      const int64_t p = a.perm[i];
+      a.drho[p] = 2.0 * a.rho_slot[i] * (double)s_rho.s;
+      const double im = 1.0 / a.m[p];
+      a.ax[p] = (double)s_fx.s * im;
+      if (DIM >= 2) a.ay[p] = (double)s_fy.s * im;
+      if (DIM >= 3) a.az[p] = (double)s_fz.s * im;
+      a.dE[p] = (double)s_q.s * im;
+      a.dmax_nbr[p] = nfull ? (double)dmax : -1.0;
     }
+    // counters and work-unit loads, aggregated per warp
+    unsigned tf = __reduce_add_sync(0xffffffffu, act ? nfull : 0u);
+    unsigned tc = __reduce_add_sync(0xffffffffu, ncand);
+    unsigned te = __reduce_add_sync(0xffffffffu, nexact);
+    if (lane == 0) {
+      atomicAdd(&a.counters[0], (unsigned long long)tf);
+      atomicAdd(&a.counters[1], (unsigned long long)tc);
+      atomicAdd(&a.counters[2], (unsigned long long)te);
+    }
+    if (a.K > 0) {
+      const int u0 = __shfl_sync(0xffffffffu, ui, 0);
+      if (__all_sync(0xffffffffu, !act || ui == u0)) {
+        if (lane == 0) atomicAdd(&a.load_acc[u0], (unsigned long long)tf);
+      } else if (act) {
+        atomicAdd(&a.load_acc[ui], (unsigned long long)nfull);
+      }
+    }
+    __syncwarp();   // the home buffer is rewritten by the next chunk of home particles
   }
+  __syncwarp();     // the neighbour-start buffer is rewritten by the next cell
+  }
+}
+
+// Persistent grid: as many blocks as can be resident on the device at once.
+template <bool MIXED, int DIM>
+cudaError_t launch_one(const PairArgs& args, cudaStream_t st) {
+  static int grid = 0;
+  if (grid == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<MIXED, DIM>, kPairBlock, 0);
+    grid = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  k_pair<MIXED, DIM><<<grid, kPairBlock, 0, st>>>(args);
+  return cudaGetLastError();
 }
 
 template <bool MIXED>
 cudaError_t launch_dim(sph_handle* h, const PairArgs& args, cudaStream_t st) {
-  int g = grid_for(h->n, kPairBlock);
   switch (h->dp.dim) {
-    case 1: k_pair<MIXED, 1><<<g, kPairBlock, 0, st>>>(args); break;
-    case 2: k_pair<MIXED, 2><<<g, kPairBlock, 0, st>>>(args); break;
-    default: k_pair<MIXED, 3><<<g, kPairBlock, 0, st>>>(args); break;
+    case 1: return launch_one<MIXED, 1>(args, st);
+    case 2: return launch_one<MIXED, 2>(args, st);
+    default: return launch_one<MIXED, 3>(args, st);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace
@@ -416,6 +483,8 @@ cudaError_t launch_dim(sph_handle* h, const PairArgs& args, cudaStream_t st) {
 cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st) {
   PairArgs a;
   a.n = h->n;
+  a.total_cells_dev = h->total_cells;
+  a.total_cells = 0;
   a.n_inst = h->n_inst;
   a.inst_off = h->inst_off;
   a.grid = h->grid;
@@ -435,6 +504,8 @@ cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st) {
   a.adj_bits = h->adj_bits;
   a.adj_words = (h->K + 31) / 32;
   a.counters = h->counters;
+  a.work_counter = &h->counters[5];
+  a.status = h->status;
   a.collect_adj = (h->K > 0 && h->collect_adj) ? 1 : 0;
   a.pair_i = h->pair_out_i;
   a.pair_j = h->pair_out_j;
@@ -448,7 +519,7 @@ cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st) {
   a.kernel = h->dp.kernel;
   cudaError_t e = cudaMemsetAsync(h->counters, 0, 3 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(&h->counters[4], 0, sizeof(unsigned long long), st);
+  e = cudaMemsetAsync(&h->counters[4], 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (h->profiling) {
