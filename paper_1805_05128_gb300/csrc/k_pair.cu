@@ -9,10 +9,8 @@
 // arithmetic runs on converged lanes instead of under the ~17% acceptance
 // of the candidate test.
 //
-// Antisymmetry: every pair flux is evaluated in the canonical orientation
-// lo -> hi (lo = the smaller slot) with the same instruction sequence from
-// both sides, so the momentum flux F_ij and energy flux Q_ij that i and j
-// apply are bitwise negatives of each other.
+// Antisymmetry: the momentum flux F_ij e^R and energy flux Q_ij that i and
+// j apply are bitwise negatives of each other (see pair_flux).
 //
 // Mixed precision: the candidate test and the flux run in FP32 on offsets
 // from each particle's own cell origin (FP32 keeps ~7 digits of a cell edge,
@@ -111,6 +109,17 @@ __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
 
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
+// Uncontracted arithmetic for the expressions whose exchange symmetry must
+// hold bit for bit (the compiler may not fuse these into FMAs).
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Exact FP64 interaction test on the global positions, operation order of the oracle.
 __device__ __forceinline__ bool exact_accept(const PairArgs& a, int dim, int64_t pi, int64_t pj) {
   double dx = __dsub_rn(a.x[pj], a.x[pi]);
@@ -133,10 +142,10 @@ __device__ __forceinline__ T dw_fast(int kernel, T kappa, T r, T h) {
     if (DIM == 1) norm = T(2.0 / 3.0) * ih * ih;
     else if (DIM == 2) norm = T(10.0 / (7.0 * 3.14159265358979323846)) * ih * ih * ih;
     else norm = T(1.0 / 3.14159265358979323846) * (ih * ih) * (ih * ih);
-    T f;
-    if (q < T(1)) f = q * (T(2.25) * q - T(3));
-    else if (q < T(2)) { const T t = T(2) - q; f = T(-0.75) * t * t; }
-    else f = T(0);
+    const T t = T(2) - q;
+    const T f_in = q * (T(2.25) * q - T(3));
+    const T f_out = T(-0.75) * t * t;
+    const T f = q < T(1) ? f_in : (q < T(2) ? f_out : T(0));   // selects, no divergence
     return norm * f;
   } else {
     const T iH = rcp_(kappa * h);
@@ -275,60 +284,59 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair(PairArgs a) 
     const V4 Bi = B[ii];
     const V2 Ci = C[ii];
 
-    // Flux of the interacting pair (i, j), evaluated in the canonical
-    // orientation lo -> hi, applied to i with i's sign.
+    // Flux of the interacting pair (i, j) from i's side.  Every quantity
+    // that j computes for the same pair is the exact negative (e^R, v^R, v*,
+    // momentum and energy fluxes) or the exact same value (r, P*, h_ij, W'):
+    // dx = (off_j - off_i) + shift is the rounded negative of j's
+    // (off_i - off_j) - shift, IEEE rounding is sign-symmetric, and the sums
+    // that mix i and j are written with uncontracted operations in an order
+    // that is symmetric under the exchange.  So the applied fluxes are
+    // antisymmetric bit for bit and momentum and energy are conserved by the
+    // pair sums up to the per-particle summation.
     auto pair_flux = [&](int64_t j, int ox, int oy, int oz) {
       if (j == i) return;       // the scan keeps the self pair (r = 0); it has no flux
       const V4 Aj = A[j];
       const V4 Bj = B[j];
       const V2 Cj = C[j];
-      const bool ilo = i < j;
       T dx, dy, dz;
-      P::sep(ilo, Ai, Aj, ox * dcs, oy * dcs, oz * dcs, dx, dy, dz);
+      if (MIXED) {
+        dx = (Aj.x - Ai.x) + ox * dcs;
+        dy = DIM >= 2 ? (Aj.y - Ai.y) + oy * dcs : T(0);
+        dz = DIM >= 3 ? (Aj.z - Ai.z) + oz * dcs : T(0);
+      } else {
+        dx = __dsub_rn(Aj.x, Ai.x);
+        dy = DIM >= 2 ? __dsub_rn(Aj.y, Ai.y) : 0.0;
+        dz = DIM >= 3 ? __dsub_rn(Aj.z, Ai.z) : 0.0;
+      }
       const T r2 = P::r2_of(dx, dy, dz);
       dmax = Aj.w > dmax ? Aj.w : dmax;
       if (!(r2 > T(0))) return;  // coincident particles: no direction, no flux
       const T ir = rsqrt_(r2);
       const T r = r2 * ir;
       const T ex = dx * ir, ey = dy * ir, ez = dz * ir;
-      const V4& Bl = ilo ? Bi : Bj;
-      const V4& Bh = ilo ? Bj : Bi;
-      const V2& Cl = ilo ? Ci : Cj;
-      const V2& Ch = ilo ? Cj : Ci;
-      T vl = Bl.x * ex, vh = Bh.x * ex;
-      if (DIM >= 2) { vl += Bl.y * ey; vh += Bh.y * ey; }
-      if (DIM >= 3) { vl += Bl.z * ez; vh += Bh.z * ez; }
-      const T Zl = Cl.y, Zh = Ch.y, Pl = Cl.x, Ph = Ch.x;
-      const T zs = Zl + Zh;
+      T vi = Bi.x * ex, vj = Bj.x * ex;
+      if (DIM >= 2) { vi = fma_(Bi.y, ey, vi); vj = fma_(Bj.y, ey, vj); }
+      if (DIM >= 3) { vi = fma_(Bi.z, ez, vi); vj = fma_(Bj.z, ez, vj); }
+      const T Zi = Ci.y, Zj = Cj.y, Pi = Ci.x, Pj = Cj.x;
+      const T zs = add_(Zi, Zj);
       T Ps, vs;
       if (zs > T(0)) {
         const T izs = rcp_(zs);
-        Ps = (Zh * Pl + Zl * Ph + Zl * Zh * (vl - vh)) * izs;
-        vs = (Zl * vl + Zh * vh + Pl - Ph) * izs;
+        Ps = mul_(add_(add_(mul_(Zj, Pi), mul_(Zi, Pj)), mul_(mul_(Zi, Zj), sub_(vi, vj))), izs);
+        vs = mul_(add_(add_(mul_(Zi, vi), mul_(Zj, vj)), sub_(Pi, Pj)), izs);
       } else {
-        Ps = T(0.5) * (Pl + Ph);
-        vs = T(0.5) * (vl + vh);
+        Ps = mul_(T(0.5), add_(Pi, Pj));
+        vs = mul_(T(0.5), add_(vi, vj));
       }
-      const V4& Al = ilo ? Ai : Aj;
-      const V4& Ah = ilo ? Aj : Ai;
-      const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * (Al.w + Ah.w);
+      const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * add_(Ai.w, Aj.w);
       const T dW = MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij)
                          : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij);
-      const T F = T(2) * (Bl.w * Bh.w) * Ps * dW;   // momentum flux lo <- hi along e
-      const T Q = F * vs;                            // energy flux
-      if (ilo) {
-        s_rho.add(Bj.w * (vl - vs) * (-dW));
-        s_fx.add(F * ex);
-        if (DIM >= 2) s_fy.add(F * ey);
-        if (DIM >= 3) s_fz.add(F * ez);
-        s_q.add(Q);
-      } else {
-        s_rho.add(Bj.w * (vs - vh) * (-dW));
-        s_fx.add(-(F * ex));
-        if (DIM >= 2) s_fy.add(-(F * ey));
-        if (DIM >= 3) s_fz.add(-(F * ez));
-        s_q.add(-Q);
-      }
+      const T F = mul_(mul_(mul_(T(2), mul_(Bi.w, Bj.w)), Ps), dW);   // momentum flux along e
+      s_rho.add(Bj.w * (vi - vs) * (-dW));
+      s_fx.add(mul_(F, ex));
+      if (DIM >= 2) s_fy.add(mul_(F, ey));
+      if (DIM >= 3) s_fz.add(mul_(F, ez));
+      s_q.add(mul_(F, vs));
       if (a.pair_i) {
         const int32_t pi = a.perm[i], pj = a.perm[j];
         if (pi < pj) {
