@@ -208,6 +208,34 @@ int sph_cell_index(sph_handle* h, const sph_state* s, int32_t* cell_out, double*
 int sph_pair_list(sph_handle* h, sph_state* s, int64_t cap, int32_t* pi_out, int32_t* pj_out,
                   int64_t* count_out, void* stream);
 
+/* Allocation-free voronoi_assign, for callers that cannot allocate device
+ * memory: code running while a stream is captured into a CUDA graph, code
+ * whose device memory all belongs to another allocator or a fixed arena, or
+ * a host loop that must not call cudaMalloc.  No handle is needed and
+ * nothing is allocated: the scratch (per-unit counts and their scan) lives
+ * in one file-scope device array of about 8.4 MB that every device which
+ * loads the library keeps until the process exits.  No counterpart in the
+ * paper; the result is that of voronoi_assign (eq. VoronoiDefinition, ties
+ * to the smaller index) on the same inputs.
+ *   x, y, z      device positions, n doubles each (y NULL for dim 1, z NULL
+ *                for dim <= 2)
+ *   gen          device, K x dim doubles
+ *   unit_out     device, n int32: the owning unit of each particle
+ *   unit_offsets device, K+1 int32, or NULL: start of each unit in unit_list
+ *   unit_list    device, n int32, or NULL: particle indices grouped by unit,
+ *                ascending inside each unit
+ * Limits: 1 <= n <= 4,194,304 and 1 <= K <= 256 (else SPH_ERR_CAPACITY, or
+ * SPH_ERR_INVALID for n < 1, K < 1, a bad dim or a missing pointer; see
+ * sph_last_error(NULL)).  The array is shared by all calls on a device:
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it; each call resets what it needs, so consecutive calls on one
+ * stream are independent.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture. */
+int voronoi_assign_static(int64_t n, const double* x, const double* y, const double* z, const double* gen,
+                          int K, int dim, int32_t* unit_out, int32_t* unit_offsets, int32_t* unit_list,
+                          void* stream);
+
 /* Measurement support.  sph_profile(h, 1) starts recording CUDA events
  * around every launch of the pair kernel on the caller's stream and counts
  * every kernel launch of the library; sph_profile(h, 0) stops.  Resets the

@@ -24,7 +24,8 @@ ERROR_NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID", 2: "SPH_ERR_CAPACITY", 3: "SPH
 # every symbol include/csph.h declares
 EXPORTS = ("sph_init", "sph_build_cells", "sph_eval_rates", "sph_step", "voronoi_assign", "voronoi_balance",
            "sph_conservation", "sph_unit_stats", "sph_read_status", "sph_last_error", "sph_pair_counts",
-           "sph_cell_index", "sph_pair_list", "sph_profile", "sph_profile_read", "sph_destroy")
+           "sph_cell_index", "sph_pair_list", "voronoi_assign_static", "sph_profile", "sph_profile_read",
+           "sph_destroy")
 
 
 class sph_material(C.Structure):
@@ -85,6 +86,7 @@ def lib() -> C.CDLL:
     L.sph_pair_counts.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64), vp]
     L.sph_cell_index.argtypes = [vp, C.POINTER(sph_state), vp, C.POINTER(C.c_double), vp]
     L.sph_pair_list.argtypes = [vp, C.POINTER(sph_state), i64, vp, vp, C.POINTER(C.c_int64), vp]
+    L.voronoi_assign_static.argtypes = [i64, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp]
     L.sph_profile.argtypes = [vp, i32]
     L.sph_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.sph_destroy.argtypes = [vp]
@@ -172,6 +174,15 @@ def sph_pair_list(h, state, cap, pi_ptr, pj_ptr, stream) -> int:
     check(lib().sph_pair_list(h, C.byref(state), cap, C.c_void_p(pi_ptr), C.c_void_p(pj_ptr), C.byref(cnt),
                               C.c_void_p(stream)), h)
     return cnt.value
+
+
+def voronoi_assign_static(n, x_ptr, y_ptr, z_ptr, gen_ptr, K, dim, unit_out_ptr, unit_offsets_ptr,
+                          unit_list_ptr, stream):
+    """Allocation-free voronoi_assign (no handle); see include/csph.h."""
+    check(lib().voronoi_assign_static(n, C.c_void_p(x_ptr), C.c_void_p(y_ptr), C.c_void_p(z_ptr),
+                                      C.c_void_p(gen_ptr), K, dim, C.c_void_p(unit_out_ptr),
+                                      C.c_void_p(unit_offsets_ptr), C.c_void_p(unit_list_ptr),
+                                      C.c_void_p(stream)))
 
 
 def sph_profile(h, enable: bool):

@@ -90,6 +90,8 @@ int assign_impl(sph_handle* h, const sph_state* s, const double* gen, int K, int
 
 }  // namespace
 
+void csph::set_global_error(const std::string& msg) { g_init_error = msg; }
+
 extern "C" {
 
 int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64_t* inst_offsets,

@@ -208,6 +208,9 @@ __device__ __forceinline__ T kernel_dw(int kernel, T kappa, T r, T h) {
 // --------------------------------------------------------------------------
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
 
+// Message reported by sph_last_error(NULL) (entry points without a handle).
+void set_global_error(const std::string& msg);
+
 // Launchers (defined in k_step.cu, k_pair.cu, k_vd3.cu).  They enqueue on
 // `st` and return the launch status.
 cudaError_t launch_derive_dt(sph_handle* h, const sph_state& s, bool with_bbox, cudaStream_t st);

@@ -3,6 +3,8 @@
 // stable per-unit particle lists, per-unit statistics (centroid, D^sh) and
 // the balancing update of the generators.
 #include <cfloat>
+#include <mutex>
+#include <string>
 
 #include "csph_internal.cuh"
 
@@ -370,3 +372,106 @@ cudaError_t launch_balance(sph_handle* h, const sph_state& s, double* gen, int K
 }
 
 }  // namespace csph
+
+// ---------------------------------------------------------------------------
+// Allocation-free Voronoi assignment for callers that cannot allocate device
+// memory (no counterpart in the paper).  Code that runs while a CUDA stream
+// is being captured into a graph, code whose device memory is all owned by
+// another pool (a framework's caching allocator, a fixed arena), or a host
+// loop that must not call cudaMalloc, cannot create a handle, whose
+// workspace is allocated in sph_init.  This entry point takes only the
+// caller's positions, generators and output arrays and keeps its scratch
+// (per-unit counts, their scan and a counter) in one file-scope device array
+// of fixed size, so it allocates nothing.
+// ---------------------------------------------------------------------------
+namespace csph {
+namespace {
+
+constexpr int64_t kStaticMaxN = int64_t(1) << 22;                                     // 4,194,304 particles
+constexpr int64_t kStaticMaxCounts = int64_t(SPH_MAX_UNITS) * (kStaticMaxN / kUnitBlock);   // 1,048,576
+constexpr int64_t kStaticSums = kStaticMaxCounts / 1024 + 2;
+// int32 layout: counts | starts (+1) | scan sums | unit offsets (K+1) | pad to 8 bytes | total, exact counter
+constexpr int64_t kOffCounts = 0;
+constexpr int64_t kOffStarts = kOffCounts + kStaticMaxCounts;
+constexpr int64_t kOffSums = kOffStarts + kStaticMaxCounts + 1;
+constexpr int64_t kOffUnitOff = kOffSums + kStaticSums;
+constexpr int64_t kOffTail = ((kOffUnitOff + SPH_MAX_UNITS + 1) + 1) & ~int64_t(1);  // even: 8-byte aligned
+constexpr int64_t kStaticWords = kOffTail + 4;                                        // int64 total + uint64 counter
+
+// The scratch shared by every call on a device (about 8.4 MB, held until exit).
+static __device__ __align__(256) int32_t g_assign_scratch[kStaticWords];
+
+__global__ void k_static_reset(int64_t* total, unsigned long long* exact, int64_t tot) {
+  *total = tot;
+  *exact = 0ull;
+}
+
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+int32_t* g_static_addr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device, resolved once per
+// device with that device current.
+cudaError_t static_scratch(int32_t** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_assign_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_addr[dev] = reinterpret_cast<int32_t*>(p);
+  }
+  *out = g_static_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace csph
+
+extern "C" int voronoi_assign_static(int64_t n, const double* x, const double* y, const double* z,
+                                     const double* gen, int K, int dim, int32_t* unit_out,
+                                     int32_t* unit_offsets, int32_t* unit_list, void* stream) {
+  using namespace csph;
+  if (n < 1 || K < 1 || dim < 1 || dim > 3 || !x || !gen || !unit_out || (dim >= 2 && !y) || (dim >= 3 && !z)) {
+    set_global_error("voronoi_assign_static: need n >= 1, 1 <= K, dim in 1..3 and non-NULL x (y, z for dim >= 2, 3), "
+                     "gen and unit_out");
+    return SPH_ERR_INVALID;
+  }
+  if (n > kStaticMaxN || K > SPH_MAX_UNITS) {
+    set_global_error("voronoi_assign_static: at most 4,194,304 particles and 256 units (fixed scratch size)");
+    return SPH_ERR_CAPACITY;
+  }
+  int32_t* scr = nullptr;
+  cudaError_t e = static_scratch(&scr);
+  if (e != cudaSuccess) {
+    set_global_error(std::string("voronoi_assign_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    return SPH_ERR_CUDA;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nb = grid_for(n, kUnitBlock);
+  const int64_t tot = (int64_t)K * nb;
+  int32_t* counts = scr + kOffCounts;
+  int32_t* starts = scr + kOffStarts;
+  int32_t* sums = scr + kOffSums;
+  int64_t* total = reinterpret_cast<int64_t*>(scr + kOffTail);
+  unsigned long long* exact = reinterpret_cast<unsigned long long*>(scr + kOffTail + 2);
+  const size_t smem = sizeof(int) * 32 * K;
+  k_static_reset<<<1, 1, 0, st>>>(total, exact, tot);   // the previous call left its values here
+  k_assign<<<grid_for(n, kBlock), kBlock, 0, st>>>(n, dim, x, y, z, gen, K, unit_out, exact);
+  k_unit_hist<<<nb, kUnitBlock, smem, st>>>(unit_out, n, K, nb, counts);   // writes every count
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_exclusive_scan(counts, total, sums, starts, n, tot, st);
+  if (e == cudaSuccess && unit_list) k_unit_scatter<<<nb, kUnitBlock, smem, st>>>(unit_out, n, K, nb, starts, unit_list);
+  if (e == cudaSuccess)
+    k_unit_offsets<<<grid_for(K + 1, kBlock), kBlock, 0, st>>>(starts, K, nb, n,
+                                                             unit_offsets ? unit_offsets : scr + kOffUnitOff, nullptr);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_global_error(std::string("voronoi_assign_static: ") + cudaGetErrorString(e));
+    return SPH_ERR_CUDA;
+  }
+  return SPH_OK;
+}
