@@ -237,15 +237,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     flops = FLOP_PAIR * half_pairs + FLOP_TEST * candidates / 2.0
     achieved = flops / (pair_ms_avg * 1e-3) / 1e12
     peak = fp32_peak_tflops()
-    traffic = None
-    prof_path = os.path.join(ROOT, "profiles", "pair_traffic.json")
-    if os.path.exists(prof_path):
-        try:
-            pt = json.load(open(prof_path))
-            if pt.get("precision") == args.precision and pt.get("kernel_rev") == kernel_rev():
-                traffic = pt["bytes_per_launch_full"]
-        except (ValueError, KeyError):
-            traffic = None
+    traffic = pair_traffic_bytes(args) if args.workload == WORKLOAD else None
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
@@ -269,6 +261,22 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                                "sample": f"plain FP64 C oracle, single thread, full {cn}-particle plate impact, "
                                          f"{args.cpu_steps} steps after one rate evaluation ({csec:.1f} s)"}
     return out
+
+
+def pair_traffic_bytes(args):
+    """DRAM bytes per pair-kernel launch of the benchmark workload, from the
+    committed ncu summary; None unless that summary was taken on the current
+    k_pair.cu source and the mixed path."""
+    import re
+    path = os.path.join(ROOT, "profiles", "k_pair_plate_impact_387k.md")
+    if args.precision != "mixed" or not os.path.exists(path):
+        return None
+    text = open(path).read()
+    sha = re.search(r"kernel_sha1:\s*([0-9a-f]+)", text)
+    val = re.search(r"traffic_bytes_per_launch_1125k:\s*([0-9]+)", text)
+    if not sha or not val or sha.group(1) != kernel_rev():
+        return None
+    return int(val.group(1))
 
 
 def kernel_rev() -> str:
