@@ -343,3 +343,103 @@ def from_problem(prob, cell_cap: int = 1 << 26):
     p = Params(dim=prob.dim, kernel=_KERNEL_IDS[prob.kernel], kappa=prob.kappa, eta=prob.eta,
                cfl=prob.cfl, cell_beta=0.0, cell_cap=cell_cap, materials=mats)
     return p, State(prob.dim, prob.arrays, prob.mat)
+
+
+# --------------------------------------------------------------------------
+# Reverse mode (hand-derived adjoint, pair set and dt held fixed)
+# --------------------------------------------------------------------------
+def _bind_adjoint():
+    L = lib()
+    if getattr(L, "_adj_bound", False):
+        return L
+    L.orc_rates_vjp.restype = C.c_int
+    L.orc_rates_vjp.argtypes = [C.POINTER(_Params), C.POINTER(_State), C.c_int64, _IP, _IP,
+                                _DP, _DP, _DP, _DP, _DP, _DP, _DP, _DP]
+    L.orc_step_replay.restype = C.c_int
+    L.orc_step_replay.argtypes = [C.POINTER(_Params), C.POINTER(_State), C.c_int, C.c_int, _DP]
+    L.orc_step_vjp.restype = C.c_int
+    L.orc_step_vjp.argtypes = [C.POINTER(_Params), C.POINTER(_State), C.c_double] + [_DP] * 8
+    L._adj_bound = True
+    return L
+
+
+def rates_vjp(p: Params, s: State, pi, pj, ga, gr, gE):
+    """dL/d(x, v, rho, E, c0, gamma) for L = <ga, a> + <gr, drho> + <gE, dE> of
+    the rates over the pair list (s carries d, P, c from derive)."""
+    L = _bind_adjoint()
+    n = s.n
+    ga = np.ascontiguousarray(ga, dtype=np.float64).reshape(n, 3)
+    out = dict(bx=np.zeros((n, 3)), bv=np.zeros((n, 3)), brho=np.zeros(n), bE=np.zeros(n), bpar=np.zeros(2))
+    pi = np.ascontiguousarray(pi, dtype=np.int32)
+    pj = np.ascontiguousarray(pj, dtype=np.int32)
+    pc, sc = p.cs(), s.cs()
+    gr = np.ascontiguousarray(gr, dtype=np.float64)
+    gE = np.ascontiguousarray(gE, dtype=np.float64)
+    rc = L.orc_rates_vjp(C.byref(pc), C.byref(sc), len(pi), pi.ctypes.data_as(_IP), pj.ctypes.data_as(_IP),
+                         _dp(ga), _dp(gr), _dp(gE), _dp(out["bx"]), _dp(out["bv"]), _dp(out["brho"]),
+                         _dp(out["bE"]), _dp(out["bpar"]))
+    if rc != 0:
+        raise ValueError("oracle rates VJP supports the cubic kernel with ideal/stiffened gas only")
+    return out
+
+
+def step_replay(p: Params, s: State, dts, rates_valid: bool = True):
+    L = _bind_adjoint()
+    dts = np.ascontiguousarray(dts, dtype=np.float64)
+    pc, sc = p.cs(), s.cs()
+    if L.orc_step_replay(C.byref(pc), C.byref(sc), len(dts), int(rates_valid), _dp(dts)) != 0:
+        raise ValueError("oracle replay failed")
+
+
+ADJ_KEYS = ("x", "v", "rho", "E", "a", "drho", "dE")
+
+
+def zero_adjoint(n: int) -> dict:
+    return dict(x=np.zeros((n, 3)), v=np.zeros((n, 3)), rho=np.zeros(n), E=np.zeros(n),
+                a=np.zeros((n, 3)), drho=np.zeros(n), dE=np.zeros(n))
+
+
+def step_vjp(p: Params, s: State, dt: float, y: dict, bpar) -> None:
+    """In place: y (adjoint of the state after one step from s with this dt)
+    becomes the adjoint of s; bpar (2) accumulates dL/d(c0, gamma)."""
+    L = _bind_adjoint()
+    for k in ADJ_KEYS:
+        y[k] = np.ascontiguousarray(y[k], dtype=np.float64)
+    pc, sc = p.cs(), s.cs()
+    rc = L.orc_step_vjp(C.byref(pc), C.byref(sc), dt, _dp(y["x"]), _dp(y["v"]), _dp(y["rho"]), _dp(y["E"]),
+                        _dp(y["a"]), _dp(y["drho"]), _dp(y["dE"]), _dp(bpar))
+    if rc != 0:
+        raise ValueError("oracle step VJP failed")
+
+
+def state_vectors(s: State):
+    """(n, 3) views of positions, velocities and accelerations (zeros for unused axes)."""
+    n = s.n
+    z = np.zeros(n)
+    pos = np.stack([s.x, s.y if s.y is not None else z, s.z if s.z is not None else z], axis=1)
+    vel = np.stack([s.vx, s.vy if s.vy is not None else z, s.vz if s.vz is not None else z], axis=1)
+    acc = np.stack([s.ax, s.ay if s.ay is not None else z, s.az if s.az is not None else z], axis=1)
+    return pos, vel, acc
+
+
+def trajectory_vjp(p: Params, s0: State, dts, y_final: dict):
+    """Adjoint of a whole run from s0 with the recorded dt sequence: returns
+    (adjoint of the initial state before its first rate evaluation, i.e. of
+    x, v, rho, E, and dL/d(c0, gamma) through the EOS).  Stores every state."""
+    states = []
+    s = s0.copy()
+    eval_rates(p, s)
+    for dt in dts:
+        states.append(s.copy())
+        step_replay(p, s, [dt], rates_valid=True)
+    y = {k: np.array(v, dtype=np.float64, copy=True) for k, v in y_final.items()}
+    bpar = np.zeros(2)
+    for st, dt in zip(reversed(states), reversed(list(dts))):
+        step_vjp(p, st, dt, y, bpar)
+    # the first held rates were evaluated at s0: push their adjoint into s0
+    s = s0.copy()
+    derive(p, s)
+    pi, pj = pairs(p, s)
+    r = rates_vjp(p, s, pi, pj, y["a"], y["drho"], y["dE"])
+    out = dict(x=y["x"] + r["bx"], v=y["v"] + r["bv"], rho=y["rho"] + r["brho"], E=y["E"] + r["bE"])
+    return out, bpar + r["bpar"]

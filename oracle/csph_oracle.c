@@ -629,3 +629,283 @@ double orc_balance(int K, int gdim, double* gen, const double* load, const uint8
   free(newg);
   return shift;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reverse mode (adjoint) of the CSPH step, written by hand from the
+ * formulas above.  Readings: the pair set and the dt sequence of the
+ * forward run are held fixed (dt is a stop-gradient); the cubic-spline W'
+ * and W'' vanish at q = 2, so the gradient is continuous when pairs enter or
+ * leave.  Supported closures: cubic-spline kernel; ideal and stiffened gas,
+ * the parameters being (c0, gamma) of material 0 with P_inf = rho0 c0^2 / gamma
+ * for the stiffened gas.                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* cubic spline: W' = s h^-(D+1) g(q), dW'/dr = s h^-(D+2) g'(q),
+ * dW'/dh = s h^-(D+2) (-(D+1) g(q) - q g'(q)), s = 2/3, 10/(7 pi), 1/pi */
+static void cubic_dw_derivs(int dim, double r, double h, double* dw, double* dwdr, double* dwdh) {
+  double s = dim == 1 ? 2.0 / 3.0 : (dim == 2 ? 10.0 / (7.0 * ORC_PI) : 1.0 / ORC_PI);
+  double q = r / h, g, gp;
+  if (q < 1.0) { g = -3.0 * q + 2.25 * q * q; gp = -3.0 + 4.5 * q; }
+  else if (q < 2.0) { double t = 2.0 - q; g = -0.75 * t * t; gp = 1.5 * t; }
+  else { g = 0.0; gp = 0.0; }
+  double hp1 = pow(h, (double)(dim + 1));
+  *dw = s * g / hp1;
+  *dwdr = s * gp / (hp1 * h);
+  *dwdh = s * (-(double)(dim + 1) * g - q * gp) / (hp1 * h);
+}
+
+/* VJP of orc_rates at the state s (with d, P, c from orc_derive) for the pair
+ * list: given ga (3n, dL/da), gr (n, dL/d drho/dt), gE (n, dL/d dE/dt),
+ * ADD dL/dx (bx, 3n), dL/dv (bv, 3n), dL/drho (brho), dL/dE (bE) and
+ * dL/d(c0, gamma) of material 0 (bpar[2]).  Arrays of dimension 3 use the
+ * layout [3*i + a]. */
+int orc_rates_vjp(const orc_params* p, const orc_state* s, int64_t npairs, const int32_t* pi, const int32_t* pj,
+                  const double* ga, const double* gr, const double* gE,
+                  double* bx, double* bv, double* brho, double* bE, double* bpar) {
+  int64_t n = s->n;
+  int dim = p->dim;
+  if (p->kernel != ORC_KERNEL_CUBIC) return -1;
+  for (int k = 0; k < p->n_mat; ++k)
+    if (p->mat[k].eos != ORC_EOS_IDEAL && p->mat[k].eos != ORC_EOS_STIFFENED) return -2;
+  double* bP = calloc((size_t)n, sizeof(double));
+  double* bZ = calloc((size_t)n, sizeof(double));
+  double* bV = calloc((size_t)n, sizeof(double));
+  double* bd = calloc((size_t)n, sizeof(double));
+  const double* X[3] = {s->x, s->y, s->z};
+  const double* Vv[3] = {s->vx, s->vy, s->vz};
+  for (int64_t k = 0; k < npairs; ++k) {
+    int64_t i = pi[k], j = pj[k];
+    double dxv[3] = {0, 0, 0}, e[3] = {0, 0, 0}, vi[3] = {0, 0, 0}, vj[3] = {0, 0, 0};
+    double r2 = 0.0;
+    for (int a = 0; a < dim; ++a) { dxv[a] = X[a][j] - X[a][i]; r2 += dxv[a] * dxv[a]; }
+    double r = sqrt(r2);
+    if (r == 0.0) continue;
+    for (int a = 0; a < dim; ++a) { e[a] = dxv[a] / r; vi[a] = Vv[a][i]; vj[a] = Vv[a][j]; }
+    double vRi = 0.0, vRj = 0.0;
+    for (int a = 0; a < dim; ++a) { vRi += vi[a] * e[a]; vRj += vj[a] * e[a]; }
+    double Zi = s->rho[i] * s->c[i], Zj = s->rho[j] * s->c[j], zs = Zi + Zj;
+    double Pi = s->P[i], Pj = s->P[j], Ps, vs;
+    if (zs > 0.0) orc_riemann_acoustic(Pi, Pj, Zi, Zj, vRi, vRj, &Ps, &vs);
+    else { Ps = 0.5 * (Pi + Pj); vs = 0.5 * (vRi + vRj); }
+    double hij = p->eta * (s->d[i] + s->d[j]) * 0.5;
+    double W, Wr, Wh;
+    cubic_dw_derivs(dim, r, hij, &W, &Wr, &Wh);
+    double Vi = s->m[i] / s->rho[i], Vj = s->m[j] / s->rho[j];
+    double rhoi = s->rho[i], rhoj = s->rho[j];
+    double F = 2.0 * Vi * Vj * Ps * W;
+    double dA[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) dA[a] = ga[3 * i + a] / s->m[i] - ga[3 * j + a] / s->m[j];
+    double dB = gE[i] / s->m[i] - gE[j] / s->m[j];
+    double Ci = gr[i], Cj = gr[j];
+    /* outputs of the pair: F e (a), F v* (E), G_i, G_j (rho) */
+    double gF = dB * vs, ge[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) { gF += dA[a] * e[a]; ge[a] = F * dA[a]; }
+    double gvs = F * dB + 2.0 * W * rhoi * Vj * Ci - 2.0 * W * rhoj * Vi * Cj;
+    double gvRi = -2.0 * W * rhoi * Vj * Ci;
+    double gvRj = 2.0 * W * rhoj * Vi * Cj;
+    double gW = gF * 2.0 * Vi * Vj * Ps - Ci * 2.0 * rhoi * Vj * (vRi - vs) - Cj * 2.0 * rhoj * Vi * (vs - vRj);
+    double gPs = gF * 2.0 * Vi * Vj * W;
+    bV[i] += gF * 2.0 * Vj * Ps * W + Cj * 2.0 * rhoj * (vs - vRj) * (-W);
+    bV[j] += gF * 2.0 * Vi * Ps * W + Ci * 2.0 * rhoi * (vRi - vs) * (-W);
+    brho[i] += Ci * 2.0 * Vj * (vRi - vs) * (-W);
+    brho[j] += Cj * 2.0 * Vi * (vs - vRj) * (-W);
+    /* acoustic solver */
+    double gPi, gPj, gZi = 0.0, gZj = 0.0;
+    if (zs > 0.0) {
+      gPi = gPs * Zj / zs + gvs / zs;
+      gPj = gPs * Zi / zs - gvs / zs;
+      gvRi += gPs * Zi * Zj / zs + gvs * Zi / zs;
+      gvRj += -gPs * Zi * Zj / zs + gvs * Zj / zs;
+      gZi = gPs * ((Pj + Zj * (vRi - vRj)) - Ps) / zs + gvs * (vRi - vs) / zs;
+      gZj = gPs * ((Pi + Zi * (vRi - vRj)) - Ps) / zs + gvs * (vRj - vs) / zs;
+    } else {
+      gPi = 0.5 * gPs; gPj = 0.5 * gPs;
+      gvRi += 0.5 * gvs; gvRj += 0.5 * gvs;
+    }
+    bP[i] += gPi; bP[j] += gPj; bZ[i] += gZi; bZ[j] += gZj;
+    /* v^R = v . e */
+    for (int a = 0; a < dim; ++a) {
+      bv[3 * i + a] += gvRi * e[a];
+      bv[3 * j + a] += gvRj * e[a];
+      ge[a] += gvRi * vi[a] + gvRj * vj[a];
+    }
+    /* geometry: e = dx / r, W'(r, h_ij), h_ij = eta (d_i + d_j) / 2 */
+    double gr_ = gW * Wr;
+    double gh = gW * Wh;
+    double ede = 0.0;
+    for (int a = 0; a < dim; ++a) ede += ge[a] * e[a];
+    for (int a = 0; a < dim; ++a) {
+      double gdx = (ge[a] - ede * e[a]) / r + gr_ * e[a];
+      bx[3 * j + a] += gdx;
+      bx[3 * i + a] -= gdx;
+    }
+    bd[i] += gh * p->eta * 0.5;
+    bd[j] += gh * p->eta * 0.5;
+  }
+  /* per-particle chain: V = m/rho, d = (m/rho)^(1/dim), Z = rho c, EOS, e = E - v^2/2 */
+  for (int64_t i = 0; i < n; ++i) {
+    const orc_material* mt = &p->mat[s->mat ? s->mat[i] : 0];
+    double rho = s->rho[i], c = s->c[i], P = s->P[i];
+    double g = mt->gamma, pinf = mt->eos == ORC_EOS_STIFFENED ? mt->p_inf : 0.0;
+    double V = s->m[i] / rho;
+    brho[i] += bV[i] * (-V / rho);
+    brho[i] += bd[i] * (-s->d[i] / ((double)dim * rho));
+    brho[i] += bZ[i] * c;
+    double bc = bZ[i] * rho;
+    double bPi = bP[i], bPinf = 0.0, bg = 0.0;
+    if (c > 0.0) {
+      double bc2 = bc / (2.0 * c);
+      bPi += bc2 * g / rho;
+      brho[i] += bc2 * (-c * c / rho);
+      bPinf += bc2 * g / rho;
+      bg += bc2 * (P + pinf) / rho;
+    }
+    double v2 = 0.0;
+    for (int a = 0; a < dim; ++a) v2 += Vv[a][i] * Vv[a][i];
+    double e_int = s->E[i] - 0.5 * v2;
+    brho[i] += bPi * (g - 1.0) * e_int;
+    double be = bPi * (g - 1.0) * rho;
+    bg += bPi * (rho * e_int - pinf);
+    bPinf += -g * bPi;
+    bE[i] += be;
+    for (int a = 0; a < dim; ++a) bv[3 * i + a] -= be * Vv[a][i];
+    if ((s->mat ? s->mat[i] : 0) == 0) {
+      if (mt->eos == ORC_EOS_STIFFENED) {   /* P_inf = rho0 c0^2 / gamma */
+        bpar[0] += bPinf * 2.0 * mt->rho0 * mt->c0 / g;
+        bg += bPinf * (-pinf / g);
+      }
+      bpar[1] += bg;
+    }
+  }
+  free(bP); free(bZ); free(bV); free(bd);
+  return 0;
+}
+
+/* Forward steps with a prescribed dt sequence (replay of a recorded run). */
+int orc_step_replay(const orc_params* p, orc_state* s, int n_steps, int rates_valid, const double* dts) {
+  /* identical to orc_step with dt taken from dts */
+  orc_params q = *p;
+  int64_t n = s->n;
+  int dim = p->dim;
+  if (!rates_valid) { if (orc_eval_rates(&q, s) < 0) return -1; }
+  size_t bytes = sizeof(double) * (size_t)(n > 0 ? n : 1);
+  double *vh[3], *vp[3], *ap[3];
+  for (int a = 0; a < 3; ++a) { vh[a] = malloc(bytes); vp[a] = malloc(bytes); ap[a] = malloc(bytes); }
+  double *rh = malloc(bytes), *Eh = malloc(bytes), *rp = malloc(bytes), *Ep = malloc(bytes);
+  double *drp = malloc(bytes), *dEp = malloc(bytes), *dp = malloc(bytes), *Pp = malloc(bytes), *cp = malloc(bytes);
+  double* V[3] = {s->vx, s->vy, s->vz};
+  double* X[3] = {s->x, s->y, s->z};
+  double* A[3] = {s->ax, s->ay, s->az};
+  for (int st = 0; st < n_steps; ++st) {
+    double dt = dts[st], hdt = 0.5 * dt;
+    for (int64_t i = 0; i < n; ++i) {
+      for (int a = 0; a < dim; ++a) {
+        vh[a][i] = V[a][i] + hdt * A[a][i];
+        X[a][i] = X[a][i] + dt * vh[a][i];
+        vp[a][i] = vh[a][i] + hdt * A[a][i];
+      }
+      rh[i] = s->rho[i] + hdt * s->drho[i];
+      Eh[i] = s->E[i] + hdt * s->dE[i];
+      rp[i] = rh[i] + hdt * s->drho[i];
+      Ep[i] = Eh[i] + hdt * s->dE[i];
+    }
+    orc_state pr;
+    memset(&pr, 0, sizeof(pr));
+    pr.n = n; pr.x = s->x; pr.y = s->y; pr.z = s->z;
+    pr.vx = vp[0]; pr.vy = dim >= 2 ? vp[1] : NULL; pr.vz = dim >= 3 ? vp[2] : NULL;
+    pr.rho = rp; pr.E = Ep; pr.m = s->m; pr.mat = s->mat;
+    pr.ax = ap[0]; pr.ay = dim >= 2 ? ap[1] : NULL; pr.az = dim >= 3 ? ap[2] : NULL;
+    pr.drho = drp; pr.dE = dEp; pr.d = dp; pr.P = Pp; pr.c = cp;
+    if (orc_eval_rates(&q, &pr) < 0) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+      for (int a = 0; a < dim; ++a) { V[a][i] = vh[a][i] + hdt * ap[a][i]; A[a][i] = ap[a][i]; }
+      s->rho[i] = rh[i] + hdt * drp[i];
+      s->E[i] = Eh[i] + hdt * dEp[i];
+      s->drho[i] = drp[i]; s->dE[i] = dEp[i];
+      s->d[i] = dp[i]; s->P[i] = Pp[i]; s->c[i] = cp[i];
+    }
+  }
+  for (int a = 0; a < 3; ++a) { free(vh[a]); free(vp[a]); free(ap[a]); }
+  free(rh); free(Eh); free(rp); free(Ep); free(drp); free(dEp); free(dp); free(Pp); free(cp);
+  return 0;
+}
+
+/* VJP of one KDK step (orc_step with the given dt) at the state s (x, v,
+ * rho, E and the held rates a, drho, dE; s is not modified).  The adjoint y
+ * = (x, v [3n each, layout 3i+a], rho, E, a [3n], drho, dE) of the state
+ * after the step is replaced in place by the adjoint of the state before it;
+ * bpar (2) accumulates dL/d(c0, gamma). */
+int orc_step_vjp(const orc_params* p, const orc_state* s, double dt, double* yx, double* yv, double* yrho,
+                 double* yE, double* ya, double* ydrho, double* ydE, double* bpar) {
+  int64_t n = s->n;
+  int dim = p->dim;
+  double hdt = 0.5 * dt;
+  size_t b3 = sizeof(double) * 3 * (size_t)(n > 0 ? n : 1), b1 = sizeof(double) * (size_t)(n > 0 ? n : 1);
+  /* predicted state at the end of the drift */
+  double *xp[3], *vp[3];
+  for (int a = 0; a < 3; ++a) { xp[a] = malloc(b1); vp[a] = malloc(b1); }
+  double *rp = malloc(b1), *Ep = malloc(b1), *dp = malloc(b1), *Pp = malloc(b1), *cp = malloc(b1);
+  double *apx = malloc(b1), *apy = malloc(b1), *apz = malloc(b1), *drp = malloc(b1), *dEp = malloc(b1);
+  const double* X[3] = {s->x, s->y, s->z};
+  const double* V[3] = {s->vx, s->vy, s->vz};
+  const double* A[3] = {s->ax, s->ay, s->az};
+  for (int64_t i = 0; i < n; ++i) {
+    for (int a = 0; a < 3; ++a) { xp[a][i] = 0.0; vp[a][i] = 0.0; }
+    for (int a = 0; a < dim; ++a) {
+      double vh = V[a][i] + hdt * A[a][i];
+      xp[a][i] = X[a][i] + dt * vh;
+      vp[a][i] = vh + hdt * A[a][i];
+    }
+    double rh = s->rho[i] + hdt * s->drho[i], Eh = s->E[i] + hdt * s->dE[i];
+    rp[i] = rh + hdt * s->drho[i];
+    Ep[i] = Eh + hdt * s->dE[i];
+  }
+  orc_state pr;
+  memset(&pr, 0, sizeof(pr));
+  pr.n = n; pr.x = xp[0]; pr.y = dim >= 2 ? xp[1] : NULL; pr.z = dim >= 3 ? xp[2] : NULL;
+  pr.vx = vp[0]; pr.vy = dim >= 2 ? vp[1] : NULL; pr.vz = dim >= 3 ? vp[2] : NULL;
+  pr.rho = rp; pr.E = Ep; pr.m = s->m; pr.mat = s->mat;
+  pr.ax = apx; pr.ay = apy; pr.az = apz; pr.drho = drp; pr.dE = dEp; pr.d = dp; pr.P = Pp; pr.c = cp;
+  orc_derive(p, &pr);
+  int64_t np = orc_pairs_cells(p, &pr, 0, NULL, NULL);
+  int32_t* pi = malloc(sizeof(int32_t) * (size_t)(np > 0 ? np : 1));
+  int32_t* pj = malloc(sizeof(int32_t) * (size_t)(np > 0 ? np : 1));
+  orc_pairs_cells(p, &pr, np, pi, pj);
+  /* v' = v^h + h a', rho' = rho^h + h drho', E' = E^h + h dE' */
+  double *gvh = malloc(b3), *grh = malloc(b1), *gEh = malloc(b1);
+  double *ga = malloc(b3), *gr = malloc(b1), *gE = malloc(b1);
+  double *bx = calloc(3 * (size_t)n, sizeof(double)), *bv = calloc(3 * (size_t)n, sizeof(double));
+  double *bro = calloc((size_t)n, sizeof(double)), *bEE = calloc((size_t)n, sizeof(double));
+  for (int64_t i = 0; i < n; ++i) {
+    for (int a = 0; a < 3; ++a) {
+      gvh[3 * i + a] = yv[3 * i + a];
+      ga[3 * i + a] = ya[3 * i + a] + hdt * yv[3 * i + a];
+    }
+    grh[i] = yrho[i]; gr[i] = ydrho[i] + hdt * yrho[i];
+    gEh[i] = yE[i]; gE[i] = ydE[i] + hdt * yE[i];
+  }
+  /* rates at the predicted state */
+  int rc = orc_rates_vjp(p, &pr, np, pi, pj, ga, gr, gE, bx, bv, bro, bEE, bpar);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int a = 0; a < dim; ++a) {
+      double gxp = yx[3 * i + a] + bx[3 * i + a];       /* x' */
+      double gvp = bv[3 * i + a];                        /* v~ */
+      double gvha = gvh[3 * i + a] + gvp + dt * gxp;     /* v^h: from v', v~ and x' */
+      double gah = hdt * gvp + hdt * gvha;               /* a enters v~ and v^h */
+      yx[3 * i + a] = gxp;
+      yv[3 * i + a] = gvha;
+      ya[3 * i + a] = gah;
+    }
+    double grp = bro[i], gEp = bEE[i];
+    double grha = grh[i] + grp, gEha = gEh[i] + gEp;
+    yrho[i] = grha;
+    ydrho[i] = hdt * grp + hdt * grha;
+    yE[i] = gEha;
+    ydE[i] = hdt * gEp + hdt * gEha;
+  }
+  for (int a = 0; a < 3; ++a) { free(xp[a]); free(vp[a]); }
+  free(rp); free(Ep); free(dp); free(Pp); free(cp); free(apx); free(apy); free(apz); free(drp); free(dEp);
+  free(pi); free(pj); free(gvh); free(grh); free(gEh); free(ga); free(gr); free(gE);
+  free(bx); free(bv); free(bro); free(bEE);
+  return rc;
+}

@@ -110,6 +110,14 @@ double orc_balance(int K, int gdim, double* gen, const double* load, const uint8
                    const double* dsh, const double* centroid, const int64_t* count,
                    double theta, double sigma, double gamma_b, double* dg_out);
 
+/* ---- reverse mode (pair set and dt held fixed); cubic kernel, ideal / stiffened gas ---- */
+int orc_rates_vjp(const orc_params* p, const orc_state* s, int64_t npairs, const int32_t* pi, const int32_t* pj,
+                  const double* ga, const double* gr, const double* gE,
+                  double* bx, double* bv, double* brho, double* bE, double* bpar);
+int orc_step_replay(const orc_params* p, orc_state* s, int n_steps, int rates_valid, const double* dts);
+int orc_step_vjp(const orc_params* p, const orc_state* s, double dt, double* yx, double* yv, double* yrho,
+                 double* yE, double* ya, double* ydrho, double* ydE, double* bpar);
+
 #ifdef __cplusplus
 }
 #endif
