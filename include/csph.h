@@ -106,6 +106,16 @@ typedef struct sph_balance_params {
 
 typedef struct sph_handle sph_handle;
 
+/* A checkpoint of a forward run, for sph_step_adjoint. */
+typedef struct sph_ckpt {
+  sph_state state;            /* device: state at the checkpoint, including the held rates */
+  const double* dt;           /* device: the dt of each step after the checkpoint (n_steps doubles),
+                                 as recorded with sph_last_dt during the forward run */
+  int32_t rates_from_state;   /* 1 if the held rates were evaluated at this very state
+                                 (the run's first checkpoint), else 0 */
+  int32_t pad_;
+} sph_ckpt;
+
 /* Create a handle for `s->n` particles split into n_instances independent
  * simulations; instance b owns particles [inst_offsets[b], inst_offsets[b+1])
  * (host array of n_instances+1 entries, inst_offsets[0] = 0,
@@ -144,6 +154,12 @@ int sph_eval_rates(sph_handle* h, sph_state* s, void* stream);
  * sph_build_cells (Alg. 1, outer loop). */
 int sph_step(sph_handle* h, sph_state* s, int n_steps, double* t_dev, void* stream);
 
+/* sph_step with a prescribed time step: step k of instance b uses
+ * dt_dev[k * n_instances + b] (device) instead of the CFL condition; no
+ * rebalancing.  Replays a recorded run (e.g. for finite-difference checks of
+ * sph_step_adjoint). */
+int sph_step_dt(sph_handle* h, sph_state* s, int n_steps, const double* dt_dev, double* t_dev, void* stream);
+
 /* Assign every particle to its nearest generator, eq. (VoronoiDefinition),
  * ties to the smaller index (Sec. 3.1), in the first `dim` coordinates.
  * gen: device, K x dim doubles.  unit_out: device, n int32 (may be s->unit).
@@ -166,6 +182,33 @@ int voronoi_assign(sph_handle* h, const sph_state* s, const double* gen, int K, 
  * rate evaluation; resets the accumulators. */
 int voronoi_balance(sph_handle* h, const sph_state* s, double* gen, int K, int dim, const double* load,
                     const sph_balance_params* bp, double* shift_sum_out, void* stream);
+
+/* Reverse mode of n_steps steps of sph_step after the checkpoint ck, with
+ * the pair set and the dt sequence of the forward run held fixed (dt as a
+ * stop-gradient; the cubic-spline W' and W'' vanish at the support, so the
+ * gradient is continuous when pairs enter or leave).  The forward steps are
+ * replayed from ck in the handle's precision and kept in workspace; the
+ * vector-Jacobian products of the rates (eqs. SPH:Conti, SPH:Pulse,
+ * SPH:Energy with the acoustic pair solver) and of the kick-drift-kick
+ * algebra are accumulated in FP64.
+ *   adj_out: device arrays in sph_state layout holding dL/d(state after the
+ *            n_steps): x, y, z (positions), vx, vy, vz, rho, E, and ax, ay,
+ *            az, drho, dE (the held rates); other fields are ignored
+ *   adj_in:  receives dL/d(state at the checkpoint) in the same layout (may
+ *            be adj_out itself).  With ck->rates_from_state the adjoint of
+ *            the held rates is folded into x, v, rho, E and the rate fields
+ *            are returned as zero.
+ *   adj_params: device, 2 doubles, ADDED dL/d(c0, gamma) of material 0
+ *            (stiffened gas: P_inf = rho0 c0^2 / gamma; ideal gas: gamma).
+ * Requires one instance, the cubic spline and ideal or stiffened gas
+ * (SPH_ERR_INVALID otherwise).  No counterpart in the paper, which runs
+ * forward only; it differentiates the paper's step. */
+int sph_step_adjoint(sph_handle* h, const sph_ckpt* ck, int n_steps, const sph_state* adj_out,
+                     sph_state* adj_in, double* adj_params, void* stream);
+
+/* Copy the dt of the last step (device, n_instances doubles) to dt_out (device),
+ * asynchronously; used to record the schedule for sph_step_adjoint. */
+int sph_last_dt(sph_handle* h, double* dt_out, void* stream);
 
 /* FP64 totals per instance: out (device, n_instances x 5 doubles) receives
  * mass, momentum x/y/z and total energy sum m E, summed in a fixed order. */

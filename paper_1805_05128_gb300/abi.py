@@ -25,7 +25,7 @@ ERROR_NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID", 2: "SPH_ERR_CAPACITY", 3: "SPH
 EXPORTS = ("sph_init", "sph_build_cells", "sph_eval_rates", "sph_step", "voronoi_assign", "voronoi_balance",
            "sph_conservation", "sph_unit_stats", "sph_read_status", "sph_last_error", "sph_pair_counts",
            "sph_cell_index", "sph_pair_list", "voronoi_assign_static", "sph_profile", "sph_profile_read",
-           "sph_destroy")
+           "sph_step_adjoint", "sph_last_dt", "sph_step_dt", "sph_destroy")
 
 
 class sph_material(C.Structure):
@@ -51,6 +51,10 @@ class sph_state(C.Structure):
     _fields_ = ([("n", C.c_int64)] + [(k, C.c_void_p) for k in STATE_F64] + [("mat", C.c_void_p)]
                 + [(k, C.c_void_p) for k in STATE_RATES + STATE_DERIVED] + [("id", C.c_void_p),
                                                                               ("unit", C.c_void_p)])
+
+
+class sph_ckpt(C.Structure):
+    _fields_ = [("state", sph_state), ("dt", C.c_void_p), ("rates_from_state", C.c_int32), ("pad_", C.c_int32)]
 
 
 class sph_balance_params(C.Structure):
@@ -87,6 +91,9 @@ def lib() -> C.CDLL:
     L.sph_cell_index.argtypes = [vp, C.POINTER(sph_state), vp, C.POINTER(C.c_double), vp]
     L.sph_pair_list.argtypes = [vp, C.POINTER(sph_state), i64, vp, vp, C.POINTER(C.c_int64), vp]
     L.voronoi_assign_static.argtypes = [i64, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp]
+    L.sph_step_adjoint.argtypes = [vp, C.POINTER(sph_ckpt), i32, C.POINTER(sph_state), C.POINTER(sph_state), vp, vp]
+    L.sph_last_dt.argtypes = [vp, vp, vp]
+    L.sph_step_dt.argtypes = [vp, C.POINTER(sph_state), i32, vp, vp, vp]
     L.sph_profile.argtypes = [vp, i32]
     L.sph_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.sph_destroy.argtypes = [vp]
@@ -183,6 +190,20 @@ def voronoi_assign_static(n, x_ptr, y_ptr, z_ptr, gen_ptr, K, dim, unit_out_ptr,
                                       C.c_void_p(gen_ptr), K, dim, C.c_void_p(unit_out_ptr),
                                       C.c_void_p(unit_offsets_ptr), C.c_void_p(unit_list_ptr),
                                       C.c_void_p(stream)))
+
+
+def sph_step_adjoint(h, ckpt: sph_ckpt, n_steps, adj_out: sph_state, adj_in: sph_state, params_ptr, stream):
+    check(lib().sph_step_adjoint(h, C.byref(ckpt), n_steps, C.byref(adj_out), C.byref(adj_in),
+                                 C.c_void_p(params_ptr), C.c_void_p(stream)), h)
+
+
+def sph_last_dt(h, dt_out_ptr, stream):
+    check(lib().sph_last_dt(h, C.c_void_p(dt_out_ptr), C.c_void_p(stream)), h)
+
+
+def sph_step_dt(h, state, n_steps, dt_ptr, t_dev_ptr, stream):
+    check(lib().sph_step_dt(h, C.byref(state), n_steps, C.c_void_p(dt_ptr), C.c_void_p(t_dev_ptr),
+                            C.c_void_p(stream)), h)
 
 
 def sph_profile(h, enable: bool):

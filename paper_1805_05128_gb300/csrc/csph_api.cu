@@ -41,7 +41,8 @@ void free_all(sph_handle* h) {
                   h->inst_cap, h->total_cells, h->cell_count, h->cell_start, h->scan_sums, h->cell_of, h->rank,
                   h->perm, h->slot_cell, h->slot_unit, h->packA, h->packB, h->packC, h->rho_slot, h->dmax_nbr,
                   h->load_acc, h->adj_bits, h->unit_off, h->unit_list, h->unit_work, h->unit_total, h->unit_stats,
-                  h->status, h->counters, h->scratch};
+                  h->status, h->counters, h->scratch, h->adj_A, h->adj_B, h->adj_C, h->adj_rho, h->adj_G,
+                  h->adj_GR, h->adj_pair, h->adj_par, h->adj_W, h->adj_store};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -61,6 +62,16 @@ int check_handle_state(sph_handle* h, const sph_state* s) {
   if (rc) return rc;
   if (s->n != h->n) return fail(h, SPH_ERR_INVALID, "state size differs from the handle's");
   if (h->K > 0 && !s->unit) return fail(h, SPH_ERR_INVALID, "state: unit array NULL with work units enabled");
+  return SPH_OK;
+}
+
+// adjoint states carry x, v, rho, E and the rate fields only
+int check_adjoint_state(sph_handle* h, const sph_state* a) {
+  const int dim = h->dp.dim;
+  if (!a || !a->x || !a->vx || !a->rho || !a->E || !a->ax || !a->drho || !a->dE)
+    return fail(h, SPH_ERR_INVALID, "adjoint state: x, vx, rho, E, ax, drho, dE are required");
+  if (dim >= 2 && (!a->y || !a->vy || !a->ay)) return fail(h, SPH_ERR_INVALID, "adjoint state: y/vy/ay for dim >= 2");
+  if (dim >= 3 && (!a->z || !a->vz || !a->az)) return fail(h, SPH_ERR_INVALID, "adjoint state: z/vz/az for dim 3");
   return SPH_OK;
 }
 
@@ -313,6 +324,28 @@ int sph_step(sph_handle* h, sph_state* s, int n_steps, double* t_dev, void* stre
   return SPH_OK;
 }
 
+int sph_step_dt(sph_handle* h, sph_state* s, int n_steps, const double* dt_dev, double* t_dev, void* stream) {
+  int rc = check_handle_state(h, s);
+  if (rc) return rc;
+  if (n_steps < 0 || (n_steps > 0 && !dt_dev)) return fail(h, SPH_ERR_INVALID, "need n_steps >= 0 and dt_dev");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  if (!h->rates_valid) {
+    rc = eval_rates_impl(h, s, st);
+    if (rc) return rc;
+  }
+  for (int k = 0; k < n_steps; ++k) {
+    CK(h, cudaMemcpyAsync(h->dt, dt_dev + (size_t)k * h->n_inst, sizeof(double) * h->n_inst,
+                          cudaMemcpyDeviceToDevice, st));
+    CK(h, launch_kick_drift(h, *s, st));
+    CK(h, launch_build_grid(h, *s, st));
+    CK(h, launch_pack(h, *s, true, st));
+    CK(h, launch_pair(h, *s, st));
+    CK(h, launch_kick2(h, *s, t_dev, st));
+  }
+  return SPH_OK;
+}
+
 int voronoi_assign(sph_handle* h, const sph_state* s, const double* gen, int K, int dim, int32_t* unit_out,
                    int32_t* unit_offsets, void* stream) {
   int rc = check_handle_state(h, s);
@@ -434,6 +467,132 @@ int sph_pair_list(sph_handle* h, sph_state* s, int64_t cap, int32_t* pi_out, int
   CK(h, cudaStreamSynchronize(st));
   *count_out = (int64_t)c;
   if ((int64_t)c > cap) return fail(h, SPH_ERR_CAPACITY, "more pairs than cap");
+  return SPH_OK;
+}
+
+int sph_last_dt(sph_handle* h, double* dt_out, void* stream) {
+  if (!h || !dt_out) return SPH_ERR_INVALID;
+  CK(h, cudaMemcpyAsync(dt_out, h->dt, sizeof(double) * h->n_inst, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return SPH_OK;
+}
+
+namespace {
+
+// 13 state arrays stored per replayed step; the working state W adds d, P, c
+constexpr int kAdjStored = 13;
+constexpr int kAdjW = 16;
+
+sph_state adj_work_state(sph_handle* h, const sph_state& ck) {
+  const int64_t n = h->n;
+  double* w = h->adj_W;
+  sph_state W{};
+  W.n = n;
+  double** f[kAdjW] = {&W.x, &W.y, &W.z, &W.vx, &W.vy, &W.vz, &W.rho, &W.E, &W.ax, &W.ay, &W.az, &W.drho, &W.dE,
+                       &W.d, &W.P, &W.c};
+  for (int k = 0; k < kAdjW; ++k) *f[k] = w + (size_t)k * n;
+  if (h->dp.dim < 2) { W.y = W.vy = W.ay = nullptr; }
+  if (h->dp.dim < 3) { W.z = W.vz = W.az = nullptr; }
+  W.m = ck.m;
+  W.mat = ck.mat;
+  W.id = nullptr;
+  W.unit = nullptr;
+  return W;
+}
+
+// copy the 13 dynamic arrays (x, v, rho, E, rates) between two states
+cudaError_t copy_dynamic(const sph_state& dst, const sph_state& src, int64_t n, cudaStream_t st) {
+  double* d[kAdjStored] = {dst.x, dst.y, dst.z, dst.vx, dst.vy, dst.vz, dst.rho, dst.E, dst.ax, dst.ay, dst.az,
+                           dst.drho, dst.dE};
+  const double* s[kAdjStored] = {src.x, src.y, src.z, src.vx, src.vy, src.vz, src.rho, src.E, src.ax, src.ay,
+                                 src.az, src.drho, src.dE};
+  for (int k = 0; k < kAdjStored; ++k) {
+    if (!d[k] || !s[k]) continue;
+    cudaError_t e = cudaMemcpyAsync(d[k], s[k], sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+sph_state stored_state(sph_handle* h, int step, const sph_state& like) {
+  const int64_t n = h->n;
+  double* base = h->adj_store + (size_t)step * kAdjStored * n;
+  sph_state S = like;
+  double** f[kAdjStored] = {&S.x, &S.y, &S.z, &S.vx, &S.vy, &S.vz, &S.rho, &S.E, &S.ax, &S.ay, &S.az, &S.drho,
+                            &S.dE};
+  for (int k = 0; k < kAdjStored; ++k) *f[k] = base + (size_t)k * n;
+  if (h->dp.dim < 2) { S.y = S.vy = S.ay = nullptr; }
+  if (h->dp.dim < 3) { S.z = S.vz = S.az = nullptr; }
+  return S;
+}
+
+}  // namespace
+
+int sph_step_adjoint(sph_handle* h, const sph_ckpt* ck, int n_steps, const sph_state* adj_out, sph_state* adj_in,
+                     double* adj_params, void* stream) {
+  if (!h || !ck || !adj_out || !adj_in || !adj_params) return h ? fail(h, SPH_ERR_INVALID, "NULL argument") : SPH_ERR_INVALID;
+  if (n_steps < 0 || (n_steps > 0 && !ck->dt)) return fail(h, SPH_ERR_INVALID, "need n_steps >= 0 and the dt record");
+  if (h->n_inst != 1) return fail(h, SPH_ERR_INVALID, "the adjoint supports a single instance");
+  if (h->dp.kernel != SPH_KERNEL_CUBIC) return fail(h, SPH_ERR_INVALID, "the adjoint supports the cubic spline");
+  for (int k = 0; k < h->dp.n_mat; ++k)
+    if (h->dp.mat[k].eos != SPH_EOS_IDEAL && h->dp.mat[k].eos != SPH_EOS_STIFFENED)
+      return fail(h, SPH_ERR_INVALID, "the adjoint supports ideal and stiffened gas");
+  int rc = check_handle_state(h, &ck->state);
+  if (rc) return rc;
+  rc = check_adjoint_state(h, adj_out);
+  if (rc) return rc;
+  rc = check_adjoint_state(h, adj_in);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  const int64_t n = h->n;
+  if (!h->adj_A) {
+    CK(h, dalloc(&h->adj_A, n));
+    CK(h, dalloc(&h->adj_B, n));
+    CK(h, dalloc(&h->adj_C, n));
+    CK(h, dalloc(&h->adj_rho, n));
+    CK(h, dalloc(&h->adj_G, n));
+    CK(h, dalloc(&h->adj_GR, n));
+    CK(h, dalloc(&h->adj_pair, (size_t)11 * n));
+    CK(h, dalloc(&h->adj_par, (size_t)2 * n));
+    CK(h, dalloc(&h->adj_W, (size_t)kAdjW * n));
+    CK(h, cudaMemsetAsync(h->adj_W, 0, sizeof(double) * kAdjW * n, st));
+  }
+  if (n_steps > h->adj_store_steps) {
+    if (h->adj_store) CK(h, cudaFree(h->adj_store));
+    h->adj_store = nullptr;
+    CK(h, dalloc(&h->adj_store, (size_t)n_steps * kAdjStored * n));
+    h->adj_store_steps = n_steps;
+  }
+  sph_state W = adj_work_state(h, ck->state);
+  // forward replay from the checkpoint with the recorded dt, keeping every state
+  CK(h, copy_dynamic(W, ck->state, n, st));
+  for (int k = 0; k < n_steps; ++k) {
+    CK(h, copy_dynamic(stored_state(h, k, W), W, n, st));
+    CK(h, cudaMemcpyAsync(h->dt, ck->dt + k, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(h, launch_kick_drift(h, W, st));
+    CK(h, launch_build_grid(h, W, st));
+    CK(h, launch_pack(h, W, true, st));
+    CK(h, launch_pair(h, W, st));
+    CK(h, launch_kick2(h, W, nullptr, st));
+  }
+  // adjoint, in place in adj_in
+  if (adj_in != adj_out) CK(h, copy_dynamic(*adj_in, *adj_out, n, st));
+  for (int k = n_steps - 1; k >= 0; --k) {
+    CK(h, copy_dynamic(W, stored_state(h, k, W), n, st));
+    CK(h, cudaMemcpyAsync(h->dt, ck->dt + k, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(h, launch_kick_drift(h, W, st));
+    CK(h, launch_build_grid(h, W, st));
+    CK(h, launch_pack_fp64(h, W, true, h->adj_A, h->adj_B, h->adj_C, h->adj_rho, st));
+    CK(h, launch_rates_vjp(h, W, *adj_in, ck->dt + k, 1, adj_params, st));
+  }
+  if (ck->rates_from_state) {
+    // the held rates at the checkpoint were evaluated at its own state
+    CK(h, copy_dynamic(W, ck->state, n, st));
+    CK(h, launch_derive_dt(h, W, true, st));
+    CK(h, launch_build_grid(h, W, st));
+    CK(h, launch_pack_fp64(h, W, false, h->adj_A, h->adj_B, h->adj_C, h->adj_rho, st));
+    CK(h, launch_rates_vjp(h, W, *adj_in, h->dt, 0, adj_params, st));
+  }
   return SPH_OK;
 }
 

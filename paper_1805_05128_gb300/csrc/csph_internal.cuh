@@ -135,6 +135,19 @@ struct sph_handle {
   // renumbering scratch
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+
+  // reverse mode (sph_step_adjoint), allocated on first use
+  csph::D4* adj_A = nullptr;          // FP64 operands of the predicted state, slot order
+  csph::D4* adj_B = nullptr;
+  csph::D2* adj_C = nullptr;
+  double* adj_rho = nullptr;
+  csph::D4* adj_G = nullptr;          // rate adjoints / m, slot order
+  double* adj_GR = nullptr;
+  double* adj_pair = nullptr;         // 11 per particle: own-side pair derivatives
+  double* adj_par = nullptr;          // 2 per particle: parameter derivatives
+  double* adj_W = nullptr;            // working state, 16 arrays of n
+  double* adj_store = nullptr;        // replayed states, 13 arrays of n per step
+  int adj_store_steps = 0;
 };
 
 namespace csph {
@@ -220,6 +233,12 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
 cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st);
 cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st);
 cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st);
+// k_pack's FP64 variant writing into the given operand arrays (reverse mode)
+cudaError_t launch_pack_fp64(sph_handle* h, const sph_state& s, bool predict, void* A, void* B, void* C,
+                             double* rho_out, cudaStream_t st);
+// rates VJP at the packed state (k_adjoint.cu)
+cudaError_t launch_rates_vjp(sph_handle* h, const sph_state& W, sph_state& adj, const double* dt, int predicted,
+                             double* par, cudaStream_t st);
 // Exclusive scan of cnt[0, *total) into start[0, *total], start[*total] = n_total;
 // cnt is zeroed; launched for up to `cap` elements.
 cudaError_t launch_exclusive_scan(int32_t* cnt, const int64_t* total, int32_t* sums, int32_t* start,

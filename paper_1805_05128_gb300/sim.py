@@ -107,6 +107,15 @@ class Simulation:
     def step(self, n_steps: int = 1):
         abi.sph_step(self.handle, self.state(), n_steps, self.time.data_ptr(), _stream_ptr())
 
+    def step_dt(self, dts: torch.Tensor):
+        """Steps with prescribed time steps (device tensor, n_steps x n_instances)."""
+        dts = dts.contiguous()
+        abi.sph_step_dt(self.handle, self.state(), dts.shape[0], dts.data_ptr(), self.time.data_ptr(),
+                        _stream_ptr())
+
+    def last_dt(self, out: torch.Tensor):
+        abi.sph_last_dt(self.handle, out.data_ptr(), _stream_ptr())
+
     def assign(self, gen=None) -> torch.Tensor:
         g = self.gen if gen is None else gen
         offs = torch.zeros(self.K + 1, dtype=torch.int32, device=self.device)
