@@ -66,7 +66,7 @@ typedef struct sph_params {
   int32_t dim;        /* spatial dimension of the particles: 1, 2 or 3 */
   int32_t kernel;     /* SPH_KERNEL_* */
   int32_t precision;  /* SPH_PREC_* */
-  int32_t n_mat;      /* materials used (1..SPH_MAX_MAT) */
+  int32_t n_mat;      /* materials used: 1..SPH_MAX_MAT in mat[], or up to 65536 with materials */
   double kappa;       /* kernel support in units of h */
   double eta;         /* h_ij = eta (d_i + d_j)/2, eq. (SmoothingLengthDef) times eta */
   double cfl;         /* dt = cfl min_i eta d_i / (c_i + |v_i|) */
@@ -77,12 +77,15 @@ typedef struct sph_params {
   int32_t n_units;    /* K <= SPH_MAX_UNITS */
   int32_t unit_dim;   /* dimension of the decomposition: 1, 2 or 3 (<= dim) */
   int32_t n_upd;      /* sph_step rebalances every n_upd steps (0 = never) */
-  int32_t pad_;
+  int32_t pair_blocks_per_sm; /* resident CTAs per SM of the persistent pair kernel (128 threads,
+                                 one warp per home cell); 0 or more than fit = as many as fit */
   double theta;       /* eq. (TotalOffset) */
   double sigma;       /* eq. (BalancingOffsetPlusRot) */
   double gamma_b;     /* gamma of eq. (TotalOffset) */
   double beta_sh;     /* buffer beta of R^hrz used in D^sh, eq. (Horizon) */
   double* generators; /* device, K x unit_dim, read and updated by sph_step's rebalancing */
+  const sph_material* materials; /* host, n_mat entries, or NULL to use mat[]; copied by sph_init
+                                    (one material per instance gives per-instance EOS parameters) */
 } sph_params;
 
 /* Particle state: structure of arrays in device memory, n elements each.

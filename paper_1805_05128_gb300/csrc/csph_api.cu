@@ -42,7 +42,7 @@ void free_all(sph_handle* h) {
                   h->perm, h->slot_cell, h->slot_unit, h->packA, h->packB, h->packC, h->rho_slot, h->dmax_nbr,
                   h->load_acc, h->adj_bits, h->unit_off, h->unit_list, h->unit_work, h->unit_total, h->unit_stats,
                   h->status, h->counters, h->scratch, h->adj_A, h->adj_B, h->adj_C, h->adj_rho, h->adj_G,
-                  h->adj_GR, h->adj_pair, h->adj_par, h->adj_W, h->adj_store};
+                  h->adj_GR, h->adj_pair, h->adj_par, h->adj_W, h->adj_store, h->mat_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -115,9 +115,11 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     return fail(nullptr, SPH_ERR_INVALID, "unknown kernel");
   if (p->precision != SPH_PREC_FP64 && p->precision != SPH_PREC_MIXED)
     return fail(nullptr, SPH_ERR_INVALID, "unknown precision");
-  if (p->n_mat < 1 || p->n_mat > SPH_MAX_MAT) return fail(nullptr, SPH_ERR_INVALID, "n_mat out of range");
+  if (p->n_mat < 1 || p->n_mat > kMaxMaterials || (p->n_mat > SPH_MAX_MAT && !p->materials))
+    return fail(nullptr, SPH_ERR_INVALID, "n_mat out of range (more than SPH_MAX_MAT need params.materials)");
+  const sph_material* mats = p->materials ? p->materials : p->mat;
   for (int k = 0; k < p->n_mat; ++k)
-    if (p->mat[k].eos < SPH_EOS_IDEAL || p->mat[k].eos > SPH_EOS_MIE_GRUNEISEN)
+    if (mats[k].eos < SPH_EOS_IDEAL || mats[k].eos > SPH_EOS_MIE_GRUNEISEN)
       return fail(nullptr, SPH_ERR_INVALID, "unknown EOS");
   if (!(p->kappa > 0) || !(p->eta > 0) || !(p->cfl > 0) || !(p->cell_beta >= 0))
     return fail(nullptr, SPH_ERR_INVALID, "kappa, eta, cfl must be > 0 and cell_beta >= 0");
@@ -151,10 +153,11 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   dp.dim = p->dim; dp.kernel = p->kernel; dp.precision = p->precision; dp.n_mat = p->n_mat;
   dp.kappa = p->kappa; dp.eta = p->eta; dp.cfl = p->cfl; dp.cell_beta = p->cell_beta;
   dp.kh = (0.5 * p->kappa) * p->eta;
-  for (int k = 0; k < SPH_MAX_MAT; ++k) {
-    const sph_material& m = p->mat[k < p->n_mat ? k : 0];
-    dp.mat[k] = Mat{m.eos, m.gamma, m.rho0, m.c0, m.p_inf, m.s_a};
+  for (int k = 0; k < p->n_mat; ++k) {
+    const sph_material& m = mats[k];
+    h->mat_h.push_back(Mat{m.eos, m.gamma, m.rho0, m.c0, m.p_inf, m.s_a});
   }
+  h->p.materials = nullptr;   // the caller's host array is not kept
   cudaStream_t st = (cudaStream_t)stream;
   auto bail = [&](int code) {
     g_init_error = h->err;
@@ -167,6 +170,10 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     cudaError_t e_ = (call);                                              \
     if (e_ != cudaSuccess) { cuda_fail(h, #call, e_); return bail(SPH_ERR_CUDA); } \
   } while (0)
+
+  CKI(dalloc(&h->mat_dev, h->mat_h.size()));
+  CKI(cudaMemcpy(h->mat_dev, h->mat_h.data(), sizeof(Mat) * h->mat_h.size(), cudaMemcpyHostToDevice));
+  dp.mat = h->mat_dev;
 
   // segmented blocks
   std::vector<int32_t> bi;
@@ -534,7 +541,7 @@ int sph_step_adjoint(sph_handle* h, const sph_ckpt* ck, int n_steps, const sph_s
   if (h->n_inst != 1) return fail(h, SPH_ERR_INVALID, "the adjoint supports a single instance");
   if (h->dp.kernel != SPH_KERNEL_CUBIC) return fail(h, SPH_ERR_INVALID, "the adjoint supports the cubic spline");
   for (int k = 0; k < h->dp.n_mat; ++k)
-    if (h->dp.mat[k].eos != SPH_EOS_IDEAL && h->dp.mat[k].eos != SPH_EOS_STIFFENED)
+    if (h->mat_h[k].eos != SPH_EOS_IDEAL && h->mat_h[k].eos != SPH_EOS_STIFFENED)
       return fail(h, SPH_ERR_INVALID, "the adjoint supports ideal and stiffened gas");
   int rc = check_handle_state(h, &ck->state);
   if (rc) return rc;

@@ -50,8 +50,9 @@ struct Mat {
 struct DevParams {
   int dim, kernel, precision, n_mat;
   double kappa, eta, cfl, cell_beta, kh;  // kh = (0.5 kappa) eta
-  Mat mat[SPH_MAX_MAT];
+  const Mat* mat;                         // device table of n_mat materials
 };
+constexpr int kMaxMaterials = 65536;
 
 // FP64 packed pair operands (slot order).
 struct alignas(32) D4 { double x, y, z, w; };
@@ -127,6 +128,9 @@ struct sph_handle {
   bool profiling = false;
   std::vector<cudaEvent_t> prof_events;     // pool, used in (start, stop) pairs
   size_t prof_used = 0;
+
+  csph::Mat* mat_dev = nullptr;             // material table
+  std::vector<csph::Mat> mat_h;
 
   int* status = nullptr;                    // device status word
   unsigned long long* counters = nullptr;   // [8] full-list pairs, candidates, fp64 checks, assign FP64

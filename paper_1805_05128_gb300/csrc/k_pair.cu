@@ -462,27 +462,30 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair(PairArgs a) 
   }
 }
 
-// Persistent grid: as many blocks as can be resident on the device at once.
+// Persistent grid: SMs x resident CTAs per SM, capped by the handle's
+// pair_blocks_per_sm (0 = as many as fit).
 template <bool MIXED, int DIM>
-cudaError_t launch_one(const PairArgs& args, cudaStream_t st) {
-  static int grid = 0;
-  if (grid == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
+cudaError_t launch_one(const PairArgs& args, int blocks_per_sm, cudaStream_t st) {
+  static int sms = 0, per_sm = 0;
+  if (sms == 0) {
+    int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<MIXED, DIM>, kPairBlock, 0);
-    grid = sms * (per_sm > 0 ? per_sm : 1);
+    if (per_sm < 1) per_sm = 1;
   }
-  k_pair<MIXED, DIM><<<grid, kPairBlock, 0, st>>>(args);
+  const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
+  k_pair<MIXED, DIM><<<sms * b, kPairBlock, 0, st>>>(args);
   return cudaGetLastError();
 }
 
 template <bool MIXED>
 cudaError_t launch_dim(sph_handle* h, const PairArgs& args, cudaStream_t st) {
+  const int b = h->p.pair_blocks_per_sm;
   switch (h->dp.dim) {
-    case 1: return launch_one<MIXED, 1>(args, st);
-    case 2: return launch_one<MIXED, 2>(args, st);
-    default: return launch_one<MIXED, 3>(args, st);
+    case 1: return launch_one<MIXED, 1>(args, b, st);
+    case 2: return launch_one<MIXED, 2>(args, b, st);
+    default: return launch_one<MIXED, 3>(args, b, st);
   }
 }
 

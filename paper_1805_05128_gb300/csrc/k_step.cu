@@ -222,22 +222,26 @@ constexpr int kScanTile = 1024;
 
 __global__ void k_scan_reduce(const int32_t* __restrict__ cnt, const int64_t* __restrict__ total,
                               int32_t* sums) {
-  int64_t base = (int64_t)blockIdx.x * kScanTile;
-  int64_t tot = *total;
-  if (base >= tot) return;
-  int v = 0;
-  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
-    int64_t c = base + k;
-    if (c < tot) v += cnt[c];
-  }
+  const int64_t tot = *total;
   __shared__ int sh[kBlock];
-  sh[threadIdx.x] = v;
-  __syncthreads();
-  for (int w = kBlock / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+  // grid-stride over the tiles the current mesh has (the grid is sized for the capacity,
+  // capped at a few waves)
+  for (int64_t t = blockIdx.x; t * kScanTile < tot; t += gridDim.x) {
+    const int64_t base = t * kScanTile;
+    int v = 0;
+    for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+      int64_t c = base + k;
+      if (c < tot) v += cnt[c];
+    }
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = kBlock / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[t] = sh[0];
     __syncthreads();
   }
-  if (threadIdx.x == 0) sums[blockIdx.x] = sh[0];
 }
 
 // Single block: exclusive scan of the tile sums in place.
@@ -268,36 +272,38 @@ __global__ void k_scan_sums(int32_t* sums, const int64_t* __restrict__ total) {
 // Per tile: exclusive scan plus tile offset; zero the counts for the next use.
 __global__ void k_scan_down(int32_t* cnt, const int64_t* __restrict__ total, const int32_t* __restrict__ sums,
                             int32_t* start, int64_t n_total) {
-  int64_t base = (int64_t)blockIdx.x * kScanTile;
-  int64_t tot = *total;
-  if (base >= tot) return;
+  const int64_t tot = *total;
   constexpr int per = kScanTile / kBlock;  // 4 cells per thread
-  int vals[per];
-  int run = 0;
-  for (int k = 0; k < per; ++k) {
-    int64_t c = base + threadIdx.x * per + k;
-    vals[k] = (c < tot) ? cnt[c] : 0;
-    run += vals[k];
-  }
   __shared__ int sh[kBlock];
-  sh[threadIdx.x] = run;
-  __syncthreads();
-  for (int off = 1; off < kBlock; off <<= 1) {
-    int add = threadIdx.x >= (unsigned)off ? sh[threadIdx.x - off] : 0;
-    __syncthreads();
-    sh[threadIdx.x] += add;
-    __syncthreads();
-  }
-  int acc = sums[blockIdx.x] + sh[threadIdx.x] - run;
-  for (int k = 0; k < per; ++k) {
-    int64_t c = base + threadIdx.x * per + k;
-    if (c < tot) {
-      start[c] = acc;
-      acc += vals[k];
-      cnt[c] = 0;
+  for (int64_t t = blockIdx.x; t * kScanTile < tot; t += gridDim.x) {
+    const int64_t base = t * kScanTile;
+    int vals[per];
+    int run = 0;
+    for (int k = 0; k < per; ++k) {
+      int64_t c = base + threadIdx.x * per + k;
+      vals[k] = (c < tot) ? cnt[c] : 0;
+      run += vals[k];
     }
+    sh[threadIdx.x] = run;
+    __syncthreads();
+    for (int off = 1; off < kBlock; off <<= 1) {
+      int add = threadIdx.x >= (unsigned)off ? sh[threadIdx.x - off] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += add;
+      __syncthreads();
+    }
+    int acc = sums[t] + sh[threadIdx.x] - run;
+    for (int k = 0; k < per; ++k) {
+      int64_t c = base + threadIdx.x * per + k;
+      if (c < tot) {
+        start[c] = acc;
+        acc += vals[k];
+        cnt[c] = 0;
+      }
+    }
+    if (base + kScanTile >= tot && threadIdx.x == 0) start[tot] = (int32_t)n_total;
+    __syncthreads();
   }
-  if (base + kScanTile >= tot && threadIdx.x == 0) start[tot] = (int32_t)n_total;
 }
 
 __global__ void k_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of, const int32_t* __restrict__ rank,
@@ -310,14 +316,15 @@ __global__ void k_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of, c
 // Within each cell, order the particles by index (the atomic arrival order is
 // not reproducible; this makes the slot order a function of the state only).
 __global__ void k_cell_sort(const int64_t* __restrict__ total, const int32_t* __restrict__ start, int32_t* perm) {
-  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= *total) return;
-  int b = start[c], e = start[c + 1];
-  for (int i = b + 1; i < e; ++i) {
-    int32_t v = perm[i];
-    int j = i - 1;
-    while (j >= b && perm[j] > v) { perm[j + 1] = perm[j]; --j; }
-    perm[j + 1] = v;
+  const int64_t tot = *total;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (int64_t)gridDim.x * blockDim.x) {
+    int b = start[c], e = start[c + 1];
+    for (int i = b + 1; i < e; ++i) {
+      int32_t v = perm[i];
+      int j = i - 1;
+      while (j >= b && perm[j] > v) { perm[j + 1] = perm[j]; --j; }
+      perm[j + 1] = v;
+    }
   }
 }
 
@@ -515,6 +522,20 @@ __global__ void k_check_finite(int dim, sph_state s, int64_t n, int* status) {
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Grids over the mesh capacity, whose kernels read the live cell count on the
+// device and stride over it: at most 8 blocks of kBlock per SM, so a generous
+// capacity costs no empty waves.
+static int capped_grid(int want) {
+  static int cap = 0;
+  if (cap == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cap = 8 * (sms > 0 ? sms : 1);
+  }
+  return want < cap ? (want > 0 ? want : 1) : cap;
+}
+
 cudaError_t launch_derive_dt(sph_handle* h, const sph_state& s, bool with_bbox, cudaStream_t st) {
   k_derive<<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->part, with_bbox ? 1 : 0,
                                        with_bbox ? 1 : 0);
@@ -543,12 +564,12 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
                                  h->status);
   k_cell_count<<<h->nblk, kBlock, 0, st>>>(h->dp.dim, s, h->blk_start, h->blk_end, h->blk_inst, h->grid,
                                            h->cell_count, h->cell_of, h->rank, h->status);
-  int tiles = grid_for(h->cell_cap, kScanTile);
+  int tiles = capped_grid(grid_for(h->cell_cap, kScanTile));
   k_scan_reduce<<<tiles, kBlock, 0, st>>>(h->cell_count, h->total_cells, h->scan_sums);
   k_scan_sums<<<1, 1024, 0, st>>>(h->scan_sums, h->total_cells);
   k_scan_down<<<tiles, kBlock, 0, st>>>(h->cell_count, h->total_cells, h->scan_sums, h->cell_start, h->n);
   k_cell_scatter<<<grid_for(h->n, kBlock), kBlock, 0, st>>>(h->n, h->cell_of, h->rank, h->cell_start, h->perm);
-  k_cell_sort<<<grid_for(h->cell_cap, kBlock), kBlock, 0, st>>>(h->total_cells, h->cell_start, h->perm);
+  k_cell_sort<<<capped_grid(grid_for(h->cell_cap, kBlock)), kBlock, 0, st>>>(h->total_cells, h->cell_start, h->perm);
   h->launches += 8;
   return cudaGetLastError();
 }
@@ -604,7 +625,7 @@ cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st) {
 
 cudaError_t launch_exclusive_scan(int32_t* cnt, const int64_t* total, int32_t* sums, int32_t* start,
                                   int64_t n_total, int64_t cap, cudaStream_t st) {
-  int tiles = grid_for(cap, kScanTile);
+  int tiles = capped_grid(grid_for(cap, kScanTile));
   k_scan_reduce<<<tiles, kBlock, 0, st>>>(cnt, total, sums);
   k_scan_sums<<<1, 1024, 0, st>>>(sums, total);
   k_scan_down<<<tiles, kBlock, 0, st>>>(cnt, total, sums, start, n_total);

@@ -29,7 +29,8 @@ class Simulation:
 
     def __init__(self, problems, precision: str = "mixed", units: int | None = None,
                  generators=None, n_upd: int | None = None, theta: float = 0.25, sigma: float = 0.5,
-                 gamma_b: float = 1.0, beta_sh: float = 0.45, cell_cap: int = 1 << 24,
+                 gamma_b: float = 1.0, beta_sh: float = 0.45, cell_cap: int = 1 << 24, cell_beta: float = 0.0,
+                 pair_blocks_per_sm: int = 0,
                  device: str | torch.device = "cuda:0"):
         if not isinstance(problems, (list, tuple)):
             problems = [problems]
@@ -53,7 +54,15 @@ class Simulation:
                 self.t[k] = torch.from_numpy(np.concatenate(vals)).to(**f64).contiguous()
             else:
                 self.t[k] = torch.zeros(self.n, **f64)
-        mats = [q.mat if q.mat is not None else np.zeros(len(q.arrays["x"]), dtype=np.int32) for q in problems]
+        # material table: the problems' materials in order; each particle's index is offset
+        # by the materials of the problems before it (one table even when every instance has
+        # its own EOS parameters)
+        self.materials, mats = [], []
+        for q in problems:
+            base = len(self.materials)
+            self.materials.extend(q.materials)
+            local = q.mat if q.mat is not None else np.zeros(len(q.arrays["x"]), dtype=np.int32)
+            mats.append(np.asarray(local, dtype=np.int32) + base)
         self.t["mat"] = torch.from_numpy(np.concatenate(mats).astype(np.int32)).to(dev)
         self.t["id"] = torch.arange(self.n, dtype=torch.int64, device=dev)
         K = p0.units if units is None else units
@@ -70,14 +79,19 @@ class Simulation:
 
         prm = abi.sph_params()
         prm.dim, prm.kernel, prm.precision = self.dim, _KERNEL[p0.kernel], _PREC[precision]
-        prm.n_mat = len(p0.materials)
-        prm.kappa, prm.eta, prm.cfl, prm.cell_beta, prm.cell_cap = p0.kappa, p0.eta, p0.cfl, 0.0, cell_cap
-        for i, m in enumerate(p0.materials):
-            prm.mat[i].eos, prm.mat[i].gamma, prm.mat[i].rho0 = _EOS[m.eos], m.gamma, m.rho0
-            prm.mat[i].c0, prm.mat[i].p_inf, prm.mat[i].s_a = m.c0, m.p_inf, m.s_a
+        prm.n_mat = len(self.materials)
+        prm.kappa, prm.eta, prm.cfl, prm.cell_beta, prm.cell_cap = p0.kappa, p0.eta, p0.cfl, cell_beta, cell_cap
+        self._mat_arr = (abi.sph_material * len(self.materials))()
+        for i, m in enumerate(self.materials):
+            dst = self._mat_arr[i]
+            dst.eos, dst.gamma, dst.rho0, dst.c0, dst.p_inf, dst.s_a = _EOS[m.eos], m.gamma, m.rho0, m.c0, m.p_inf, m.s_a
+            if i < abi.SPH_MAX_MAT:
+                prm.mat[i] = dst
+        prm.materials = C.cast(self._mat_arr, C.c_void_p) if len(self.materials) > abi.SPH_MAX_MAT else None
         prm.n_units, prm.unit_dim = self.K, self.unit_dim
         prm.n_upd = (p0.n_upd if n_upd is None else n_upd) if self.K > 0 else 0
         prm.theta, prm.sigma, prm.gamma_b, prm.beta_sh = theta, sigma, gamma_b, beta_sh
+        prm.pair_blocks_per_sm = pair_blocks_per_sm
         prm.generators = self.gen.data_ptr() if self.gen is not None else None
         self.params = prm
         self.precision = precision

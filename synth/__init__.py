@@ -152,6 +152,24 @@ def plate_impact_small() -> Problem:
     return plate_impact(25, (120, 120, 13), units=64, n_steps=100)
 
 
+def ensemble(n_inst: int = 256, seed: int = 2018, n_min: int = 5000, n_max: int = 200000,
+             v_range=(500.0, 2000.0), gamma_range=(1.5, 3.0), a: float = 1e-4) -> list:
+    """Independent plate impacts of uneven size: instance b has about N_b
+    particles, N_b log-uniform in [n_min, n_max]; impact speed uniform in
+    v_range, stiffened-gas gamma uniform in gamma_range (rho0 = 2700,
+    c0 = 5300).  Each has the shape of the 1.125M plate (projector p^3 on a
+    4p x 4p x p/2 slab, N = 9 p^3)."""
+    u = uniform(seed, 3 * n_inst).reshape(n_inst, 3)
+    probs = []
+    for b in range(n_inst):
+        nb = n_min * (n_max / n_min) ** u[b, 0]
+        p = max(int(round((nb / 9.0) ** (1.0 / 3.0))), 4)
+        v = v_range[0] + (v_range[1] - v_range[0]) * u[b, 1]
+        g = gamma_range[0] + (gamma_range[1] - gamma_range[0]) * u[b, 2]
+        probs.append(plate_impact(p, (4 * p, 4 * p, max(p // 2, 2)), a=a, v=v, gamma=g, units=0, n_steps=100))
+    return probs
+
+
 # ---------------------------------------------------------------------------
 # Voronoi generator seeding
 # ---------------------------------------------------------------------------
