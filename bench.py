@@ -10,8 +10,13 @@ packing, pair loop, kick) plus, every 10th step, balancing + reassignment +
 renumbering.  Inputs are synthetic (synth.plate_impact_full) and larger than
 L2 (the FP64 state is ~190 MB), so no L2 flush is needed.
 
-Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-on the host cores instead, on a bounded sample of the same workload.
+Prints one JSON line (rank 0).  At one GPU the line also carries "extras"
+(skip with --no-extras): the plain FP64 step against the mixed step on the
+same plate; the 256-instance ensemble (one CUDA graph of 100 steps,
+autotuned) against 256 sequential single-instance runs; and the forward +
+reverse mode of a 203k-particle plate in both precisions.  --impl reference
+times the FP64 CPU oracle on the host cores instead, on a bounded sample of
+the same workload.
 """
 from __future__ import annotations
 
@@ -44,6 +49,7 @@ WORKLOADS = {
 #   per interacting half pair (e^R, v^R, acoustic P*, v*, W', three rate terms for both ends): 70 flops
 FLOP_TEST = 11.0
 FLOP_PAIR = 70.0
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate; the FP64 pair kernel is bound by it
 
 
 def fp32_peak_tflops() -> float:
@@ -255,11 +261,133 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
            "clocks": clk.summary(), "gpu_launches": launches, "device_status": status,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "steps": e2e_steps}}
+    if world == 1 and not args.no_extras:
+        sim.close()
+        out["extras"] = run_extras(args, dev)
     if world == 1 and not args.no_cpu_baseline:
         cval, csec, cn = oracle_sample(args.cpu_steps)
         out["cpu_baseline"] = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
                                "sample": f"plain FP64 C oracle, single thread, full {cn}-particle plate impact, "
                                          f"{args.cpu_steps} steps after one rate evaluation ({csec:.1f} s)"}
+    return out
+
+
+def _fields_rel(a: dict, b: dict, keys) -> dict:
+    out = {}
+    for k in keys:
+        d = np.abs(a[k] - b[k])
+        out[k] = {"max_rel": float(d.max() / max(np.abs(b[k]).max(), 1e-300)),
+                  "l1_rel": float(d.mean() / max(np.abs(b[k]).mean(), 1e-300))}
+    return out
+
+
+def run_extras(args, dev) -> dict:
+    """The other forms on the same GPU, each against the plain FP64 step:
+    precision (FP64 vs mixed step on the benchmark plate, no work units),
+    batching (256-instance ensemble, 100 steps in one CUDA graph, autotuned,
+    vs 256 sequential single-instance runs) and differentiation (forward +
+    reverse mode of a 203k-particle plate, 100 steps, checkpoints every 10)."""
+    import torch
+    import synth
+    from paper_1805_05128_gb300 import Simulation
+    from paper_1805_05128_gb300 import ensemble as ens
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    # (1) precision: same inputs, same number of steps
+    prob = synth.plate_impact(units=0, n_steps=500, **WORKLOADS[args.workload])
+    steps, res, states = 20, {}, {}
+    for prec in ("fp64", "mixed"):
+        sim = Simulation(prob, precision=prec, units=0, device=dev)
+        sim.eval_rates()
+        sim.step(2)
+        torch.cuda.synchronize()
+        sim.profile(True)
+        e0, e1 = ev(), ev()
+        e0.record()
+        sim.step(steps)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        pair_ms, pair_launches, _ = sim.profile_read()
+        half_pairs, candidates, _ = sim.pair_counts()
+        flops = FLOP_PAIR * half_pairs + FLOP_TEST * candidates / 2.0
+        peak = fp32_peak_tflops() if prec == "mixed" else FP64_PEAK_TFLOPS
+        achieved = flops / (pair_ms / max(pair_launches, 1) * 1e-3) / 1e12
+        res[prec] = {"value": prob.n * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                     "pair_ms_per_launch": pair_ms / max(pair_launches, 1),
+                     "pair_roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                       "frac": achieved / peak}}
+        states[prec] = sim.numpy()
+        sim.close()
+    res["fp64"]["pair_roofline"]["peak_note"] = "nominal GB300 FP64 (not measured)"
+    res["mixed_vs_fp64_after_22_steps"] = _fields_rel(states["mixed"], states["fp64"], ("rho", "vz", "E", "z"))
+    res["speedup_mixed_over_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
+    out["precision"] = res
+
+    # (2) batching
+    probs = synth.ensemble()
+    n_tot = sum(q.n for q in probs)
+    tune = ens.autotune(probs, cell_betas=(0.0, 0.15, 0.3), pair_blocks=(3, 0), n_steps=5, reps=1, device=dev)
+    sim, ms_b = ens.run_batched(probs, 100, tuning=tune, device=dev)
+    st_b = sim.read_status()
+    sim.close()
+    sims, ms_s = ens.run_sequential(probs, 100, tuning=tune, device=dev)
+    st_s = max(s.read_status() for s in sims)
+    for s_ in sims:
+        s_.close()
+    out["ensemble"] = {
+        "workload": "256 plate impacts, N log-uniform 5k-200k (seed 2018), v U[0.5,2] km/s, gamma U[1.5,3]",
+        "particles": n_tot, "steps": 100,
+        "batched": {"value": n_tot * 100 / (ms_b * 1e-3), "unit": UNIT, "ms": ms_b,
+                    "form": "one handle, 256 instances, 100 steps in one CUDA graph replay", "status": st_b},
+        "sequential": {"value": n_tot * 100 / (ms_s * 1e-3), "unit": UNIT, "ms": ms_s,
+                       "form": "256 handles, each stepped 100 times eagerly in turn", "status": st_s},
+        "speedup_batched_over_sequential": ms_s / ms_b,
+        "tuning": {"cell_beta": tune.cell_beta, "pair_blocks_per_sm": tune.pair_blocks,
+                   "ms_per_step": {f"{k[0]}/{k[1]}": v for k, v in tune.timings.items()}}}
+
+    # (3) differentiation
+    from paper_1805_05128_gb300.adjoint import RunSpec, csph_run
+    q = synth.plate_impact(25, (120, 120, 13), a=1e-4, v=1000.0, units=0)
+    A = q.arrays
+    pos = torch.tensor(np.stack([A["x"], A["y"], A["z"]], axis=1), dtype=torch.float64, device=dev)
+    proj = torch.tensor(A["vz"] < 0.0, device=dev).double()
+    rear = torch.tensor(A["z"] < 0.5e-4, device=dev)
+    m = torch.tensor(A["m"], dtype=torch.float64, device=dev)
+    rho0, c0v, gv = 2700.0, 5300.0, 2.0
+    adj = {}
+
+    def grad_run(prec, n_steps, every):
+        v = torch.tensor(1000.0, dtype=torch.float64, device=dev, requires_grad=True)
+        c0 = torch.tensor(c0v, dtype=torch.float64, device=dev, requires_grad=True)
+        g = torch.tensor(gv, dtype=torch.float64, device=dev, requires_grad=True)
+        vel = torch.zeros(q.n, 3, dtype=torch.float64, device=dev)
+        vel = vel + torch.stack([torch.zeros_like(m), torch.zeros_like(m), -v * proj], dim=1)
+        rho = torch.full((q.n,), rho0, dtype=torch.float64, device=dev)
+        E = c0 * c0 / (g - 1.0) + 0.5 * vel[:, 2] ** 2
+        spec = RunSpec(m=m, n_steps=n_steps, every=every, precision=prec, rho0=rho0)
+        torch.cuda.synchronize()
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record()
+        _, v1, _, _ = csph_run(pos, vel, rho, E, c0, g, spec)
+        loss = v1[rear, 2].mean()
+        e1.record()
+        loss.backward()
+        e2.record()
+        e2.synchronize()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2), [v.grad.item(), c0.grad.item(), g.grad.item()]
+
+    for prec in ("fp64", "mixed"):
+        grad_run(prec, 10, 5)                      # warm-up: first-use costs of the reverse path
+        fwd, bwd, grad = grad_run(prec, 100, 10)
+        adj[prec] = {"forward_ms": fwd, "backward_ms": bwd,
+                     "value": q.n * 100 / ((fwd + bwd) * 1e-3), "unit": UNIT + " (forward + reverse)",
+                     "grad": grad}
+    gm, g64 = np.array(adj["mixed"]["grad"]), np.array(adj["fp64"]["grad"])
+    adj["mixed_vs_fp64_grad_max_rel"] = float(np.max(np.abs(gm - g64) / np.abs(g64)))
+    adj["workload"] = f"plate impact {q.n} particles, 100 steps, checkpoints every 10, d(rear-face v_z)/d(v, c0, gamma)"
+    out["adjoint"] = adj
     return out
 
 
@@ -296,6 +424,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64-step, batched-ensemble and adjoint measurements")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

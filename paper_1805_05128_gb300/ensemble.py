@@ -48,6 +48,18 @@ class GraphRun:
         self.graph.replay()
 
 
+def cell_cap(problems) -> int:
+    """Mesh capacity for a set of plate-like instances: one cell per particle
+    (at least 4096) per instance, several times what their meshes use."""
+    return int(sum(max(4096, len(q.arrays["x"])) for q in problems))
+
+
+def _kw(problems, sim_kw: dict) -> dict:
+    kw = dict(sim_kw)
+    kw.setdefault("cell_cap", cell_cap(problems))
+    return kw
+
+
 def time_steps(sim: Simulation, n_steps: int, reps: int = 2) -> float:
     """Milliseconds per step of a graph of n_steps steps (best of reps)."""
     sim.eval_rates()
@@ -71,7 +83,8 @@ def autotune(problems, precision: str = "mixed", cell_betas=(0.0, 0.15, 0.3), pa
     means as many CTAs per SM as fit."""
     best, table = None, {}
     for cb, pb in itertools.product(cell_betas, pair_blocks):
-        sim = Simulation(problems, precision=precision, units=0, cell_beta=cb, pair_blocks_per_sm=pb, **sim_kw)
+        sim = Simulation(problems, precision=precision, units=0, cell_beta=cb, pair_blocks_per_sm=pb,
+                         **_kw(problems, sim_kw))
         try:
             ms = time_steps(sim, n_steps, reps)
             status = sim.read_status()
@@ -94,7 +107,7 @@ def run_batched(problems, n_steps: int, tuning: Tuning | None = None, precision:
     replay's device time in ms."""
     t = tuning or Tuning()
     sim = Simulation(problems, precision=precision, units=0, cell_beta=t.cell_beta,
-                     pair_blocks_per_sm=t.pair_blocks, **sim_kw)
+                     pair_blocks_per_sm=t.pair_blocks, **_kw(problems, sim_kw))
     sim.eval_rates()
     g = GraphRun(sim, n_steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -112,7 +125,7 @@ def run_sequential(problems, n_steps: int, tuning: Tuning | None = None, precisi
     simulations and the device time of all the steps in ms."""
     t = tuning or Tuning()
     sims = [Simulation(q, precision=precision, units=0, cell_beta=t.cell_beta, pair_blocks_per_sm=t.pair_blocks,
-                       **sim_kw) for q in problems]
+                       **_kw([q], sim_kw)) for q in problems]
     for s in sims:
         s.eval_rates()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
