@@ -8,6 +8,9 @@ CSPHRun.apply(pos, vel, rho, E, c0, gamma, spec) -> (pos, vel, rho, E)
   parameters of material 0; spec: RunSpec (fixed problem data).
 The time steps of the forward run are recorded and held fixed in the
 backward pass (dt is a stop-gradient), as is the pair set of each step.
+spec.precision sets both passes: "mixed" runs the pair fluxes and the pair
+derivatives in FP32 (Kahan sums), "fp64" runs both in FP64; the chain through
+the EOS and the kick-drift-kick algebra is FP64 in both.
 """
 from __future__ import annotations
 

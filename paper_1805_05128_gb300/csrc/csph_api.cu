@@ -41,7 +41,7 @@ void free_all(sph_handle* h) {
                   h->inst_cap, h->total_cells, h->cell_count, h->cell_start, h->scan_sums, h->cell_of, h->rank,
                   h->perm, h->slot_cell, h->slot_unit, h->packA, h->packB, h->packC, h->rho_slot, h->dmax_nbr,
                   h->load_acc, h->adj_bits, h->unit_off, h->unit_list, h->unit_work, h->unit_total, h->unit_stats,
-                  h->status, h->counters, h->scratch, h->adj_A, h->adj_B, h->adj_C, h->adj_rho, h->adj_G,
+                  h->status, h->counters, h->scratch, h->adj_G,
                   h->adj_GR, h->adj_pair, h->adj_par, h->adj_W, h->adj_store, h->mat_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -552,11 +552,7 @@ int sph_step_adjoint(sph_handle* h, const sph_ckpt* ck, int n_steps, const sph_s
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
   const int64_t n = h->n;
-  if (!h->adj_A) {
-    CK(h, dalloc(&h->adj_A, n));
-    CK(h, dalloc(&h->adj_B, n));
-    CK(h, dalloc(&h->adj_C, n));
-    CK(h, dalloc(&h->adj_rho, n));
+  if (!h->adj_G) {
     CK(h, dalloc(&h->adj_G, n));
     CK(h, dalloc(&h->adj_GR, n));
     CK(h, dalloc(&h->adj_pair, (size_t)11 * n));
@@ -589,7 +585,7 @@ int sph_step_adjoint(sph_handle* h, const sph_ckpt* ck, int n_steps, const sph_s
     CK(h, cudaMemcpyAsync(h->dt, ck->dt + k, sizeof(double), cudaMemcpyDeviceToDevice, st));
     CK(h, launch_kick_drift(h, W, st));
     CK(h, launch_build_grid(h, W, st));
-    CK(h, launch_pack_fp64(h, W, true, h->adj_A, h->adj_B, h->adj_C, h->adj_rho, st));
+    CK(h, launch_pack(h, W, true, st));
     CK(h, launch_rates_vjp(h, W, *adj_in, ck->dt + k, 1, adj_params, st));
   }
   if (ck->rates_from_state) {
@@ -597,7 +593,7 @@ int sph_step_adjoint(sph_handle* h, const sph_ckpt* ck, int n_steps, const sph_s
     CK(h, copy_dynamic(W, ck->state, n, st));
     CK(h, launch_derive_dt(h, W, true, st));
     CK(h, launch_build_grid(h, W, st));
-    CK(h, launch_pack_fp64(h, W, false, h->adj_A, h->adj_B, h->adj_C, h->adj_rho, st));
+    CK(h, launch_pack(h, W, false, st));
     CK(h, launch_rates_vjp(h, W, *adj_in, h->dt, 0, adj_params, st));
   }
   return SPH_OK;

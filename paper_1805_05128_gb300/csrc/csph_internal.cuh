@@ -141,12 +141,8 @@ struct sph_handle {
   size_t scratch_bytes = 0;
 
   // reverse mode (sph_step_adjoint), allocated on first use
-  csph::D4* adj_A = nullptr;          // FP64 operands of the predicted state, slot order
-  csph::D4* adj_B = nullptr;
-  csph::D2* adj_C = nullptr;
-  double* adj_rho = nullptr;
-  csph::D4* adj_G = nullptr;          // rate adjoints / m, slot order
-  double* adj_GR = nullptr;
+  csph::D4* adj_G = nullptr;          // rate adjoints / m, slot order (float4 in mixed mode)
+  csph::D2* adj_GR = nullptr;         // (dL/ddrho, rho) of the slot (float2 in mixed mode)
   double* adj_pair = nullptr;         // 11 per particle: own-side pair derivatives
   double* adj_par = nullptr;          // 2 per particle: parameter derivatives
   double* adj_W = nullptr;            // working state, 16 arrays of n
@@ -237,10 +233,7 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
 cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st);
 cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st);
 cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st);
-// k_pack's FP64 variant writing into the given operand arrays (reverse mode)
-cudaError_t launch_pack_fp64(sph_handle* h, const sph_state& s, bool predict, void* A, void* B, void* C,
-                             double* rho_out, cudaStream_t st);
-// rates VJP at the packed state (k_adjoint.cu)
+// rates VJP at the state packed by launch_pack (k_adjoint.cu)
 cudaError_t launch_rates_vjp(sph_handle* h, const sph_state& W, sph_state& adj, const double* dt, int predicted,
                              double* par, cudaStream_t st);
 // Exclusive scan of cnt[0, *total) into start[0, *total], start[*total] = n_total;
@@ -250,6 +243,8 @@ cudaError_t launch_exclusive_scan(int32_t* cnt, const int64_t* total, int32_t* s
 cudaError_t launch_conservation(sph_handle* h, const sph_state& s, double* out, cudaStream_t st);
 cudaError_t launch_check_finite(sph_handle* h, const sph_state& s, cudaStream_t st);
 cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st);
+cudaError_t launch_pair_vjp(sph_handle* h, const sph_state& s, const void* G, const void* GR2, double* out,
+                            cudaStream_t st);
 cudaError_t launch_assign(sph_handle* h, const sph_state& s, const double* gen, int K, int dim,
                           int32_t* unit_out, cudaStream_t st);
 cudaError_t launch_unit_lists(sph_handle* h, const int32_t* unit, int32_t* unit_offsets, cudaStream_t st);

@@ -63,6 +63,12 @@ struct PairArgs {
   float kh_f, eta_half_f, kappa_f;
   double eta_half, kappa;
   int kernel;
+  // reverse mode (k_pair<..., VJP = true>): adjoint operands in slot order,
+  // G = ((dL/da)/m, (dL/ddE)/m), GR2 = (dL/ddrho, rho), and the 11 own-side
+  // derivatives per particle (particle order) it writes
+  const void* G;
+  const void* GR2;
+  double* vjp_out;
 };
 
 template <bool MIXED>
@@ -158,6 +164,25 @@ __device__ __forceinline__ T dw_fast(int kernel, T kappa, T r, T h) {
   }
 }
 
+// Cubic spline W'(r, h) = s h^-(D+1) g(q) and its derivatives
+// dW'/dr = s h^-(D+2) g'(q), dW'/dh = s h^-(D+2) (-(D+1) g - q g'), q = r/h.
+template <typename T, int DIM>
+__device__ __forceinline__ void cubic_dw3(T r, T h, T& w, T& wr, T& wh) {
+  const T ih = rcp_(h);
+  const T q = r * ih;
+  T norm;
+  if (DIM == 1) norm = T(2.0 / 3.0) * ih * ih;
+  else if (DIM == 2) norm = T(10.0 / (7.0 * 3.14159265358979323846)) * ih * ih * ih;
+  else norm = T(1.0 / 3.14159265358979323846) * (ih * ih) * (ih * ih);
+  const T t = T(2) - q;
+  const T g = q < T(1) ? q * (T(2.25) * q - T(3)) : (q < T(2) ? T(-0.75) * t * t : T(0));
+  const T gp = q < T(1) ? T(4.5) * q - T(3) : (q < T(2) ? T(1.5) * t : T(0));
+  w = norm * g;
+  const T nh = norm * ih;
+  wr = nh * gp;
+  wh = nh * (T(-(DIM + 1)) * g - q * gp);
+}
+
 template <bool MIXED, int DIM>
 struct Pair {
   using T = typename Ops<MIXED>::T;
@@ -212,8 +237,8 @@ struct Pair {
 constexpr int kWarps = kPairBlock / 32;
 constexpr int kRow = kListCap + 2;   // padded row stride (16-bit entries): lane rows fall in distinct banks
 
-template <bool MIXED, int DIM>
-__global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair(PairArgs a) {
+template <bool MIXED, int DIM, bool VJP>
+__global__ void __launch_bounds__(kPairBlock, VJP ? (MIXED ? 4 : 2) : (MIXED ? 6 : 4)) k_pair(PairArgs a) {
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
   using V4 = typename P::V4;
@@ -283,6 +308,13 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair(PairArgs a) 
     Kahan<T> s_rho, s_fx, s_fy, s_fz, s_q;
     const V4 Bi = B[ii];
     const V2 Ci = C[ii];
+    // reverse mode: i's adjoint operands and the 11 own-side sums
+    const V4* __restrict__ Gp = reinterpret_cast<const V4*>(a.G);
+    const V2* __restrict__ Rp = reinterpret_cast<const V2*>(a.GR2);
+    V4 Gi{};
+    V2 Ri{};
+    if constexpr (VJP) { Gi = Gp[ii]; Ri = Rp[ii]; }
+    Kahan<T> s_bx[3], s_bv[3], s_bP, s_bZ, s_bV, s_bd, s_brho;
 
     // Flux of the interacting pair (i, j) from i's side.  Every quantity
     // that j computes for the same pair is the exact negative (e^R, v^R, v*,
@@ -353,13 +385,101 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair(PairArgs a) 
       }
     };
 
+    // Reverse mode of the pair's contributions (VJP = true): the derivative of
+    // the pair's terms in a, drho, dE of both i and j, contracted with their
+    // adjoints, with respect to i's own variables: position (through r, e and
+    // W'), v (through v^R), P and Z = rho c (through the acoustic solver),
+    // V = m/rho, d (through h_ij) and the rho factor of the continuity term.
+    auto pair_vjp = [&](int64_t j, int ox, int oy, int oz) {
+      if (j == i) return;
+      const V4 Aj = A[j];
+      const V4 Bj = B[j];
+      const V2 Cj = C[j];
+      const V4 Gj = Gp[j];
+      const V2 Rj = Rp[j];
+      T dx, dy, dz;
+      if (MIXED) {
+        dx = (Aj.x - Ai.x) + ox * dcs;
+        dy = DIM >= 2 ? (Aj.y - Ai.y) + oy * dcs : T(0);
+        dz = DIM >= 3 ? (Aj.z - Ai.z) + oz * dcs : T(0);
+      } else {
+        dx = __dsub_rn(Aj.x, Ai.x);
+        dy = DIM >= 2 ? __dsub_rn(Aj.y, Ai.y) : 0.0;
+        dz = DIM >= 3 ? __dsub_rn(Aj.z, Ai.z) : 0.0;
+      }
+      const T r2 = P::r2_of(dx, dy, dz);
+      if (!(r2 > T(0))) return;
+      const T ir = rsqrt_(r2);
+      const T r = r2 * ir;
+      const T e[3] = {dx * ir, dy * ir, dz * ir};
+      const T vi[3] = {Bi.x, Bi.y, Bi.z}, vj[3] = {Bj.x, Bj.y, Bj.z};
+      T vRi = T(0), vRj = T(0);
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) { vRi += vi[q] * e[q]; vRj += vj[q] * e[q]; }
+      const T Zi = Ci.y, Zj = Cj.y, zs = Zi + Zj, Pi = Ci.x, Pj = Cj.x;
+      T Ps, vs, izs = T(0);
+      if (zs > T(0)) {
+        izs = rcp_(zs);
+        Ps = (Zj * Pi + Zi * Pj + Zi * Zj * (vRi - vRj)) * izs;
+        vs = (Zi * vRi + Zj * vRj + Pi - Pj) * izs;
+      } else {
+        Ps = T(0.5) * (Pi + Pj);
+        vs = T(0.5) * (vRi + vRj);
+      }
+      const T eh = MIXED ? (T)a.eta_half_f : (T)a.eta_half;
+      const T hij = eh * (Ai.w + Aj.w);
+      T W, Wr, Wh;
+      cubic_dw3<T, DIM>(r, hij, W, Wr, Wh);
+      const T Vi = Bi.w, Vj = Bj.w, GRi = Ri.x, rhoi = Ri.y, GRj = Rj.x, rhoj = Rj.y;
+      const T F = T(2) * Vi * Vj * Ps * W;
+      const T dA[3] = {Gi.x - Gj.x, Gi.y - Gj.y, Gi.z - Gj.z};
+      const T dB = Gi.w - Gj.w;
+      T gF = dB * vs, ge[3] = {T(0), T(0), T(0)};
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) { gF += dA[q] * e[q]; ge[q] = F * dA[q]; }
+      const T ti = T(2) * W * rhoi * Vj * GRi;          // continuity terms of i and of j
+      const T tj = T(2) * W * rhoj * Vi * GRj;
+      const T gvs = F * dB + ti - tj;
+      T gvRi = -ti, gvRj = tj;
+      const T gW = gF * T(2) * Vi * Vj * Ps - GRi * T(2) * rhoi * Vj * (vRi - vs) - GRj * T(2) * rhoj * Vi * (vs - vRj);
+      const T gPs = gF * T(2) * Vi * Vj * W;
+      s_bV.add(gF * T(2) * Vj * Ps * W - GRj * T(2) * rhoj * (vs - vRj) * W);
+      s_brho.add(-(GRi * T(2) * Vj * (vRi - vs) * W));
+      T gPi, gZi = T(0);
+      if (zs > T(0)) {
+        gPi = (gPs * Zj + gvs) * izs;
+        gvRi += (gPs * Zi * Zj + gvs * Zi) * izs;
+        gvRj += (gvs * Zj - gPs * Zi * Zj) * izs;
+        gZi = (gPs * ((Pj + Zj * (vRi - vRj)) - Ps) + gvs * (vRi - vs)) * izs;
+      } else {
+        gPi = T(0.5) * gPs;
+        gvRi += T(0.5) * gvs;
+        gvRj += T(0.5) * gvs;
+      }
+      s_bP.add(gPi);
+      s_bZ.add(gZi);
+      T ede = T(0);
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) {
+        s_bv[q].add(gvRi * e[q]);
+        ge[q] += gvRi * vi[q] + gvRj * vj[q];
+        ede += ge[q] * e[q];
+      }
+      const T grr = gW * Wr;
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) s_bx[q].add(-((ge[q] - ede * e[q]) * ir + grr * e[q]));
+      s_bd.add(gW * Wh * eh);
+    };
+
     auto flush = [&]() {
       nfull += (unsigned)cnt;
       for (int k = 0; k < cnt; ++k) {
         const unsigned ent = list[warp][lane][k];
         const int code = ent >> 11;
         const int oz = code / 9, oy = (code - 9 * oz) / 3, ox = code - 9 * oz - 3 * oy;
-        pair_flux((int64_t)nb_start[warp][code] + (ent & 2047u), ox - 1, oy - 1, oz - 1);
+        const int64_t j = (int64_t)nb_start[warp][code] + (ent & 2047u);
+        if constexpr (VJP) pair_vjp(j, ox - 1, oy - 1, oz - 1);
+        else pair_flux(j, ox - 1, oy - 1, oz - 1);
       }
       cnt = 0;
     };
@@ -428,6 +548,20 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair(PairArgs a) 
     }
     if (act) flush();
 
+    if constexpr (VJP) {
+      if (act) {
+        double* o = a.vjp_out + 11 * (int64_t)a.perm[i];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) { o[q] = (double)s_bx[q].s; o[3 + q] = (double)s_bv[q].s; }
+        o[6] = (double)s_bP.s;
+        o[7] = (double)s_bZ.s;
+        o[8] = (double)s_bV.s;
+        o[9] = (double)s_bd.s;
+        o[10] = (double)s_brho.s;
+      }
+      __syncwarp();
+      continue;
+    }
     if (act) {
       nfull -= 1;   // the self pair
       const int64_t p = a.perm[i];
@@ -464,35 +598,33 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair(PairArgs a) 
 
 // Persistent grid: SMs x resident CTAs per SM, capped by the handle's
 // pair_blocks_per_sm (0 = as many as fit).
-template <bool MIXED, int DIM>
+template <bool MIXED, int DIM, bool VJP>
 cudaError_t launch_one(const PairArgs& args, int blocks_per_sm, cudaStream_t st) {
   static int sms = 0, per_sm = 0;
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<MIXED, DIM>, kPairBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<MIXED, DIM, VJP>, kPairBlock, 0);
     if (per_sm < 1) per_sm = 1;
   }
   const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
-  k_pair<MIXED, DIM><<<sms * b, kPairBlock, 0, st>>>(args);
+  k_pair<MIXED, DIM, VJP><<<sms * b, kPairBlock, 0, st>>>(args);
   return cudaGetLastError();
 }
 
-template <bool MIXED>
+template <bool MIXED, bool VJP>
 cudaError_t launch_dim(sph_handle* h, const PairArgs& args, cudaStream_t st) {
   const int b = h->p.pair_blocks_per_sm;
   switch (h->dp.dim) {
-    case 1: return launch_one<MIXED, 1>(args, b, st);
-    case 2: return launch_one<MIXED, 2>(args, b, st);
-    default: return launch_one<MIXED, 3>(args, b, st);
+    case 1: return launch_one<MIXED, 1, VJP>(args, b, st);
+    case 2: return launch_one<MIXED, 2, VJP>(args, b, st);
+    default: return launch_one<MIXED, 3, VJP>(args, b, st);
   }
 }
 
-}  // namespace
-
-cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st) {
-  PairArgs a;
+PairArgs make_args(sph_handle* h, const sph_state& s) {
+  PairArgs a{};
   a.n = h->n;
   a.total_cells_dev = h->total_cells;
   a.total_cells = 0;
@@ -528,6 +660,32 @@ cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st) {
   a.kappa = h->dp.kappa;
   a.kappa_f = (float)h->dp.kappa;
   a.kernel = h->dp.kernel;
+  return a;
+}
+
+}  // namespace
+
+// Reverse mode over the same pair set: the mesh and packs of the state s
+// (k_pack of the handle's precision) and the adjoint operands G, GR2 (slot
+// order, same precision) must be in place; writes 11 doubles per particle.
+cudaError_t launch_pair_vjp(sph_handle* h, const sph_state& s, const void* G, const void* GR2, double* out,
+                            cudaStream_t st) {
+  PairArgs a = make_args(h, s);
+  a.K = 0;
+  a.collect_adj = 0;
+  a.pair_i = a.pair_j = nullptr;
+  a.G = G;
+  a.GR2 = GR2;
+  a.vjp_out = out;
+  cudaError_t e = cudaMemsetAsync(&h->counters[5], 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, true>(h, a, st) : launch_dim<false, true>(h, a, st);
+  h->launches += 1;
+  return e;
+}
+
+cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st) {
+  PairArgs a = make_args(h, s);
   cudaError_t e = cudaMemsetAsync(h->counters, 0, 3 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(&h->counters[4], 0, 2 * sizeof(unsigned long long), st);
@@ -547,7 +705,7 @@ cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st) {
     e = cudaEventRecord(e0, st);
     if (e != cudaSuccess) return e;
   }
-  e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true>(h, a, st) : launch_dim<false>(h, a, st);
+  e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, false>(h, a, st) : launch_dim<false, false>(h, a, st);
   h->launches += 1;
   if (e == cudaSuccess && h->profiling) e = cudaEventRecord(e1, st);
   return e;
