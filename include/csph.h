@@ -70,7 +70,8 @@ typedef struct sph_params {
   double kappa;       /* kernel support in units of h */
   double eta;         /* h_ij = eta (d_i + d_j)/2, eq. (SmoothingLengthDef) times eta */
   double cfl;         /* dt = cfl min_i eta d_i / (c_i + |v_i|) */
-  double cell_beta;   /* beta of eq. (Dcell); 0 = cells rebuilt every step */
+  double cell_beta;   /* beta of eq. (Dcell); 0 = mesh and pairs found every step; > 0 = Verlet
+                         lists over (1 + beta) kappa h_ij reused across steps (sph_list_builds) */
   int64_t cell_cap;   /* maximum cells of the dense mesh over all instances */
   sph_material mat[SPH_MAX_MAT];
   /* Voronoi work units (VD3).  n_units = 0 disables them. */
@@ -236,6 +237,17 @@ const char* sph_last_error(const sph_handle* h);
  * evaluation, candidates tested, and pairs decided by the FP64 fallback. */
 int sph_pair_counts(sph_handle* h, int64_t* half_pairs, int64_t* candidates, int64_t* fp64_checks,
                     void* stream);
+
+/* Verlet lists (cell_beta = beta > 0; the pair list with buffer beta of
+ * Sec. 4.2, reused over several steps): *builds = number of list builds since
+ * sph_init, *capacity = list entries held per particle.  sph_step keeps the
+ * mesh, the slot order and the lists while every particle satisfies
+ * |x - x_b| + kh max(0, d - d_b) <= 0.95 beta kh d_b (x_b, d_b at the last
+ * build, kh = kappa eta / 2), which keeps every pair within kappa h_ij listed,
+ * and rebuilds them otherwise (decided on the device), as well as after any
+ * call that rebuilds the mesh or renumbers.  Synchronises the stream.
+ * Errors: SPH_ERR_INVALID if the handle has no lists (cell_beta = 0). */
+int sph_list_builds(sph_handle* h, int64_t* builds, int32_t* capacity, void* stream);
 
 /* Inspection of the neighbour search (Sec. 4.2) at the current state,
  * for verification: derives d, builds the cell mesh of eq. (Dcell) and

@@ -25,7 +25,7 @@ ERROR_NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID", 2: "SPH_ERR_CAPACITY", 3: "SPH
 EXPORTS = ("sph_init", "sph_build_cells", "sph_eval_rates", "sph_step", "voronoi_assign", "voronoi_balance",
            "sph_conservation", "sph_unit_stats", "sph_read_status", "sph_last_error", "sph_pair_counts",
            "sph_cell_index", "sph_pair_list", "voronoi_assign_static", "sph_profile", "sph_profile_read",
-           "sph_step_adjoint", "sph_last_dt", "sph_step_dt", "sph_destroy")
+           "sph_step_adjoint", "sph_last_dt", "sph_step_dt", "sph_list_builds", "sph_destroy")
 
 
 class sph_material(C.Structure):
@@ -94,6 +94,7 @@ def lib() -> C.CDLL:
     L.sph_step_adjoint.argtypes = [vp, C.POINTER(sph_ckpt), i32, C.POINTER(sph_state), C.POINTER(sph_state), vp, vp]
     L.sph_last_dt.argtypes = [vp, vp, vp]
     L.sph_step_dt.argtypes = [vp, C.POINTER(sph_state), i32, vp, vp, vp]
+    L.sph_list_builds.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32), vp]
     L.sph_profile.argtypes = [vp, i32]
     L.sph_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.sph_destroy.argtypes = [vp]
@@ -170,6 +171,13 @@ def sph_pair_counts(h, stream):
     a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
     check(lib().sph_pair_counts(h, C.byref(a), C.byref(b), C.byref(c), C.c_void_p(stream)), h)
     return a.value, b.value, c.value
+
+
+def sph_list_builds(h, stream):
+    """(Verlet-list builds since sph_init, list capacity per particle)."""
+    b, c = C.c_int64(), C.c_int32()
+    check(lib().sph_list_builds(h, C.byref(b), C.byref(c), C.c_void_p(stream)), h)
+    return b.value, c.value
 
 
 def sph_cell_index(h, state, cell_out_ptr, grid_out, stream):

@@ -42,7 +42,8 @@ void free_all(sph_handle* h) {
                   h->perm, h->slot_cell, h->slot_unit, h->packA, h->packB, h->packC, h->rho_slot, h->dmax_nbr,
                   h->load_acc, h->adj_bits, h->unit_off, h->unit_list, h->unit_work, h->unit_total, h->unit_stats,
                   h->status, h->counters, h->scratch, h->adj_G,
-                  h->adj_GR, h->adj_pair, h->adj_par, h->adj_W, h->adj_store, h->mat_dev};
+                  h->adj_GR, h->adj_pair, h->adj_par, h->adj_W, h->adj_store, h->mat_dev, h->vlist, h->vcnt,
+                  h->vref, h->vflag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -153,6 +154,8 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   dp.dim = p->dim; dp.kernel = p->kernel; dp.precision = p->precision; dp.n_mat = p->n_mat;
   dp.kappa = p->kappa; dp.eta = p->eta; dp.cfl = p->cfl; dp.cell_beta = p->cell_beta;
   dp.kh = (0.5 * p->kappa) * p->eta;
+  dp.n = s->n;
+  dp.vref = nullptr;
   for (int k = 0; k < p->n_mat; ++k) {
     const sph_material& m = mats[k];
     h->mat_h.push_back(Mat{m.eos, m.gamma, m.rho0, m.c0, m.p_inf, m.s_a});
@@ -263,6 +266,29 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     CKI(dalloc(&h->unit_stats, (size_t)K * 5));
   }
 
+  // Verlet lists (cell_beta > 0): capacity per particle from the neighbours of a uniform
+  // lattice within (1 + beta) kappa eta spacings, with a margin for non-uniform spacing
+  h->verlet = p->cell_beta > 0.0;
+  if (h->verlet) {
+    if (n >= (int64_t(1) << 27)) {
+      fail(h, SPH_ERR_INVALID, "Verlet lists (cell_beta > 0) hold at most 2^27 - 1 particles");
+      return bail(SPH_ERR_INVALID);
+    }
+    const double rr = p->kappa * p->eta * (1.0 + p->cell_beta);
+    const double pi = 3.14159265358979323846;
+    const double vol = p->dim == 1 ? 2.0 * rr : (p->dim == 2 ? pi * rr * rr : 4.0 / 3.0 * pi * rr * rr * rr);
+    const double cap = std::ceil((p->dim == 3 ? 2.0 : 3.0) * vol + 32.0);
+    h->vcap = (int)std::min(65536.0, std::ceil(cap / 32.0) * 32.0);
+    CKI(dalloc(&h->vlist, (size_t)h->vcap * n));
+    CKI(dalloc(&h->vcnt, n));
+    CKI(dalloc(&h->vref, (size_t)4 * n));
+    CKI(cudaMemset(h->vref, 0, sizeof(double) * 4 * n));
+    CKI(dalloc(&h->vflag, 4));
+    const int flags[4] = {1, 1, 0, 0};    // lists invalid until the first build
+    CKI(cudaMemcpy(h->vflag, flags, sizeof(flags), cudaMemcpyHostToDevice));
+    dp.vref = h->vref;
+  }
+
   CKI(launch_check_finite(h, *s, st));
   int status = 0;
   CKI(cudaStreamSynchronize(st));
@@ -311,11 +337,23 @@ int sph_step(sph_handle* h, sph_state* s, int n_steps, double* t_dev, void* stre
     CK(h, launch_derive_dt(h, *s, false, st));
     CK(h, launch_reduce_dt(h, st));
     CK(h, launch_kick_drift(h, *s, st));
-    CK(h, launch_build_grid(h, *s, st));
+    if (h->verlet) {
+      // Verlet lists: the mesh, slot order and lists are rebuilt only when the device flag
+      // says so (validity criterion failed or lists invalidated); the kernels read the flag
+      CK(h, launch_verlet_flag(h, st));
+      CK(h, launch_build_grid(h, *s, st, h->vflag));
+    } else {
+      CK(h, launch_build_grid(h, *s, st));
+    }
     CK(h, launch_pack(h, *s, true, st));
     // unit adjacency is needed only from the evaluation that precedes a rebalance
     h->collect_adj = !vd3 || h->steps_since_balance + 1 >= h->p.n_upd;
-    CK(h, launch_pair(h, *s, st));
+    if (h->verlet) {
+      CK(h, launch_list_build(h, *s, st));
+      CK(h, launch_pair_lists(h, *s, st));
+    } else {
+      CK(h, launch_pair(h, *s, st));
+    }
     h->collect_adj = true;
     CK(h, launch_kick2(h, *s, t_dev, st));
     if (vd3 && ++h->steps_since_balance >= h->p.n_upd) {
@@ -424,6 +462,18 @@ int sph_pair_counts(sph_handle* h, int64_t* half_pairs, int64_t* candidates, int
   if (half_pairs) *half_pairs = (int64_t)(c[0] / 2);
   if (candidates) *candidates = (int64_t)c[1];
   if (fp64_checks) *fp64_checks = (int64_t)c[2];
+  return SPH_OK;
+}
+
+int sph_list_builds(sph_handle* h, int64_t* builds, int32_t* capacity, void* stream) {
+  if (!h) return SPH_ERR_INVALID;
+  if (!h->verlet) return fail(h, SPH_ERR_INVALID, "the handle keeps no Verlet lists (cell_beta = 0)");
+  int f[4];
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(h, cudaMemcpyAsync(f, h->vflag, sizeof(f), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  if (builds) *builds = f[2];
+  if (capacity) *capacity = h->vcap;
   return SPH_OK;
 }
 

@@ -38,7 +38,7 @@ struct BlockPart {
   long long lo[3], hi[3];  // bounding box
   long long d1, d2;        // two largest particle sizes
   long long dtmin;         // min_i eta d_i / (c_i + |v_i|)
-  long long pad;
+  long long viol;          // Verlet lists: max_i of the validity criterion (> 0: rebuild)
 };
 
 // Material constants on the device.
@@ -51,6 +51,8 @@ struct DevParams {
   int dim, kernel, precision, n_mat;
   double kappa, eta, cfl, cell_beta, kh;  // kh = (0.5 kappa) eta
   const Mat* mat;                         // device table of n_mat materials
+  const double* vref;                     // Verlet lists: x, y, z, d at the last build (4 arrays of n), or NULL
+  int64_t n;                              // particles of the handle (stride of vref)
 };
 constexpr int kMaxMaterials = 65536;
 
@@ -148,6 +150,17 @@ struct sph_handle {
   double* adj_W = nullptr;            // working state, 16 arrays of n
   double* adj_store = nullptr;        // replayed states, 13 arrays of n per step
   int adj_store_steps = 0;
+
+  // Verlet lists (cell_beta > 0): every pair within (1 + beta) kappa h_ij at the
+  // last build, in slot order, reused by sph_step while the validity criterion
+  // holds for every particle (displacement plus size growth since the build
+  // within the buffer); the mesh, slot order and lists are rebuilt otherwise.
+  bool verlet = false;
+  int vcap = 0;                       // list capacity per particle
+  uint32_t* vlist = nullptr;          // [n][vcap]: entry k of slot i at i vcap + k = (slot j << 5) | cell code
+  int32_t* vcnt = nullptr;            // [n] entries of slot i
+  double* vref = nullptr;             // [4 n] x, y, z, d of each particle at the last build
+  int* vflag = nullptr;               // [0]: rebuild in this step; [1]: lists invalid; [2]: builds done
 };
 
 namespace csph {
@@ -229,7 +242,9 @@ void set_global_error(const std::string& msg);
 cudaError_t launch_derive_dt(sph_handle* h, const sph_state& s, bool with_bbox, cudaStream_t st);
 cudaError_t launch_reduce_dt(sph_handle* h, cudaStream_t st);
 cudaError_t launch_kick_drift(sph_handle* h, const sph_state& s, cudaStream_t st);
-cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st);
+// gate (Verlet mode): device flag, the mesh kernels return at once while gate[0] == 0
+cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st, const int* gate = nullptr);
+cudaError_t launch_verlet_flag(sph_handle* h, cudaStream_t st);
 cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st);
 cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st);
 cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st);
@@ -245,6 +260,10 @@ cudaError_t launch_check_finite(sph_handle* h, const sph_state& s, cudaStream_t 
 cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st);
 cudaError_t launch_pair_vjp(sph_handle* h, const sph_state& s, const void* G, const void* GR2, double* out,
                             cudaStream_t st);
+// Verlet lists: build (k_pair over the (1 + beta) radius, returns at once unless vflag[0]) and
+// the pair evaluation over the lists
+cudaError_t launch_list_build(sph_handle* h, const sph_state& s, cudaStream_t st);
+cudaError_t launch_pair_lists(sph_handle* h, const sph_state& s, cudaStream_t st);
 cudaError_t launch_assign(sph_handle* h, const sph_state& s, const double* gen, int K, int dim,
                           int32_t* unit_out, cudaStream_t st);
 cudaError_t launch_unit_lists(sph_handle* h, const int32_t* unit, int32_t* unit_offsets, cudaStream_t st);

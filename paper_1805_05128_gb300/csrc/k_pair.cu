@@ -69,7 +69,17 @@ struct PairArgs {
   const void* G;
   const void* GR2;
   double* vjp_out;
+  // Verlet lists (k_pair in list mode writes them, k_pair_lists reads them)
+  uint32_t* vlist;   // [n][vcap]: (slot j << 5) | neighbour-cell code, particle-major
+  int32_t* vcnt;
+  double* vref;      // x, y, z, d per particle at the build (4 arrays of n)
+  int* vflag;        // [0] rebuild now, [1] lists invalid, [2] builds done
+  int vcap;
 };
+
+constexpr int kModeFwd = 0;    // rates
+constexpr int kModeVjp = 1;    // reverse mode of the rates
+constexpr int kModeList = 2;   // Verlet list build over the (1 + beta) radius
 
 template <bool MIXED>
 struct Ops;
@@ -221,6 +231,123 @@ struct Pair {
   }
 };
 
+// Flux of the interacting pair (i, j) from i's side.  Every quantity
+// that j computes for the same pair is the exact negative (e^R, v^R, v*,
+// momentum and energy fluxes) or the exact same value (r, P*, h_ij, W'):
+// dx = (off_j - off_i) + shift is the rounded negative of j's
+// (off_i - off_j) - shift, IEEE rounding is sign-symmetric, and the sums
+// that mix i and j are written with uncontracted operations in an order
+// that is symmetric under the exchange.  So the applied fluxes are
+// antisymmetric bit for bit and momentum and energy are conserved by the
+// pair sums up to the per-particle summation.
+template <bool MIXED, int DIM>
+struct FwdAcc {
+  using P = Pair<MIXED, DIM>;
+  using T = typename P::T;
+  using V4 = typename P::V4;
+  using V2 = typename P::V2;
+  Kahan<T> s_rho, s_fx, s_fy, s_fz, s_q;
+  T dmax = T(0);
+  int last_adj = -1;
+
+  __device__ __forceinline__ void pair(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi, const V2& Ci,
+                                       int ui, int64_t j, T sx, T sy, T sz) {
+    const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
+    const V4* __restrict__ B = reinterpret_cast<const V4*>(a.B);
+    const V2* __restrict__ C = reinterpret_cast<const V2*>(a.C);
+    if (j == i) return;       // the scan keeps the self pair (r = 0); it has no flux
+    const V4 Aj = A[j];
+    const V4 Bj = B[j];
+    const V2 Cj = C[j];
+    T dx, dy, dz;
+    if (MIXED) {
+      dx = (Aj.x - Ai.x) + sx;
+      dy = DIM >= 2 ? (Aj.y - Ai.y) + sy : T(0);
+      dz = DIM >= 3 ? (Aj.z - Ai.z) + sz : T(0);
+    } else {
+      dx = __dsub_rn(Aj.x, Ai.x);
+      dy = DIM >= 2 ? __dsub_rn(Aj.y, Ai.y) : 0.0;
+      dz = DIM >= 3 ? __dsub_rn(Aj.z, Ai.z) : 0.0;
+    }
+    const T r2 = P::r2_of(dx, dy, dz);
+    dmax = Aj.w > dmax ? Aj.w : dmax;
+    if (!(r2 > T(0))) return;  // coincident particles: no direction, no flux
+    const T ir = rsqrt_(r2);
+    const T r = r2 * ir;
+    const T ex = dx * ir, ey = dy * ir, ez = dz * ir;
+    T vi = Bi.x * ex, vj = Bj.x * ex;
+    if (DIM >= 2) { vi = fma_(Bi.y, ey, vi); vj = fma_(Bj.y, ey, vj); }
+    if (DIM >= 3) { vi = fma_(Bi.z, ez, vi); vj = fma_(Bj.z, ez, vj); }
+    const T Zi = Ci.y, Zj = Cj.y, Pi = Ci.x, Pj = Cj.x;
+    const T zs = add_(Zi, Zj);
+    T Ps, vs;
+    if (zs > T(0)) {
+      const T izs = rcp_(zs);
+      Ps = mul_(add_(add_(mul_(Zj, Pi), mul_(Zi, Pj)), mul_(mul_(Zi, Zj), sub_(vi, vj))), izs);
+      vs = mul_(add_(add_(mul_(Zi, vi), mul_(Zj, vj)), sub_(Pi, Pj)), izs);
+    } else {
+      Ps = mul_(T(0.5), add_(Pi, Pj));
+      vs = mul_(T(0.5), add_(vi, vj));
+    }
+    const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * add_(Ai.w, Aj.w);
+    const T dW = MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij)
+                       : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij);
+    const T F = mul_(mul_(mul_(T(2), mul_(Bi.w, Bj.w)), Ps), dW);   // momentum flux along e
+    s_rho.add(Bj.w * (vi - vs) * (-dW));
+    s_fx.add(mul_(F, ex));
+    if (DIM >= 2) s_fy.add(mul_(F, ey));
+    if (DIM >= 3) s_fz.add(mul_(F, ez));
+    s_q.add(mul_(F, vs));
+    if (a.pair_i) {
+      const int32_t pi = a.perm[i], pj = a.perm[j];
+      if (pi < pj) {
+        const unsigned long long q = atomicAdd(&a.counters[4], 1ull);
+        if ((int64_t)q < a.pair_cap) { a.pair_i[q] = pi; a.pair_j[q] = pj; }
+      }
+    }
+    if (a.collect_adj) {
+      const int uj = a.slot_unit[j];
+      if (uj != ui && uj != last_adj) {
+        atomicOr(&a.adj_bits[ui * a.adj_words + (uj >> 5)], 1u << (uj & 31));
+        last_adj = uj;
+      }
+    }
+  }
+
+  // Rates of home slot i (particle perm[i]) from the sums; nfull: its interacting pairs.
+  __device__ __forceinline__ void write(const PairArgs& a, int64_t i, unsigned nfull) const {
+    const int64_t p = a.perm[i];
+    a.drho[p] = 2.0 * a.rho_slot[i] * (double)s_rho.s;
+    const double im = 1.0 / a.m[p];
+    a.ax[p] = (double)s_fx.s * im;
+    if (DIM >= 2) a.ay[p] = (double)s_fy.s * im;
+    if (DIM >= 3) a.az[p] = (double)s_fz.s * im;
+    a.dE[p] = (double)s_q.s * im;
+    a.dmax_nbr[p] = nfull ? (double)dmax : -1.0;
+  }
+};
+
+// Pair counters and work-unit loads (full-list pairs per unit), aggregated per warp.
+__device__ __forceinline__ void warp_counters(const PairArgs& a, bool act, unsigned nfull, unsigned ncand,
+                                              unsigned nexact, int ui, int lane) {
+  const unsigned tf = __reduce_add_sync(0xffffffffu, act ? nfull : 0u);
+  const unsigned tc = __reduce_add_sync(0xffffffffu, ncand);
+  const unsigned te = __reduce_add_sync(0xffffffffu, nexact);
+  if (lane == 0) {
+    atomicAdd(&a.counters[0], (unsigned long long)tf);
+    atomicAdd(&a.counters[1], (unsigned long long)tc);
+    atomicAdd(&a.counters[2], (unsigned long long)te);
+  }
+  if (a.K > 0) {
+    const int u0 = __shfl_sync(0xffffffffu, ui, 0);
+    if (__all_sync(0xffffffffu, !act || ui == u0)) {
+      if (lane == 0) atomicAdd(&a.load_acc[u0], (unsigned long long)tf);
+    } else if (act) {
+      atomicAdd(&a.load_acc[ui], (unsigned long long)nfull);
+    }
+  }
+}
+
 // One warp per home cell, lane l owning home particle start_c + chunk + l.
 // Candidate test, transposed: for each neighbour row (the 3 x-consecutive
 // cells at (oy, oz), contiguous in slot order) the warp takes 32 candidates
@@ -237,8 +364,10 @@ struct Pair {
 constexpr int kWarps = kPairBlock / 32;
 constexpr int kRow = kListCap + 2;   // padded row stride (16-bit entries): lane rows fall in distinct banks
 
-template <bool MIXED, int DIM, bool VJP>
-__global__ void __launch_bounds__(kPairBlock, VJP ? (MIXED ? 4 : 2) : (MIXED ? 6 : 4)) k_pair(PairArgs a) {
+template <bool MIXED, int DIM, int MODE>
+__global__ void __launch_bounds__(kPairBlock, MODE == kModeVjp ? (MIXED ? 4 : 2) : (MIXED ? 6 : 4)) k_pair(PairArgs a) {
+  constexpr bool VJP = MODE == kModeVjp;
+  constexpr bool LIST = MODE == kModeList;
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
   using V4 = typename P::V4;
@@ -246,6 +375,7 @@ __global__ void __launch_bounds__(kPairBlock, VJP ? (MIXED ? 4 : 2) : (MIXED ? 6
   __shared__ uint16_t list[kWarps][32][kRow];               // [warp][home particle][entry]
   __shared__ V4 home[kWarps][32];                            // home particles: x, y, z, kh d (mixed) or d (FP64)
   __shared__ int32_t nb_start[kWarps][27];                   // start slot of each neighbour cell
+  __shared__ float4 nb_tab[kWarps][27];                      // per neighbour cell: start (bits), shift x, y, z
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -253,6 +383,10 @@ __global__ void __launch_bounds__(kPairBlock, VJP ? (MIXED ? 4 : 2) : (MIXED ? 6
   const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
   const V4* __restrict__ B = reinterpret_cast<const V4*>(a.B);
   const V2* __restrict__ C = reinterpret_cast<const V2*>(a.C);
+  if constexpr (LIST) {
+    if (a.vflag[0] == 0) return;                 // lists still valid: nothing to build
+    if (blockIdx.x == 0 && threadIdx.x == 0) { a.vflag[1] = 0; a.vflag[2] += 1; }
+  }
   // Persistent warps: each takes the next cell from a global counter, so the
   // work spreads evenly whatever the mix of empty and crowded cells.
   for (;;) {
@@ -284,7 +418,11 @@ __global__ void __launch_bounds__(kPairBlock, VJP ? (MIXED ? 4 : 2) : (MIXED ? 6
     const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
     const int xx = cx + ox, yy = cy + oy, zz = cz + oz;
     const bool in = xx >= 0 && xx < nx && yy >= 0 && yy < ny && zz >= 0 && zz < nz;
-    nb_start[warp][lane] = in ? a.cell_start[g.cell_off + xx + (int64_t)nx * (yy + (int64_t)ny * zz)] : -1;
+    const int st0 = in ? a.cell_start[g.cell_off + xx + (int64_t)nx * (yy + (int64_t)ny * zz)] : -1;
+    nb_start[warp][lane] = st0;
+    // the shift from the home cell's origin to this cell's, exact (ox, oy, oz in {-1, 0, 1})
+    nb_tab[warp][lane] = make_float4(__int_as_float(st0), MIXED ? (float)ox * (float)dcs : 0.f,
+                                     MIXED ? (float)oy * (float)dcs : 0.f, MIXED ? (float)oz * (float)dcs : 0.f);
   }
 
   for (int h0 = hs; h0 < he; h0 += 32) {
@@ -300,12 +438,9 @@ __global__ void __launch_bounds__(kPairBlock, VJP ? (MIXED ? 4 : 2) : (MIXED ? 6
       home[warp][lane] = hv;
     }
     __syncwarp();
-    int cnt = 0;
+    int cnt = 0, vc = 0;
     unsigned nfull = 0, ncand = 0, nexact = 0;
-    T dmax = T(0);
     const int ui = a.K > 0 ? a.slot_unit[ii] : 0;
-    int last_adj = -1;
-    Kahan<T> s_rho, s_fx, s_fy, s_fz, s_q;
     const V4 Bi = B[ii];
     const V2 Ci = C[ii];
     // reverse mode: i's adjoint operands and the 11 own-side sums
@@ -316,81 +451,15 @@ __global__ void __launch_bounds__(kPairBlock, VJP ? (MIXED ? 4 : 2) : (MIXED ? 6
     if constexpr (VJP) { Gi = Gp[ii]; Ri = Rp[ii]; }
     Kahan<T> s_bx[3], s_bv[3], s_bP, s_bZ, s_bV, s_bd, s_brho;
 
-    // Flux of the interacting pair (i, j) from i's side.  Every quantity
-    // that j computes for the same pair is the exact negative (e^R, v^R, v*,
-    // momentum and energy fluxes) or the exact same value (r, P*, h_ij, W'):
-    // dx = (off_j - off_i) + shift is the rounded negative of j's
-    // (off_i - off_j) - shift, IEEE rounding is sign-symmetric, and the sums
-    // that mix i and j are written with uncontracted operations in an order
-    // that is symmetric under the exchange.  So the applied fluxes are
-    // antisymmetric bit for bit and momentum and energy are conserved by the
-    // pair sums up to the per-particle summation.
-    auto pair_flux = [&](int64_t j, int ox, int oy, int oz) {
-      if (j == i) return;       // the scan keeps the self pair (r = 0); it has no flux
-      const V4 Aj = A[j];
-      const V4 Bj = B[j];
-      const V2 Cj = C[j];
-      T dx, dy, dz;
-      if (MIXED) {
-        dx = (Aj.x - Ai.x) + ox * dcs;
-        dy = DIM >= 2 ? (Aj.y - Ai.y) + oy * dcs : T(0);
-        dz = DIM >= 3 ? (Aj.z - Ai.z) + oz * dcs : T(0);
-      } else {
-        dx = __dsub_rn(Aj.x, Ai.x);
-        dy = DIM >= 2 ? __dsub_rn(Aj.y, Ai.y) : 0.0;
-        dz = DIM >= 3 ? __dsub_rn(Aj.z, Ai.z) : 0.0;
-      }
-      const T r2 = P::r2_of(dx, dy, dz);
-      dmax = Aj.w > dmax ? Aj.w : dmax;
-      if (!(r2 > T(0))) return;  // coincident particles: no direction, no flux
-      const T ir = rsqrt_(r2);
-      const T r = r2 * ir;
-      const T ex = dx * ir, ey = dy * ir, ez = dz * ir;
-      T vi = Bi.x * ex, vj = Bj.x * ex;
-      if (DIM >= 2) { vi = fma_(Bi.y, ey, vi); vj = fma_(Bj.y, ey, vj); }
-      if (DIM >= 3) { vi = fma_(Bi.z, ez, vi); vj = fma_(Bj.z, ez, vj); }
-      const T Zi = Ci.y, Zj = Cj.y, Pi = Ci.x, Pj = Cj.x;
-      const T zs = add_(Zi, Zj);
-      T Ps, vs;
-      if (zs > T(0)) {
-        const T izs = rcp_(zs);
-        Ps = mul_(add_(add_(mul_(Zj, Pi), mul_(Zi, Pj)), mul_(mul_(Zi, Zj), sub_(vi, vj))), izs);
-        vs = mul_(add_(add_(mul_(Zi, vi), mul_(Zj, vj)), sub_(Pi, Pj)), izs);
-      } else {
-        Ps = mul_(T(0.5), add_(Pi, Pj));
-        vs = mul_(T(0.5), add_(vi, vj));
-      }
-      const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * add_(Ai.w, Aj.w);
-      const T dW = MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij)
-                         : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij);
-      const T F = mul_(mul_(mul_(T(2), mul_(Bi.w, Bj.w)), Ps), dW);   // momentum flux along e
-      s_rho.add(Bj.w * (vi - vs) * (-dW));
-      s_fx.add(mul_(F, ex));
-      if (DIM >= 2) s_fy.add(mul_(F, ey));
-      if (DIM >= 3) s_fz.add(mul_(F, ez));
-      s_q.add(mul_(F, vs));
-      if (a.pair_i) {
-        const int32_t pi = a.perm[i], pj = a.perm[j];
-        if (pi < pj) {
-          const unsigned long long q = atomicAdd(&a.counters[4], 1ull);
-          if ((int64_t)q < a.pair_cap) { a.pair_i[q] = pi; a.pair_j[q] = pj; }
-        }
-      }
-      if (a.collect_adj) {
-        const int uj = a.slot_unit[j];
-        if (uj != ui && uj != last_adj) {
-          atomicOr(&a.adj_bits[ui * a.adj_words + (uj >> 5)], 1u << (uj & 31));
-          last_adj = uj;
-        }
-      }
-    };
+    FwdAcc<MIXED, DIM> fw;
+    auto pair_flux = [&](int64_t j, T sx, T sy, T sz) { fw.pair(a, i, Ai, Bi, Ci, ui, j, sx, sy, sz); };
 
     // Reverse mode of the pair's contributions (VJP = true): the derivative of
     // the pair's terms in a, drho, dE of both i and j, contracted with their
     // adjoints, with respect to i's own variables: position (through r, e and
     // W'), v (through v^R), P and Z = rho c (through the acoustic solver),
     // V = m/rho, d (through h_ij) and the rho factor of the continuity term.
-    auto pair_vjp = [&](int64_t j, int ox, int oy, int oz) {
+    auto pair_vjp = [&](int64_t j, T sx, T sy, T sz) {
       if (j == i) return;
       const V4 Aj = A[j];
       const V4 Bj = B[j];
@@ -399,9 +468,9 @@ __global__ void __launch_bounds__(kPairBlock, VJP ? (MIXED ? 4 : 2) : (MIXED ? 6
       const V2 Rj = Rp[j];
       T dx, dy, dz;
       if (MIXED) {
-        dx = (Aj.x - Ai.x) + ox * dcs;
-        dy = DIM >= 2 ? (Aj.y - Ai.y) + oy * dcs : T(0);
-        dz = DIM >= 3 ? (Aj.z - Ai.z) + oz * dcs : T(0);
+        dx = (Aj.x - Ai.x) + sx;
+        dy = DIM >= 2 ? (Aj.y - Ai.y) + sy : T(0);
+        dz = DIM >= 3 ? (Aj.z - Ai.z) + sz : T(0);
       } else {
         dx = __dsub_rn(Aj.x, Ai.x);
         dy = DIM >= 2 ? __dsub_rn(Aj.y, Ai.y) : 0.0;
@@ -475,11 +544,18 @@ __global__ void __launch_bounds__(kPairBlock, VJP ? (MIXED ? 4 : 2) : (MIXED ? 6
       nfull += (unsigned)cnt;
       for (int k = 0; k < cnt; ++k) {
         const unsigned ent = list[warp][lane][k];
-        const int code = ent >> 11;
-        const int oz = code / 9, oy = (code - 9 * oz) / 3, ox = code - 9 * oz - 3 * oy;
-        const int64_t j = (int64_t)nb_start[warp][code] + (ent & 2047u);
-        if constexpr (VJP) pair_vjp(j, ox - 1, oy - 1, oz - 1);
-        else pair_flux(j, ox - 1, oy - 1, oz - 1);
+        const float4 t = nb_tab[warp][ent >> 11];
+        const int64_t j = (int64_t)__float_as_int(t.x) + (ent & 2047u);
+        if constexpr (LIST) {
+          if (j != i) {
+            if (vc < a.vcap) a.vlist[(int64_t)i * a.vcap + vc] = ((uint32_t)j << 5) | (ent >> 11);
+            ++vc;
+          }
+        } else if constexpr (VJP) {
+          pair_vjp(j, (T)t.y, (T)t.z, (T)t.w);
+        } else {
+          pair_flux(j, (T)t.y, (T)t.z, (T)t.w);
+        }
       }
       cnt = 0;
     };
@@ -523,10 +599,14 @@ __global__ void __launch_bounds__(kPairBlock, VJP ? (MIXED ? 4 : 2) : (MIXED ? 6
               const T r2 = P::r2_of(dx, dy, dz);
               const T R = fmaf((T)a.kh_f, S.w, H.w);
               const T diff = fmaf(-R, R, r2);          // r^2 - R^2
-              acc = diff < T(0);
-              if (fabsf(diff) <= band && jv) {          // too close to call in FP32: FP64 decides
-                ++nexact;
-                acc = (j == h0 + hp) || exact_accept(a, DIM, a.perm[h0 + hp], a.perm[j]);
+              if constexpr (LIST) {
+                acc = diff < band;                      // superset of the (1 + beta) radius
+              } else {
+                acc = diff < T(0);
+                if (fabsf(diff) <= band && jv) {        // too close to call in FP32: FP64 decides
+                  ++nexact;
+                  acc = (j == h0 + hp) || exact_accept(a, DIM, a.perm[h0 + hp], a.perm[j]);
+                }
               }
             } else {
               T dx, dy, dz;
@@ -548,6 +628,19 @@ __global__ void __launch_bounds__(kPairBlock, VJP ? (MIXED ? 4 : 2) : (MIXED ? 6
     }
     if (act) flush();
 
+    if constexpr (LIST) {
+      if (act) {
+        if (vc > a.vcap) set_status(a.status, SPH_ERR_CAPACITY);
+        a.vcnt[i] = vc < a.vcap ? vc : a.vcap;
+        const int64_t p = a.perm[i];
+        a.vref[p] = a.x[p];
+        if (DIM >= 2) a.vref[a.n + p] = a.y[p];
+        if (DIM >= 3) a.vref[2 * a.n + p] = a.z[p];
+        a.vref[3 * a.n + p] = a.d[p];
+      }
+      __syncwarp();
+      continue;
+    }
     if constexpr (VJP) {
       if (act) {
         double* o = a.vjp_out + 11 * (int64_t)a.perm[i];
@@ -564,63 +657,260 @@ __global__ void __launch_bounds__(kPairBlock, VJP ? (MIXED ? 4 : 2) : (MIXED ? 6
     }
     if (act) {
       nfull -= 1;   // the self pair
-      const int64_t p = a.perm[i];
-      a.drho[p] = 2.0 * a.rho_slot[i] * (double)s_rho.s;
-      const double im = 1.0 / a.m[p];
-      a.ax[p] = (double)s_fx.s * im;
-      if (DIM >= 2) a.ay[p] = (double)s_fy.s * im;
-      if (DIM >= 3) a.az[p] = (double)s_fz.s * im;
-      a.dE[p] = (double)s_q.s * im;
-      a.dmax_nbr[p] = nfull ? (double)dmax : -1.0;
+      fw.write(a, i, nfull);
     }
-    // counters and work-unit loads, aggregated per warp
-    unsigned tf = __reduce_add_sync(0xffffffffu, act ? nfull : 0u);
-    unsigned tc = __reduce_add_sync(0xffffffffu, ncand);
-    unsigned te = __reduce_add_sync(0xffffffffu, nexact);
-    if (lane == 0) {
-      atomicAdd(&a.counters[0], (unsigned long long)tf);
-      atomicAdd(&a.counters[1], (unsigned long long)tc);
-      atomicAdd(&a.counters[2], (unsigned long long)te);
-    }
-    if (a.K > 0) {
-      const int u0 = __shfl_sync(0xffffffffu, ui, 0);
-      if (__all_sync(0xffffffffu, !act || ui == u0)) {
-        if (lane == 0) atomicAdd(&a.load_acc[u0], (unsigned long long)tf);
-      } else if (act) {
-        atomicAdd(&a.load_acc[ui], (unsigned long long)nfull);
-      }
-    }
+    warp_counters(a, act, nfull, ncand, nexact, ui, lane);
     __syncwarp();   // the home buffer is rewritten by the next chunk of home particles
   }
   __syncwarp();     // the neighbour-start buffer is rewritten by the next cell
   }
 }
 
+// Pair evaluation over the Verlet lists: one warp per slot i, taken in
+// groups of 32 consecutive slots from a global counter.  The warp reads i's
+// list 32 entries at a time (particle-major, so the reads are contiguous),
+// decides each entry as k_pair does (FP32 test outside the band of
+// 2^-12 D^c^2, FP64 in the oracle's operation order inside it), and appends
+// the accepted ones to a per-warp queue in shared memory (ballot + prefix
+// popcount, list order kept).  Whenever the queue holds 32 pairs, every lane
+// evaluates one flux with FwdAcc; the lanes' Kahan sums (a few pairs each)
+// are combined by a fixed butterfly, and the FP64 scaling of the rates is
+// done for the 32 slots of the group at once, one slot per lane.  Offsets stay relative to the cells of
+// the build and each pair's shift comes from its neighbour-cell code, so the
+// fluxes keep their bitwise antisymmetry; every order is fixed, so results
+// are reproducible bit for bit.
+constexpr int kListQueue = 64;
+
+// Sum over the warp's lanes of their Kahan sums (s - c), by a fixed butterfly.
+template <typename T>
+__device__ __forceinline__ T warp_sum(const Kahan<T>& k) {
+  T v = k.s - k.c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <bool MIXED, int DIM>
+__global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair_lists(PairArgs a) {
+  using P = Pair<MIXED, DIM>;
+  using T = typename P::T;
+  using V4 = typename P::V4;
+  using V2 = typename P::V2;
+  __shared__ uint32_t queue[kWarps][kListQueue];
+  __shared__ float res[kWarps][6][32];            // per slot of the group: sums of rho, a (3), E, and dmax
+  __shared__ double res64[kWarps][6][MIXED ? 1 : 32];
+  __shared__ unsigned res_n[kWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
+  uint32_t* q = queue[warp];
+  for (;;) {
+    int64_t g0 = 0;
+    if (lane == 0) g0 = (int64_t)atomicAdd(a.work_counter, 32ull);
+    g0 = __shfl_sync(0xffffffffu, g0, 0);
+    if (g0 >= a.n) break;
+    const int64_t g1 = g0 + 32 < a.n ? g0 + 32 : a.n;
+    int unit_run = -1;
+    unsigned unit_load = 0;
+    unsigned tf = 0, tc = 0, te = 0;
+    for (int64_t i = g0; i < g1; ++i) {                 // warp-uniform
+      int b = 0;
+      if (a.n_inst > 1) {
+        int lo = 0, hi = a.n_inst;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (a.inst_off[mid] <= i) lo = mid; else hi = mid;
+        }
+        b = lo;
+      }
+      const GridInfo& g = a.grid[b];
+      const T dcs = MIXED ? (T)g.dc_f : T(0);
+      const float band = MIXED ? 0x1p-12f * g.dc_f * g.dc_f : 0.f;
+      const V4 Ai = A[i];
+      const V4 Bi = reinterpret_cast<const V4*>(a.B)[i];
+      const V2 Ci = reinterpret_cast<const V2*>(a.C)[i];
+      const T khdi = MIXED ? (T)a.kh_f * Ai.w : T(0);
+      const int ui = a.K > 0 ? a.slot_unit[i] : 0;
+      const int cnt = a.vcnt[i];
+      const uint32_t* __restrict__ row = a.vlist + i * (int64_t)a.vcap;
+      FwdAcc<MIXED, DIM> fw;
+      int qn = 0;          // queued pairs (warp-uniform)
+      unsigned nacc = 0;   // accepted pairs of i (warp-uniform)
+      auto drain = [&](int m) {                        // one flux per lane over the first m queued pairs
+        if (lane < m) {
+          const uint32_t e = q[lane];
+          const int code = (int)(e & 31u);
+          const T sx = MIXED ? (T)(code % 3 - 1) * dcs : T(0);
+          const T sy = MIXED ? (T)((code / 3) % 3 - 1) * dcs : T(0);
+          const T sz = MIXED ? (T)(code / 9 - 1) * dcs : T(0);
+          fw.pair(a, i, Ai, Bi, Ci, ui, (int64_t)(e >> 5), sx, sy, sz);
+        }
+        __syncwarp();
+        if (lane + m < qn) q[lane] = q[lane + m];      // keep the rest (fewer than 32) in order
+        __syncwarp();
+        qn -= m;
+      };
+      for (int base = 0; base < cnt; base += 32) {
+        const int k = base + lane;
+        const bool kv = k < cnt;
+        const uint32_t e = kv ? row[k] : 0u;
+        const int64_t j = e >> 5;
+        const V4 S = A[kv ? j : i];
+        bool acc = false;
+        if (kv) {
+          if (MIXED) {
+            const int code = (int)(e & 31u);
+            const T sx = (T)(code % 3 - 1) * dcs, sy = (T)((code / 3) % 3 - 1) * dcs, sz = (T)(code / 9 - 1) * dcs;
+            const T dx = (S.x + sx) - Ai.x;
+            const T dy = DIM >= 2 ? (S.y + sy) - Ai.y : T(0);
+            const T dz = DIM >= 3 ? (S.z + sz) - Ai.z : T(0);
+            const T r2 = P::r2_of(dx, dy, dz);
+            const T R = fmaf((T)a.kh_f, S.w, khdi);
+            const T diff = fmaf(-R, R, r2);
+            acc = diff < T(0);
+            if (fabsf(diff) <= band) {
+              ++te;
+              acc = exact_accept(a, DIM, a.perm[i], a.perm[j]);
+            }
+          } else {
+            T dx, dy, dz;
+            P::sep(true, Ai, S, T(0), T(0), T(0), dx, dy, dz);   // x_j - x_i, oracle order
+            const T r2 = P::r2_of(dx, dy, dz);
+            const double R = __dmul_rn(a.kh, __dadd_rn(Ai.w, S.w));
+            acc = r2 < __dmul_rn(R, R);
+          }
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, acc);
+        if (acc) q[qn + __popc(mask & lt)] = e;
+        __syncwarp();
+        qn += __popc(mask);
+        nacc += __popc(mask);
+        if (qn >= 32) drain(32);
+      }
+      if (qn > 0) drain(qn);
+      // combine the lanes' sums (fixed butterfly order); the rates are scaled below, per lane
+      const T srho = warp_sum(fw.s_rho), sfx = warp_sum(fw.s_fx);
+      const T sfy = DIM >= 2 ? warp_sum(fw.s_fy) : T(0), sfz = DIM >= 3 ? warp_sum(fw.s_fz) : T(0);
+      const T sq = warp_sum(fw.s_q);
+      T dm = fw.dmax;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T other = __shfl_xor_sync(0xffffffffu, dm, o);
+        dm = other > dm ? other : dm;
+      }
+      if (lane == 0) {
+        const int r = (int)(i - g0);
+        const T vals[6] = {srho, sfx, sfy, sfz, sq, dm};
+#pragma unroll
+        for (int qv = 0; qv < 6; ++qv) {
+          if constexpr (MIXED) res[warp][qv][r] = (float)vals[qv];
+          else res64[warp][qv][r] = (double)vals[qv];
+        }
+        res_n[warp][r] = nacc;
+      }
+      tf += nacc;
+      tc += (unsigned)cnt;
+      if (a.K > 0) {                                   // loads per unit, flushed when the unit changes
+        if (ui != unit_run && unit_run >= 0 && lane == 0 && unit_load)
+          atomicAdd(&a.load_acc[unit_run], (unsigned long long)unit_load);
+        if (ui != unit_run) { unit_run = ui; unit_load = 0; }
+        unit_load += nacc;
+      }
+    }
+    if (a.K > 0 && lane == 0 && unit_run >= 0 && unit_load)
+      atomicAdd(&a.load_acc[unit_run], (unsigned long long)unit_load);
+    __syncwarp();
+    {
+      const int64_t i = g0 + lane;                     // one slot of the group per lane
+      if (i < g1) {
+        auto rv = [&](int qv) -> double {
+          if constexpr (MIXED) return (double)res[warp][qv][lane];
+          else return res64[warp][qv][lane];
+        };
+        const int64_t p = a.perm[i];
+        a.drho[p] = 2.0 * a.rho_slot[i] * rv(0);
+        const double im = 1.0 / a.m[p];
+        a.ax[p] = rv(1) * im;
+        if (DIM >= 2) a.ay[p] = rv(2) * im;
+        if (DIM >= 3) a.az[p] = rv(3) * im;
+        a.dE[p] = rv(4) * im;
+        a.dmax_nbr[p] = res_n[warp][lane] ? rv(5) : -1.0;
+      }
+    }
+    __syncwarp();
+    te = __reduce_add_sync(0xffffffffu, te);
+    if (lane == 0) {
+      atomicAdd(&a.counters[0], (unsigned long long)tf);
+      atomicAdd(&a.counters[1], (unsigned long long)tc);
+      atomicAdd(&a.counters[2], (unsigned long long)te);
+    }
+  }
+}
+
 // Persistent grid: SMs x resident CTAs per SM, capped by the handle's
 // pair_blocks_per_sm (0 = as many as fit).
-template <bool MIXED, int DIM, bool VJP>
+template <bool MIXED, int DIM, int MODE>
 cudaError_t launch_one(const PairArgs& args, int blocks_per_sm, cudaStream_t st) {
   static int sms = 0, per_sm = 0;
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<MIXED, DIM, VJP>, kPairBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<MIXED, DIM, MODE>, kPairBlock, 0);
     if (per_sm < 1) per_sm = 1;
   }
   const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
-  k_pair<MIXED, DIM, VJP><<<sms * b, kPairBlock, 0, st>>>(args);
+  k_pair<MIXED, DIM, MODE><<<sms * b, kPairBlock, 0, st>>>(args);
   return cudaGetLastError();
 }
 
-template <bool MIXED, bool VJP>
+template <bool MIXED, int MODE>
 cudaError_t launch_dim(sph_handle* h, const PairArgs& args, cudaStream_t st) {
   const int b = h->p.pair_blocks_per_sm;
   switch (h->dp.dim) {
-    case 1: return launch_one<MIXED, 1, VJP>(args, b, st);
-    case 2: return launch_one<MIXED, 2, VJP>(args, b, st);
-    default: return launch_one<MIXED, 3, VJP>(args, b, st);
+    case 1: return launch_one<MIXED, 1, MODE>(args, b, st);
+    case 2: return launch_one<MIXED, 2, MODE>(args, b, st);
+    default: return launch_one<MIXED, 3, MODE>(args, b, st);
   }
+}
+
+template <bool MIXED, int DIM>
+cudaError_t launch_lists_one(const PairArgs& args, int blocks_per_sm, cudaStream_t st) {
+  static int sms = 0, per_sm = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_lists<MIXED, DIM>, kPairBlock, 0);
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
+  k_pair_lists<MIXED, DIM><<<sms * b, kPairBlock, 0, st>>>(args);
+  return cudaGetLastError();
+}
+
+template <bool MIXED>
+cudaError_t launch_lists_dim(sph_handle* h, const PairArgs& args, cudaStream_t st) {
+  const int b = h->p.pair_blocks_per_sm;
+  switch (h->dp.dim) {
+    case 1: return launch_lists_one<MIXED, 1>(args, b, st);
+    case 2: return launch_lists_one<MIXED, 2>(args, b, st);
+    default: return launch_lists_one<MIXED, 3>(args, b, st);
+  }
+}
+
+// CUDA events around a pair-kernel launch when profiling (sph_profile).
+cudaError_t prof_record(sph_handle* h, bool start, cudaStream_t st) {
+  if (!h->profiling) return cudaSuccess;
+  if (start && h->prof_used + 2 > h->prof_events.size()) {
+    for (int k = 0; k < 64; ++k) {
+      cudaEvent_t ev;
+      cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return e;
+      h->prof_events.push_back(ev);
+    }
+  }
+  return cudaEventRecord(h->prof_events[h->prof_used++], st);
 }
 
 PairArgs make_args(sph_handle* h, const sph_state& s) {
@@ -660,6 +950,11 @@ PairArgs make_args(sph_handle* h, const sph_state& s) {
   a.kappa = h->dp.kappa;
   a.kappa_f = (float)h->dp.kappa;
   a.kernel = h->dp.kernel;
+  a.vlist = h->vlist;
+  a.vcnt = h->vcnt;
+  a.vref = h->vref;
+  a.vflag = h->vflag;
+  a.vcap = h->vcap;
   return a;
 }
 
@@ -679,8 +974,41 @@ cudaError_t launch_pair_vjp(sph_handle* h, const sph_state& s, const void* G, co
   a.vjp_out = out;
   cudaError_t e = cudaMemsetAsync(&h->counters[5], 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, true>(h, a, st) : launch_dim<false, true>(h, a, st);
+  e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, kModeVjp>(h, a, st)
+                                        : launch_dim<false, kModeVjp>(h, a, st);
   h->launches += 1;
+  return e;
+}
+
+// Verlet list build: the pair kernel over the radius (1 + beta) kappa h_ij;
+// returns at once on the device unless vflag[0] is set.
+cudaError_t launch_list_build(sph_handle* h, const sph_state& s, cudaStream_t st) {
+  PairArgs a = make_args(h, s);
+  a.K = 0;
+  a.collect_adj = 0;
+  a.pair_i = a.pair_j = nullptr;
+  const double khl = h->dp.kh * (1.0 + h->dp.cell_beta);
+  a.kh = khl;
+  a.kh_f = (float)khl;
+  cudaError_t e = cudaMemsetAsync(&h->counters[5], 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, kModeList>(h, a, st)
+                                        : launch_dim<false, kModeList>(h, a, st);
+  h->launches += 1;
+  return e;
+}
+
+// Pair evaluation over the Verlet lists (rates, counters, unit loads).
+cudaError_t launch_pair_lists(sph_handle* h, const sph_state& s, cudaStream_t st) {
+  PairArgs a = make_args(h, s);
+  cudaError_t e = cudaMemsetAsync(h->counters, 0, 3 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(&h->counters[5], 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  if ((e = prof_record(h, true, st)) != cudaSuccess) return e;
+  e = h->dp.precision == SPH_PREC_MIXED ? launch_lists_dim<true>(h, a, st) : launch_lists_dim<false>(h, a, st);
+  h->launches += 1;
+  if (e == cudaSuccess) e = prof_record(h, false, st);
   return e;
 }
 
@@ -690,24 +1018,11 @@ cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(&h->counters[4], 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (h->profiling) {
-    if (h->prof_used + 2 > h->prof_events.size()) {
-      for (int k = 0; k < 64; ++k) {
-        cudaEvent_t ev;
-        e = cudaEventCreate(&ev);
-        if (e != cudaSuccess) return e;
-        h->prof_events.push_back(ev);
-      }
-    }
-    e0 = h->prof_events[h->prof_used++];
-    e1 = h->prof_events[h->prof_used++];
-    e = cudaEventRecord(e0, st);
-    if (e != cudaSuccess) return e;
-  }
-  e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, false>(h, a, st) : launch_dim<false, false>(h, a, st);
+  if ((e = prof_record(h, true, st)) != cudaSuccess) return e;
+  e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, kModeFwd>(h, a, st)
+                                        : launch_dim<false, kModeFwd>(h, a, st);
   h->launches += 1;
-  if (e == cudaSuccess && h->profiling) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = prof_record(h, false, st);
   return e;
 }
 

@@ -37,12 +37,12 @@ __device__ __forceinline__ void top2_merge(long long& a1, long long& a2, long lo
 }
 
 struct Red {
-  long long lo[3], hi[3], d1, d2, dtmin;
+  long long lo[3], hi[3], d1, d2, dtmin, viol;
 };
 
 __device__ __forceinline__ void red_init(Red& r) {
   for (int a = 0; a < 3; ++a) { r.lo[a] = LLONG_MAX; r.hi[a] = LLONG_MIN; }
-  r.d1 = 0; r.d2 = 0; r.dtmin = LLONG_MAX;
+  r.d1 = 0; r.d2 = 0; r.dtmin = LLONG_MAX; r.viol = LLONG_MIN;
 }
 
 __device__ __forceinline__ void red_merge(Red& a, const Red& b) {
@@ -52,6 +52,7 @@ __device__ __forceinline__ void red_merge(Red& a, const Red& b) {
   }
   top2_merge(a.d1, a.d2, b.d1, b.d2);
   a.dtmin = a.dtmin < b.dtmin ? a.dtmin : b.dtmin;
+  a.viol = a.viol > b.viol ? a.viol : b.viol;
 }
 
 // Block-wide reduction of Red through shared memory; result in thread 0.
@@ -70,7 +71,7 @@ __device__ void block_reduce(Red& r) {
 __device__ __forceinline__ void write_part(BlockPart* part, const Red& r) {
   BlockPart& b = part[blockIdx.x];
   for (int a = 0; a < 3; ++a) { b.lo[a] = r.lo[a]; b.hi[a] = r.hi[a]; }
-  b.d1 = r.d1; b.d2 = r.d2; b.dtmin = r.dtmin;
+  b.d1 = r.d1; b.d2 = r.d2; b.dtmin = r.dtmin; b.viol = r.viol;
 }
 
 // Cube root in FP64 with little FP64 work: the FP32 cube root as seed, then
@@ -124,7 +125,8 @@ __global__ void k_derive(DevParams P, sph_state s, const int64_t* __restrict__ b
 // One block per instance: reduce the block partials of the instance.
 // mode 1: dt = cfl * min; mode 2: bounding box and sizes into the grid record.
 __global__ void k_reduce_inst(const int32_t* __restrict__ inst_blk, const BlockPart* __restrict__ part,
-                              double cfl, double* dt, GridInfo* grid, int mode) {
+                              double cfl, double* dt, GridInfo* grid, int mode, const int* __restrict__ gate) {
+  if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   int b = blockIdx.x;
   Red r;
   red_init(r);
@@ -151,7 +153,8 @@ __global__ void k_reduce_inst(const int32_t* __restrict__ inst_blk, const BlockP
 // mesh; dims per axis; global cell offsets.  Matches the oracle bit for bit.
 __global__ void k_grid_setup(DevParams P, int n_inst, const int64_t* __restrict__ inst_off,
                              const int64_t* __restrict__ inst_cap, GridInfo* grid, int64_t* total_cells,
-                             int* status) {
+                             int* status, const int* __restrict__ gate) {
+  if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   if (threadIdx.x != 0) return;
   int64_t off = 0;
   for (int b = 0; b < n_inst; ++b) {
@@ -200,7 +203,8 @@ __device__ __forceinline__ int64_t local_cell(const GridInfo& g, int dim, double
 __global__ void k_cell_count(int dim, sph_state s, const int64_t* __restrict__ blk_start,
                              const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst,
                              const GridInfo* __restrict__ grid, int32_t* cell_count, int32_t* cell_of,
-                             int32_t* rank, int* status) {
+                             int32_t* rank, int* status, const int* __restrict__ gate) {
+  if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   int64_t p = blk_start[blockIdx.x] + threadIdx.x;
   if (p >= blk_end[blockIdx.x]) return;
   const GridInfo& g = grid[blk_inst[blockIdx.x]];
@@ -221,7 +225,8 @@ __global__ void k_cell_count(int dim, sph_state s, const int64_t* __restrict__ b
 constexpr int kScanTile = 1024;
 
 __global__ void k_scan_reduce(const int32_t* __restrict__ cnt, const int64_t* __restrict__ total,
-                              int32_t* sums) {
+                              int32_t* sums, const int* __restrict__ gate) {
+  if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   const int64_t tot = *total;
   __shared__ int sh[kBlock];
   // grid-stride over the tiles the current mesh has (the grid is sized for the capacity,
@@ -245,7 +250,8 @@ __global__ void k_scan_reduce(const int32_t* __restrict__ cnt, const int64_t* __
 }
 
 // Single block: exclusive scan of the tile sums in place.
-__global__ void k_scan_sums(int32_t* sums, const int64_t* __restrict__ total) {
+__global__ void k_scan_sums(int32_t* sums, const int64_t* __restrict__ total, const int* __restrict__ gate) {
+  if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   int64_t ntiles = (*total + kScanTile - 1) / kScanTile;
   __shared__ int carry;
   __shared__ int sh[1024];
@@ -271,7 +277,8 @@ __global__ void k_scan_sums(int32_t* sums, const int64_t* __restrict__ total) {
 
 // Per tile: exclusive scan plus tile offset; zero the counts for the next use.
 __global__ void k_scan_down(int32_t* cnt, const int64_t* __restrict__ total, const int32_t* __restrict__ sums,
-                            int32_t* start, int64_t n_total) {
+                            int32_t* start, int64_t n_total, const int* __restrict__ gate) {
+  if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   const int64_t tot = *total;
   constexpr int per = kScanTile / kBlock;  // 4 cells per thread
   __shared__ int sh[kBlock];
@@ -307,7 +314,8 @@ __global__ void k_scan_down(int32_t* cnt, const int64_t* __restrict__ total, con
 }
 
 __global__ void k_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of, const int32_t* __restrict__ rank,
-                               const int32_t* __restrict__ start, int32_t* perm) {
+                               const int32_t* __restrict__ start, int32_t* perm, const int* __restrict__ gate) {
+  if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   perm[start[cell_of[p]] + rank[p]] = (int32_t)p;
@@ -315,7 +323,9 @@ __global__ void k_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of, c
 
 // Within each cell, order the particles by index (the atomic arrival order is
 // not reproducible; this makes the slot order a function of the state only).
-__global__ void k_cell_sort(const int64_t* __restrict__ total, const int32_t* __restrict__ start, int32_t* perm) {
+__global__ void k_cell_sort(const int64_t* __restrict__ total, const int32_t* __restrict__ start, int32_t* perm,
+                            const int* __restrict__ gate) {
+  if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   const int64_t tot = *total;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (int64_t)gridDim.x * blockDim.x) {
     int b = start[c], e = start[c + 1];
@@ -360,6 +370,19 @@ __global__ void k_kick_drift(DevParams P, sph_state s, const int64_t* __restrict
     double d = size_of(P.dim, s.m[p], rp);
     s.d[p] = d;
     r.d1 = dkey(d);
+    if (P.vref) {
+      // Verlet-list validity: a listed superset of the pairs within kappa h_ij holds as long
+      // as |x_i - x_i^b| + kh max(0, d_i - d_i^b) <= beta kh d_i^b for every particle (b: the
+      // last build; summing the bounds of i and j covers the pair), kept with a 5 % margin
+      double dsq = 0.0;
+      for (int a = 0; a < P.dim; ++a) {
+        const double dx = X[a][p] - P.vref[(int64_t)a * P.n + p];
+        dsq += dx * dx;
+      }
+      const double db = P.vref[3 * P.n + p];
+      const double crit = sqrt(dsq) + P.kh * fmax(d - db, 0.0) - 0.95 * P.cell_beta * P.kh * db;
+      r.viol = dkey(crit);
+    }
     if (!finite || !isfinite(d)) set_status(status, SPH_ERR_NONFINITE);
   }
   block_reduce(r);
@@ -544,7 +567,7 @@ cudaError_t launch_derive_dt(sph_handle* h, const sph_state& s, bool with_bbox, 
 }
 
 cudaError_t launch_reduce_dt(sph_handle* h, cudaStream_t st) {
-  k_reduce_inst<<<h->n_inst, kBlock, 0, st>>>(h->inst_blk, h->part, h->dp.cfl, h->dt, h->grid, 1);
+  k_reduce_inst<<<h->n_inst, kBlock, 0, st>>>(h->inst_blk, h->part, h->dp.cfl, h->dt, h->grid, 1, nullptr);
   h->launches += 1;
   return cudaGetLastError();
 }
@@ -558,19 +581,44 @@ cudaError_t launch_kick_drift(sph_handle* h, const sph_state& s, cudaStream_t st
 
 // Mesh from the block partials left by k_derive(with_bbox) or k_kick_drift,
 // then the counting sort of particles into cells.
-cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st) {
-  k_reduce_inst<<<h->n_inst, kBlock, 0, st>>>(h->inst_blk, h->part, h->dp.cfl, h->dt, h->grid, 2);
+cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st, const int* gate) {
+  k_reduce_inst<<<h->n_inst, kBlock, 0, st>>>(h->inst_blk, h->part, h->dp.cfl, h->dt, h->grid, 2, gate);
   k_grid_setup<<<1, 32, 0, st>>>(h->dp, h->n_inst, h->inst_off, h->inst_cap, h->grid, h->total_cells,
-                                 h->status);
+                                 h->status, gate);
   k_cell_count<<<h->nblk, kBlock, 0, st>>>(h->dp.dim, s, h->blk_start, h->blk_end, h->blk_inst, h->grid,
-                                           h->cell_count, h->cell_of, h->rank, h->status);
+                                           h->cell_count, h->cell_of, h->rank, h->status, gate);
   int tiles = capped_grid(grid_for(h->cell_cap, kScanTile));
-  k_scan_reduce<<<tiles, kBlock, 0, st>>>(h->cell_count, h->total_cells, h->scan_sums);
-  k_scan_sums<<<1, 1024, 0, st>>>(h->scan_sums, h->total_cells);
-  k_scan_down<<<tiles, kBlock, 0, st>>>(h->cell_count, h->total_cells, h->scan_sums, h->cell_start, h->n);
-  k_cell_scatter<<<grid_for(h->n, kBlock), kBlock, 0, st>>>(h->n, h->cell_of, h->rank, h->cell_start, h->perm);
-  k_cell_sort<<<capped_grid(grid_for(h->cell_cap, kBlock)), kBlock, 0, st>>>(h->total_cells, h->cell_start, h->perm);
+  k_scan_reduce<<<tiles, kBlock, 0, st>>>(h->cell_count, h->total_cells, h->scan_sums, gate);
+  k_scan_sums<<<1, 1024, 0, st>>>(h->scan_sums, h->total_cells, gate);
+  k_scan_down<<<tiles, kBlock, 0, st>>>(h->cell_count, h->total_cells, h->scan_sums, h->cell_start, h->n, gate);
+  k_cell_scatter<<<grid_for(h->n, kBlock), kBlock, 0, st>>>(h->n, h->cell_of, h->rank, h->cell_start, h->perm,
+                                                            gate);
+  k_cell_sort<<<capped_grid(grid_for(h->cell_cap, kBlock)), kBlock, 0, st>>>(h->total_cells, h->cell_start,
+                                                                             h->perm, gate);
   h->launches += 8;
+  // a mesh built outside the Verlet sequence changes the slot order under the lists
+  if (!gate && h->verlet) return cudaMemsetAsync(&h->vflag[1], 0xff, sizeof(int), st);
+  return cudaGetLastError();
+}
+
+// Verlet lists: vflag[0] = lists invalid (vflag[1]) or the validity criterion
+// of k_kick_drift failed for some particle of any instance.
+__global__ void k_verlet_flag(const BlockPart* __restrict__ part, int nblk, int* vflag) {
+  __shared__ long long sh[1024];
+  long long m = LLONG_MIN;
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) m = part[k].viol > m ? part[k].viol : m;
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] = sh[threadIdx.x + w] > sh[threadIdx.x] ? sh[threadIdx.x + w] : sh[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) vflag[0] = (sh[0] > 0 || vflag[1] != 0) ? 1 : 0;
+}
+
+cudaError_t launch_verlet_flag(sph_handle* h, cudaStream_t st) {
+  k_verlet_flag<<<1, 1024, 0, st>>>(h->part, h->nblk, h->vflag);
+  h->launches += 1;
   return cudaGetLastError();
 }
 
@@ -612,15 +660,17 @@ cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st) {
   k_gather<<<g, kBlock, 0, st>>>(h->n, h->perm, a, reinterpret_cast<char*>(h->scratch));
   k_scatter_back<<<g, kBlock, 0, st>>>(h->n, a, reinterpret_cast<const char*>(h->scratch));
   h->launches += 2;
+  // particle indices changed under the slot order of the Verlet lists
+  if (h->verlet) return cudaMemsetAsync(&h->vflag[1], 0xff, sizeof(int), st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_exclusive_scan(int32_t* cnt, const int64_t* total, int32_t* sums, int32_t* start,
                                   int64_t n_total, int64_t cap, cudaStream_t st) {
   int tiles = capped_grid(grid_for(cap, kScanTile));
-  k_scan_reduce<<<tiles, kBlock, 0, st>>>(cnt, total, sums);
-  k_scan_sums<<<1, 1024, 0, st>>>(sums, total);
-  k_scan_down<<<tiles, kBlock, 0, st>>>(cnt, total, sums, start, n_total);
+  k_scan_reduce<<<tiles, kBlock, 0, st>>>(cnt, total, sums, nullptr);
+  k_scan_sums<<<1, 1024, 0, st>>>(sums, total, nullptr);
+  k_scan_down<<<tiles, kBlock, 0, st>>>(cnt, total, sums, start, n_total, nullptr);
   return cudaGetLastError();
 }
 // (launch_exclusive_scan's three kernels are counted by its callers)

@@ -181,6 +181,10 @@ class Simulation:
         """(pair-kernel ms summed, pair launches, kernel launches) since the last call."""
         return abi.sph_profile_read(self.handle)
 
+    def list_builds(self):
+        """(Verlet-list builds so far, list capacity per particle); needs cell_beta > 0."""
+        return abi.sph_list_builds(self.handle, _stream_ptr())
+
     def read_status(self) -> int:
         return abi.sph_read_status(self.handle)
 
