@@ -4,11 +4,15 @@
 Workload: the 3D plate impact (50^3 projector at 1 km/s onto a 200x200x25
 slab, 1,125,000 particles, cubic lattice 0.1 mm, stiffened gas rho0 = 2700,
 c0 = 5.3 km/s, gamma = 2, h = 1.3 spacing), FP32 pair fluxes with FP64
-positions, 64 Voronoi work units rebalanced every 10 steps.  A step is one
-full CSPH time step (CFL reduction, kick-drift, cell mesh and sort, operand
-packing, pair loop, kick) plus, every 10th step, balancing + reassignment +
-renumbering.  Inputs are synthetic (synth.plate_impact_full) and larger than
-L2 (the FP64 state is ~190 MB), so no L2 flush is needed.
+positions, 64 Voronoi work units rebalanced every 10 steps, Verlet lists
+with buffer beta = 0.15.  A step is one full CSPH time step (CFL reduction,
+kick-drift, list validity check, operand packing, pair evaluation over the
+lists, kick), plus the cell mesh, sort and list build whenever the device-side
+criterion asks for them (the count is reported in config.list_builds), plus,
+every 10th step, balancing + reassignment + renumbering.  --beta 0 gives the
+per-step mesh and pair search instead.  Inputs are synthetic
+(synth.plate_impact_full) and larger than L2 (the FP64 state is ~190 MB), so
+no L2 flush is needed.
 
 Prints one JSON line (rank 0).  At one GPU the line also carries "extras"
 (skip with --no-extras): the plain FP64 step against the mixed step on the
@@ -50,6 +54,7 @@ WORKLOADS = {
 FLOP_TEST = 11.0
 FLOP_PAIR = 70.0
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate; the FP64 pair kernel is bound by it
+BETA = 0.15               # Verlet buffer of the benchmark (best of 0.1 / 0.15 / 0.2 / 0.3 on this workload)
 
 
 def fp32_peak_tflops() -> float:
@@ -172,7 +177,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         import torch.distributed as dist
     prob = synth.plate_impact(units=64, n_steps=500, **WORKLOADS[args.workload])
     gen = synth.problem_generators(prob)
-    sim = Simulation(prob, precision=args.precision, generators=gen, n_upd=10, device=dev)
+    sim = Simulation(prob, precision=args.precision, generators=gen, n_upd=10, cell_beta=args.beta, device=dev)
     sim.assign()
     sim.build_cells()
     sim.step(max(args.warmup, 3))
@@ -185,6 +190,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    builds0 = sim.list_builds()[0] if args.beta > 0 else 0
     with ClockSampler(gpu_index) as clk:
         sim.profile(True)
         e0.record()
@@ -198,6 +204,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     pair_ms, pair_launches, launches = sim.profile_read()
     sim.profile(False)
     half_pairs, candidates, fp64_checks = sim.pair_counts()
+    builds = (sim.list_builds()[0] - builds0) if args.beta > 0 else args.steps
     status = sim.read_status()
     if dist:
         t = torch.tensor([ms], device=dev)
@@ -249,12 +256,14 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
            "data": "synthetic",
            "config": {"workload": args.workload, "particles": prob.n, "precision": args.precision, "units": 64,
+                      "verlet_beta": args.beta, "list_builds": builds,
                       "rebalance_every": 10, "l2": "inputs larger than L2 (no flush)",
                       "parallelism": f"replicas{world}" if world > 1 else "single"},
            "pair_interactions_per_s": half_pairs * world * args.steps / (ms * 1e-3),
            "half_pairs_per_step": half_pairs, "candidates_per_step": candidates,
            "fp64_pair_checks_per_step": fp64_checks,
-           "roofline": {"kernel": "k_pair", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "roofline": {"kernel": "k_pair_lists" if args.beta > 0 else "k_pair", "bound": "alu",
+                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": traffic,
                         "peak_note": "FP32 152 SM x 128 lanes x 2 x 2.07 GHz (derived from unit counts and clock)",
                         "pair_ms_per_launch": pair_ms_avg, "pair_share": pair_ms / ms},
@@ -282,11 +291,13 @@ def _fields_rel(a: dict, b: dict, keys) -> dict:
 
 
 def run_extras(args, dev) -> dict:
-    """The other forms on the same GPU, each against the plain FP64 step:
-    precision (FP64 vs mixed step on the benchmark plate, no work units),
-    batching (256-instance ensemble, 100 steps in one CUDA graph, autotuned,
-    vs 256 sequential single-instance runs) and differentiation (forward +
-    reverse mode of a 203k-particle plate, 100 steps, checkpoints every 10)."""
+    """The other forms on the same GPU: precision (FP64 vs mixed step on the
+    benchmark plate, no work units, mesh and search every step), neighbour
+    search (per-step mesh and search vs Verlet lists on the benchmark
+    configuration), batching (256-instance ensemble, 100 steps in one CUDA
+    graph, autotuned, vs 256 sequential single-instance runs) and
+    differentiation (forward + reverse mode of a 203k-particle plate, 100
+    steps, checkpoints every 10)."""
     import torch
     import synth
     from paper_1805_05128_gb300 import Simulation
@@ -325,7 +336,34 @@ def run_extras(args, dev) -> dict:
     res["speedup_mixed_over_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
     out["precision"] = res
 
-    # (2) batching
+    # (2) neighbour search: the per-step mesh and pair search against Verlet lists (the
+    # benchmark's work units and rebalancing, same inputs)
+    prob_u = synth.plate_impact(units=64, n_steps=500, **WORKLOADS[args.workload])
+    gen = synth.problem_generators(prob_u)
+    ns = {}
+    for beta in (0.0, args.beta if args.beta > 0 else BETA):
+        sim = Simulation(prob_u, precision="mixed", generators=gen, n_upd=10, cell_beta=beta, device=dev)
+        sim.assign()
+        sim.build_cells()
+        sim.step(10)
+        b0 = sim.list_builds()[0] if beta > 0 else 0
+        torch.cuda.synchronize()
+        sim.profile(True)
+        e0, e1 = ev(), ev()
+        e0.record()
+        sim.step(100)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        pair_ms, pair_launches, _ = sim.profile_read()
+        ns["per_step_search" if beta == 0 else f"verlet_beta_{beta}"] = {
+            "value": prob_u.n * 100 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / 100,
+            "pair_kernel_ms": pair_ms / max(pair_launches, 1),
+            "mesh_and_search_per_100_steps": 100 if beta == 0 else sim.list_builds()[0] - b0}
+        sim.close()
+    out["neighbour_search"] = ns
+
+    # (3) batching
     probs = synth.ensemble()
     n_tot = sum(q.n for q in probs)
     tune = ens.autotune(probs, cell_betas=(0.0, 0.15, 0.3), pair_blocks=(3, 0), n_steps=5, reps=1, device=dev)
@@ -347,7 +385,7 @@ def run_extras(args, dev) -> dict:
         "tuning": {"cell_beta": tune.cell_beta, "pair_blocks_per_sm": tune.pair_blocks,
                    "ms_per_step": {f"{k[0]}/{k[1]}": v for k, v in tune.timings.items()}}}
 
-    # (3) differentiation
+    # (4) differentiation
     from paper_1805_05128_gb300.adjoint import RunSpec, csph_run
     q = synth.plate_impact(25, (120, 120, 13), a=1e-4, v=1000.0, units=0)
     A = q.arrays
@@ -392,11 +430,12 @@ def run_extras(args, dev) -> dict:
 
 
 def pair_traffic_bytes(args):
-    """DRAM bytes per pair-kernel launch of the benchmark workload, from the
-    committed ncu summary; None unless that summary was taken on the current
-    k_pair.cu source and the mixed path."""
+    """DRAM bytes per launch of the dominant kernel of the benchmark workload,
+    from the committed ncu summary of that kernel; None unless the summary was
+    taken on the current k_pair.cu source and the mixed path."""
     import re
-    path = os.path.join(ROOT, "profiles", "k_pair_plate_impact_387k.md")
+    name = "k_pair_lists" if args.beta > 0 else "k_pair"
+    path = os.path.join(ROOT, "profiles", f"{name}_plate_impact_387k.md")
     if args.precision != "mixed" or not os.path.exists(path):
         return None
     text = open(path).read()
@@ -421,6 +460,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="csph", choices=["csph", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--beta", type=float, default=BETA,
+                    help="Verlet buffer beta (0: mesh and pairs found every step)")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
