@@ -55,17 +55,46 @@ __device__ __forceinline__ void red_merge(Red& a, const Red& b) {
   a.viol = a.viol > b.viol ? a.viol : b.viol;
 }
 
-// Block-wide reduction of Red through shared memory; result in thread 0.
-__device__ void block_reduce(Red& r) {
-  __shared__ Red sh[kBlock];
-  int t = threadIdx.x;
-  sh[t] = r;
-  __syncthreads();
-  for (int w = kBlock / 2; w > 0; w >>= 1) {
-    if (t < w) red_merge(sh[t], sh[t + w]);
-    __syncthreads();
+__device__ __forceinline__ Red shfl_red(const Red& r, int o) {
+  Red q;
+  for (int a = 0; a < 3; ++a) {
+    q.lo[a] = __shfl_xor_sync(0xffffffffu, r.lo[a], o);
+    q.hi[a] = __shfl_xor_sync(0xffffffffu, r.hi[a], o);
   }
-  if (t == 0) r = sh[0];
+  q.d1 = __shfl_xor_sync(0xffffffffu, r.d1, o);
+  q.d2 = __shfl_xor_sync(0xffffffffu, r.d2, o);
+  q.dtmin = __shfl_xor_sync(0xffffffffu, r.dtmin, o);
+  q.viol = __shfl_xor_sync(0xffffffffu, r.viol, o);
+  return q;
+}
+
+// Block-wide reduction of Red: butterfly within each warp, then the warp
+// results through shared memory; result in thread 0.  Every merge is a
+// min / max / top-2 of integer keys, so the order does not change the result.
+__device__ void block_reduce(Red& r) {
+  __shared__ Red sh[kBlock / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) red_merge(r, shfl_red(r, o));
+  const int t = threadIdx.x;
+  if ((t & 31) == 0) sh[t >> 5] = r;
+  __syncthreads();
+  if (t == 0)
+    for (int w = 1; w < kBlock / 32; ++w) red_merge(r, sh[w]);
+}
+
+// Block minimum of the dt keys only (a step's k_derive); result in thread 0.
+__device__ long long block_min_key(long long k) {
+  __shared__ long long sh[kBlock / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long q = __shfl_xor_sync(0xffffffffu, k, o);
+    k = q < k ? q : k;
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = k;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < kBlock / 32; ++w) k = sh[w] < k ? sh[w] : k;
+  return k;
 }
 
 __device__ __forceinline__ void write_part(BlockPart* part, const Red& r) {
@@ -117,6 +146,11 @@ __global__ void k_derive(DevParams P, sph_state s, const int64_t* __restrict__ b
       if (P.dim >= 3) r.lo[2] = r.hi[2] = dkey(s.z[p]);
       r.d1 = dkey(d);
     }
+  }
+  if (!with_bbox) {   // a step's dt: only the minimum is read (the other partials come from k_kick_drift)
+    const long long k = block_min_key(r.dtmin);
+    if (threadIdx.x == 0) part[blockIdx.x].dtmin = k;
+    return;
   }
   block_reduce(r);
   if (threadIdx.x == 0) write_part(part, r);
