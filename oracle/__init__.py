@@ -47,7 +47,8 @@ class _Material(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("dim", C.c_int), ("kernel", C.c_int), ("kappa", C.c_double),
                 ("eta", C.c_double), ("cfl", C.c_double), ("cell_beta", C.c_double),
-                ("cell_cap", C.c_int64), ("n_mat", C.c_int), ("mat", _Material * MAX_MAT)]
+                ("cell_cap", C.c_int64), ("n_mat", C.c_int), ("mat", _Material * MAX_MAT),
+                ("order", C.c_int)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -134,11 +135,13 @@ class Params:
     cell_beta: float = 0.0
     cell_cap: int = 1 << 26
     materials: list = field(default_factory=lambda: [Material()])
+    order: int = 1              # 2: states reconstructed to the pair midpoint (see orc_rates)
 
     def cs(self) -> _Params:
         p = _Params()
         p.dim, p.kernel, p.kappa, p.eta, p.cfl = self.dim, self.kernel, self.kappa, self.eta, self.cfl
         p.cell_beta, p.cell_cap, p.n_mat = self.cell_beta, self.cell_cap, len(self.materials)
+        p.order = self.order
         for i, m in enumerate(self.materials):
             p.mat[i].eos, p.mat[i].gamma, p.mat[i].rho0 = m.eos, m.gamma, m.rho0
             p.mat[i].c0, p.mat[i].p_inf, p.mat[i].s_a = m.c0, m.p_inf, m.s_a
@@ -256,6 +259,22 @@ def rates(p: Params, s: State, pi, pj):
     lib().orc_rates(C.byref(pc), C.byref(sc), len(pi), pi.ctypes.data_as(_IP), pj.ctypes.data_as(_IP))
 
 
+def pair_gradients(p: Params, s: State):
+    """SPH gradients of P and v used by the order-2 reconstruction, at the
+    state's d and P (call derive first): (n, 3) and (n, 3, 3) arrays,
+    gV[i, a, b] = d v_a / d x_b."""
+    pi, pj = pairs(p, s)
+    n = s.n
+    gP = np.zeros(3 * n)
+    gV = np.zeros(9 * n)
+    pc, sc = p.cs(), s.cs()
+    L = lib()
+    L.orc_pair_gradients.restype = None
+    L.orc_pair_gradients(C.byref(pc), C.byref(sc), C.c_int64(len(pi)), pi.ctypes.data_as(_IP),
+                         pj.ctypes.data_as(_IP), _dp(gP), _dp(gV))
+    return gP.reshape(n, 3), gV.reshape(n, 3, 3)
+
+
 def eval_rates(p: Params, s: State) -> int:
     pc, sc = p.cs(), s.cs()
     n = lib().orc_eval_rates(C.byref(pc), C.byref(sc))
@@ -337,11 +356,11 @@ _EOS_IDS = {"ideal": EOS_IDEAL, "stiffened": EOS_STIFFENED, "tait": EOS_TAIT,
 _KERNEL_IDS = {"cubic": KERNEL_CUBIC, "wendland_c2": KERNEL_WENDLAND_C2}
 
 
-def from_problem(prob, cell_cap: int = 1 << 26):
+def from_problem(prob, cell_cap: int = 1 << 26, order: int = 1):
     """Oracle Params and State for a ``synth.Problem``."""
     mats = [Material(_EOS_IDS[m.eos], m.gamma, m.rho0, m.c0, m.p_inf, m.s_a) for m in prob.materials]
     p = Params(dim=prob.dim, kernel=_KERNEL_IDS[prob.kernel], kappa=prob.kappa, eta=prob.eta,
-               cfl=prob.cfl, cell_beta=0.0, cell_cap=cell_cap, materials=mats)
+               cfl=prob.cfl, cell_beta=0.0, cell_cap=cell_cap, materials=mats, order=order)
     return p, State(prob.dim, prob.arrays, prob.mat)
 
 
@@ -379,7 +398,7 @@ def rates_vjp(p: Params, s: State, pi, pj, ga, gr, gE):
                          _dp(ga), _dp(gr), _dp(gE), _dp(out["bx"]), _dp(out["bv"]), _dp(out["brho"]),
                          _dp(out["bE"]), _dp(out["bpar"]))
     if rc != 0:
-        raise ValueError("oracle rates VJP supports the cubic kernel with ideal/stiffened gas only")
+        raise ValueError("oracle rates VJP supports the first-order scheme, cubic kernel, ideal/stiffened gas")
     return out
 
 

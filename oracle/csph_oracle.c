@@ -313,11 +313,67 @@ int64_t orc_pairs_cells(const orc_params* p, const orc_state* s, int64_t cap, in
  * grad_i W_ij = -e^R W'_ij (Sec. 4.1).  Each pair contributes to both
  * particles; from j's side e^R flips sign, so v*^R flips and P* is unchanged. */
 /* ------------------------------------------------------------------------ */
+/* Second-order variant (order = 2).  Sec. 4.1 feeds the particle values
+ * v_i^R, v_j^R (and P_i, P_j) to the Riemann solver; the cited CSPH scheme
+ * may instead reconstruct the states at the contact point between the two
+ * particles, and the paper gives no formula for it.  Reading used here:
+ *  - SPH gradients of P and of the velocity over the same pair set, h_ij and
+ *    W' as the rates:  grad q_i = sum_j V_j (q_j - q_i) (-W'_ij) e^R_ij
+ *    (exact for a linear field when the kernel is normalised);
+ *  - linear extrapolation of P and v^R from each particle to the pair
+ *    midpoint, each increment limited by minmod against the pair jump:
+ *      q_L = q_i + 1/2 minmod(r e.grad q_i, q_j - q_i)
+ *      q_R = q_j - 1/2 minmod(r e.grad q_j, q_j - q_i)
+ *    with e.grad v^R = e . (grad v) . e; so q_i <= q_L <= q_R <= q_j (or the
+ *    reverse) and a linear field gives q_L = q_R = its midpoint value;
+ *  - the acoustic solver on (P_L, v_L; P_R, v_R) with the particles' Z.
+ * The reconstruction is exchange-symmetric (from j's side e^R flips and L, R
+ * swap), so the fluxes keep their antisymmetry.                              */
+static double minmod(double a, double b) {
+  if (a > 0.0 && b > 0.0) return a < b ? a : b;
+  if (a < 0.0 && b < 0.0) return a > b ? a : b;
+  return 0.0;
+}
+
+/* grad P (3 per particle) and grad v (9 per particle, [a][b] = d v_a / d x_b). */
+void orc_pair_gradients(const orc_params* p, const orc_state* s, int64_t npairs, const int32_t* pi,
+                           const int32_t* pj, double* gP, double* gV) {
+  for (int64_t i = 0; i < 3 * s->n; ++i) gP[i] = 0.0;
+  for (int64_t i = 0; i < 9 * s->n; ++i) gV[i] = 0.0;
+  for (int64_t k = 0; k < npairs; ++k) {
+    int64_t i = pi[k], j = pj[k];
+    double e[3] = {s->x[j] - s->x[i], p->dim >= 2 ? s->y[j] - s->y[i] : 0.0, p->dim >= 3 ? s->z[j] - s->z[i] : 0.0};
+    double r = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    if (r == 0.0) continue;
+    for (int a = 0; a < 3; ++a) e[a] /= r;
+    double hij = p->eta * (s->d[i] + s->d[j]) * 0.5;
+    double w = -orc_kernel_dw(p->kernel, p->dim, p->kappa, r, hij);   /* -W' >= 0 */
+    double Vi = s->m[i] / s->rho[i], Vj = s->m[j] / s->rho[j];
+    double dP = s->P[j] - s->P[i];
+    double dv[3] = {get(s->vx, j) - get(s->vx, i), get(s->vy, j) - get(s->vy, i), get(s->vz, j) - get(s->vz, i)};
+    /* from j's side both (q_i - q_j) and e^R change sign: the same product */
+    for (int b = 0; b < 3; ++b) {
+      gP[3 * i + b] += Vj * dP * w * e[b];
+      gP[3 * j + b] += Vi * dP * w * e[b];
+      for (int a = 0; a < 3; ++a) {
+        gV[9 * i + 3 * a + b] += Vj * dv[a] * w * e[b];
+        gV[9 * j + 3 * a + b] += Vi * dv[a] * w * e[b];
+      }
+    }
+  }
+}
+
 void orc_rates(const orc_params* p, orc_state* s, int64_t npairs, const int32_t* pi, const int32_t* pj) {
   for (int64_t i = 0; i < s->n; ++i) {
     s->drho[i] = 0.0; s->dE[i] = 0.0; s->ax[i] = 0.0;
     if (s->ay) s->ay[i] = 0.0;
     if (s->az) s->az[i] = 0.0;
+  }
+  double *gP = NULL, *gV = NULL;
+  if (p->order == 2) {
+    gP = (double*)malloc(sizeof(double) * 3 * (size_t)(s->n > 0 ? s->n : 1));
+    gV = (double*)malloc(sizeof(double) * 9 * (size_t)(s->n > 0 ? s->n : 1));
+    orc_pair_gradients(p, s, npairs, pi, pj, gP, gV);
   }
   for (int64_t k = 0; k < npairs; ++k) {
     int64_t i = pi[k], j = pj[k];
@@ -330,9 +386,27 @@ void orc_rates(const orc_params* p, orc_state* s, int64_t npairs, const int32_t*
     double vRi = get(s->vx, i) * ex + get(s->vy, i) * ey + get(s->vz, i) * ez;
     double vRj = get(s->vx, j) * ex + get(s->vy, j) * ey + get(s->vz, j) * ez;
     double Zi = s->rho[i] * s->c[i], Zj = s->rho[j] * s->c[j];
+    double PL = s->P[i], PR = s->P[j], vL = vRi, vR = vRj;
+    if (p->order == 2) {
+      const double e[3] = {ex, ey, ez};
+      double sPi = 0.0, sPj = 0.0, svi = 0.0, svj = 0.0;
+      for (int b = 0; b < 3; ++b) {
+        sPi += gP[3 * i + b] * e[b];
+        sPj += gP[3 * j + b] * e[b];
+        for (int a = 0; a < 3; ++a) {
+          svi += e[a] * gV[9 * i + 3 * a + b] * e[b];
+          svj += e[a] * gV[9 * j + 3 * a + b] * e[b];
+        }
+      }
+      double dP = s->P[j] - s->P[i], dv = vRj - vRi;
+      PL = s->P[i] + 0.5 * minmod(r * sPi, dP);
+      PR = s->P[j] - 0.5 * minmod(r * sPj, dP);
+      vL = vRi + 0.5 * minmod(r * svi, dv);
+      vR = vRj - 0.5 * minmod(r * svj, dv);
+    }
     double Ps, vs;
-    if (Zi + Zj > 0.0) orc_riemann_acoustic(s->P[i], s->P[j], Zi, Zj, vRi, vRj, &Ps, &vs);
-    else { Ps = 0.5 * (s->P[i] + s->P[j]); vs = 0.5 * (vRi + vRj); }
+    if (Zi + Zj > 0.0) orc_riemann_acoustic(PL, PR, Zi, Zj, vL, vR, &Ps, &vs);
+    else { Ps = 0.5 * (PL + PR); vs = 0.5 * (vL + vR); }
     double hij = p->eta * (s->d[i] + s->d[j]) * 0.5;
     double dW = orc_kernel_dw(p->kernel, p->dim, p->kappa, r, hij);   /* W'_ij <= 0 */
     double Vi = s->m[i] / s->rho[i], Vj = s->m[j] / s->rho[j];
@@ -349,6 +423,8 @@ void orc_rates(const orc_params* p, orc_state* s, int64_t npairs, const int32_t*
     s->dE[i] += fi * vs;
     s->dE[j] -= fj * vs;
   }
+  free(gP);
+  free(gV);
 }
 
 /* Derive e, P, c, d, search pairs through cells, evaluate rates. */
@@ -662,6 +738,7 @@ static void cubic_dw_derivs(int dim, double r, double h, double* dw, double* dwd
 int orc_rates_vjp(const orc_params* p, const orc_state* s, int64_t npairs, const int32_t* pi, const int32_t* pj,
                   const double* ga, const double* gr, const double* gE,
                   double* bx, double* bv, double* brho, double* bE, double* bpar) {
+  if (p->order == 2) return -2;   /* the reverse mode covers the first-order scheme only */
   int64_t n = s->n;
   int dim = p->dim;
   if (p->kernel != ORC_KERNEL_CUBIC) return -1;
@@ -837,6 +914,7 @@ int orc_step_replay(const orc_params* p, orc_state* s, int n_steps, int rates_va
  * bpar (2) accumulates dL/d(c0, gamma). */
 int orc_step_vjp(const orc_params* p, const orc_state* s, double dt, double* yx, double* yv, double* yrho,
                  double* yE, double* ya, double* ydrho, double* ydE, double* bpar) {
+  if (p->order == 2) return -2;   /* first-order scheme only */
   int64_t n = s->n;
   int dim = p->dim;
   double hdt = 0.5 * dt;

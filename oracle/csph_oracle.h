@@ -50,6 +50,8 @@ typedef struct {
   int64_t cell_cap; /* maximum number of cells of the dense grid */
   int n_mat;
   orc_material mat[ORC_MAX_MAT];
+  int order;      /* 1 (particle-centre states, Sec. 4.1 as written) or 2 (states reconstructed
+                     to the pair midpoint, the NEXT variant; see orc_rates) */
 } orc_params;
 
 /* Particle state, structure of arrays, host memory.  For dim < 3 the unused
@@ -92,6 +94,11 @@ int64_t orc_pairs_cells(const orc_params* p, const orc_state* s, int64_t cap, in
 
 /* ---- CSPH rates over a pair list ---- */
 void orc_rates(const orc_params* p, orc_state* s, int64_t npairs, const int32_t* pi, const int32_t* pj);
+/* SPH gradients used by the order-2 reconstruction: gP (3 per particle) and
+ * gV (9 per particle, [a][b] = d v_a / d x_b), grad q_i = sum_j V_j (q_j - q_i)
+ * (-W'_ij) e^R_ij over the pair list, at the state's d, P. */
+void orc_pair_gradients(const orc_params* p, const orc_state* s, int64_t npairs, const int32_t* pi,
+                        const int32_t* pj, double* gP, double* gV);
 int64_t orc_eval_rates(const orc_params* p, orc_state* s);   /* derive + pairs + rates; returns npairs or <0 */
 
 /* ---- KDK leapfrog ---- */
