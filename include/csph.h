@@ -87,6 +87,10 @@ typedef struct sph_params {
   double* generators; /* device, K x unit_dim, read and updated by sph_step's rebalancing */
   const sph_material* materials; /* host, n_mat entries, or NULL to use mat[]; copied by sph_init
                                     (one material per instance gives per-instance EOS parameters) */
+  int32_t order;      /* 1 (or 0): the particles' own P, v^R feed the pair Riemann solver (Sec. 4.1);
+                         2: P and v^R extrapolated to the pair midpoint with SPH gradients, minmod-
+                         limited against the pair jump (an extension; needs cell_beta = 0, no adjoint) */
+  int32_t pad2_;
 } sph_params;
 
 /* Particle state: structure of arrays in device memory, n elements each.

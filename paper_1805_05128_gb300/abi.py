@@ -39,7 +39,8 @@ class sph_params(C.Structure):
                 ("cell_cap", C.c_int64), ("mat", sph_material * SPH_MAX_MAT),
                 ("n_units", C.c_int32), ("unit_dim", C.c_int32), ("n_upd", C.c_int32), ("pair_blocks_per_sm", C.c_int32),
                 ("theta", C.c_double), ("sigma", C.c_double), ("gamma_b", C.c_double), ("beta_sh", C.c_double),
-                ("generators", C.c_void_p), ("materials", C.c_void_p)]
+                ("generators", C.c_void_p), ("materials", C.c_void_p),
+                ("order", C.c_int32), ("pad2_", C.c_int32)]
 
 
 STATE_F64 = ("x", "y", "z", "vx", "vy", "vz", "rho", "E", "m")

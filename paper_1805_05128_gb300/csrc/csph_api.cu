@@ -43,7 +43,7 @@ void free_all(sph_handle* h) {
                   h->load_acc, h->adj_bits, h->unit_off, h->unit_list, h->unit_work, h->unit_total, h->unit_stats,
                   h->status, h->counters, h->scratch, h->adj_G,
                   h->adj_GR, h->adj_pair, h->adj_par, h->adj_W, h->adj_store, h->mat_dev, h->vlist, h->vcnt,
-                  h->vref, h->vflag};
+                  h->vref, h->vflag, h->grad_p, h->grad_v};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -116,6 +116,9 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     return fail(nullptr, SPH_ERR_INVALID, "unknown kernel");
   if (p->precision != SPH_PREC_FP64 && p->precision != SPH_PREC_MIXED)
     return fail(nullptr, SPH_ERR_INVALID, "unknown precision");
+  if (p->order < 0 || p->order > 2) return fail(nullptr, SPH_ERR_INVALID, "order must be 1 or 2");
+  if (p->order == 2 && p->cell_beta > 0.0)
+    return fail(nullptr, SPH_ERR_INVALID, "order 2 runs with the per-step neighbour search (cell_beta = 0)");
   if (p->n_mat < 1 || p->n_mat > kMaxMaterials || (p->n_mat > SPH_MAX_MAT && !p->materials))
     return fail(nullptr, SPH_ERR_INVALID, "n_mat out of range (more than SPH_MAX_MAT need params.materials)");
   const sph_material* mats = p->materials ? p->materials : p->mat;
@@ -264,6 +267,18 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     CKI(dalloc(&h->unit_total, 1));
     CKI(cudaMemcpy(h->unit_total, &h->unit_work_total, sizeof(int64_t), cudaMemcpyHostToDevice));
     CKI(dalloc(&h->unit_stats, (size_t)K * 5));
+  }
+
+  // order-2 reconstruction: SPH gradients of P and v in slot order
+  h->order2 = p->order == 2;
+  if (h->order2) {
+    if (p->precision == SPH_PREC_MIXED) {
+      CKI(dalloc(reinterpret_cast<float4**>(&h->grad_p), n));
+      CKI(dalloc(reinterpret_cast<float4**>(&h->grad_v), (size_t)3 * n));
+    } else {
+      CKI(dalloc(reinterpret_cast<D4**>(&h->grad_p), n));
+      CKI(dalloc(reinterpret_cast<D4**>(&h->grad_v), (size_t)3 * n));
+    }
   }
 
   // Verlet lists (cell_beta > 0): capacity per particle from the neighbours of a uniform
@@ -589,6 +604,7 @@ int sph_step_adjoint(sph_handle* h, const sph_ckpt* ck, int n_steps, const sph_s
   if (!h || !ck || !adj_out || !adj_in || !adj_params) return h ? fail(h, SPH_ERR_INVALID, "NULL argument") : SPH_ERR_INVALID;
   if (n_steps < 0 || (n_steps > 0 && !ck->dt)) return fail(h, SPH_ERR_INVALID, "need n_steps >= 0 and the dt record");
   if (h->n_inst != 1) return fail(h, SPH_ERR_INVALID, "the adjoint supports a single instance");
+  if (h->order2) return fail(h, SPH_ERR_INVALID, "the adjoint covers the first-order scheme (order 1)");
   if (h->dp.kernel != SPH_KERNEL_CUBIC) return fail(h, SPH_ERR_INVALID, "the adjoint supports the cubic spline");
   for (int k = 0; k < h->dp.n_mat; ++k)
     if (h->mat_h[k].eos != SPH_EOS_IDEAL && h->mat_h[k].eos != SPH_EOS_STIFFENED)

@@ -161,6 +161,12 @@ struct sph_handle {
   int32_t* vcnt = nullptr;            // [n] entries of slot i
   double* vref = nullptr;             // [4 n] x, y, z, d of each particle at the last build
   int* vflag = nullptr;               // [0]: rebuild in this step; [1]: lists invalid; [2]: builds done
+
+  // order-2 reconstruction (sph_params.order = 2): SPH gradients in slot order,
+  // the pair kernel's precision: grad P, then grad v_x, grad v_y, grad v_z
+  bool order2 = false;
+  void* grad_p = nullptr;             // [n] float4 / D4
+  void* grad_v = nullptr;             // [3 n] float4 / D4
 };
 
 namespace csph {

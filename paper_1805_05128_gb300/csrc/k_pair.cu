@@ -75,11 +75,17 @@ struct PairArgs {
   double* vref;      // x, y, z, d per particle at the build (4 arrays of n)
   int* vflag;        // [0] rebuild now, [1] lists invalid, [2] builds done
   int vcap;
+  // order-2 reconstruction: SPH gradients in slot order, the kernel's precision;
+  // gP: grad P; gV: grad v_x, grad v_y, grad v_z (three arrays of n, consecutive)
+  void* gP;
+  void* gV;
 };
 
 constexpr int kModeFwd = 0;    // rates
 constexpr int kModeVjp = 1;    // reverse mode of the rates
 constexpr int kModeList = 2;   // Verlet list build over the (1 + beta) radius
+constexpr int kModeGrad = 3;   // SPH gradients of P and v (order-2 reconstruction)
+constexpr int kModeFwd2 = 4;   // rates with states reconstructed to the pair midpoint
 
 template <bool MIXED>
 struct Ops;
@@ -240,7 +246,20 @@ struct Pair {
 // that is symmetric under the exchange.  So the applied fluxes are
 // antisymmetric bit for bit and momentum and energy are conserved by the
 // pair sums up to the per-particle summation.
-template <bool MIXED, int DIM>
+//
+// Order 2 (ORDER2): P and v^R are extrapolated from each particle to the pair
+// midpoint with the SPH gradients, each increment limited by minmod against
+// the pair jump (q_L = q_i + minmod(r e.grad q_i, q_j - q_i)/2, q_R = q_j -
+// minmod(r e.grad q_j, q_j - q_i)/2, e.grad v^R = e.(grad v).e), and the
+// acoustic solver takes (P_L, v_L; P_R, v_R).  Written with the same
+// uncontracted, sign-symmetric operations, j's side sees exactly (P_R, P_L,
+// -v_R, -v_L), so the antisymmetry is kept.
+template <typename T>
+__device__ __forceinline__ T minmod(T a, T b) {
+  return (a > T(0) && b > T(0)) ? (a < b ? a : b) : ((a < T(0) && b < T(0)) ? (a > b ? a : b) : T(0));
+}
+
+template <bool MIXED, int DIM, bool ORDER2 = false>
 struct FwdAcc {
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
@@ -249,6 +268,22 @@ struct FwdAcc {
   Kahan<T> s_rho, s_fx, s_fy, s_fz, s_q;
   T dmax = T(0);
   int last_adj = -1;
+  V4 gPi{}, gVi[3]{};   // order 2: i's gradients (set by the caller)
+
+  // e . g, in a fixed uncontracted order (sign-symmetric in e)
+  static __device__ __forceinline__ T dot_e(const V4& g, T ex, T ey, T ez) {
+    T s = mul_(g.x, ex);
+    if (DIM >= 2) s = fma_(g.y, ey, s);
+    if (DIM >= 3) s = fma_(g.z, ez, s);
+    return s;
+  }
+  // e . (grad v) . e  (even in e)
+  static __device__ __forceinline__ T dvv(const V4* gv, T ex, T ey, T ez) {
+    T s = mul_(ex, dot_e(gv[0], ex, ey, ez));
+    if (DIM >= 2) s = fma_(ey, dot_e(gv[1], ex, ey, ez), s);
+    if (DIM >= 3) s = fma_(ez, dot_e(gv[2], ex, ey, ez), s);
+    return s;
+  }
 
   __device__ __forceinline__ void pair(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi, const V2& Ci,
                                        int ui, int64_t j, T sx, T sy, T sz) {
@@ -278,16 +313,32 @@ struct FwdAcc {
     T vi = Bi.x * ex, vj = Bj.x * ex;
     if (DIM >= 2) { vi = fma_(Bi.y, ey, vi); vj = fma_(Bj.y, ey, vj); }
     if (DIM >= 3) { vi = fma_(Bi.z, ez, vi); vj = fma_(Bj.z, ez, vj); }
-    const T Zi = Ci.y, Zj = Cj.y, Pi = Ci.x, Pj = Cj.x;
+    const T Zi = Ci.y, Zj = Cj.y;
+    T Pi = Ci.x, Pj = Cj.x, wi = vi, wj = vj;   // states fed to the solver
+    if constexpr (ORDER2) {
+      const V4* __restrict__ GP = reinterpret_cast<const V4*>(a.gP);
+      const V4* __restrict__ GV = reinterpret_cast<const V4*>(a.gV);
+      V4 gvj[3];
+      gvj[0] = GV[j];
+      if (DIM >= 2) gvj[1] = GV[a.n + j];
+      if (DIM >= 3) gvj[2] = GV[2 * a.n + j];
+      const T dP = sub_(Pj, Pi), dv = sub_(vj, vi);
+      const T sPi = mul_(r, dot_e(gPi, ex, ey, ez)), sPj = mul_(r, dot_e(GP[j], ex, ey, ez));
+      const T svi = mul_(r, dvv(gVi, ex, ey, ez)), svj = mul_(r, dvv(gvj, ex, ey, ez));
+      Pi = add_(Ci.x, mul_(T(0.5), minmod(sPi, dP)));
+      Pj = sub_(Cj.x, mul_(T(0.5), minmod(sPj, dP)));
+      wi = add_(vi, mul_(T(0.5), minmod(svi, dv)));
+      wj = sub_(vj, mul_(T(0.5), minmod(svj, dv)));
+    }
     const T zs = add_(Zi, Zj);
     T Ps, vs;
     if (zs > T(0)) {
       const T izs = rcp_(zs);
-      Ps = mul_(add_(add_(mul_(Zj, Pi), mul_(Zi, Pj)), mul_(mul_(Zi, Zj), sub_(vi, vj))), izs);
-      vs = mul_(add_(add_(mul_(Zi, vi), mul_(Zj, vj)), sub_(Pi, Pj)), izs);
+      Ps = mul_(add_(add_(mul_(Zj, Pi), mul_(Zi, Pj)), mul_(mul_(Zi, Zj), sub_(wi, wj))), izs);
+      vs = mul_(add_(add_(mul_(Zi, wi), mul_(Zj, wj)), sub_(Pi, Pj)), izs);
     } else {
       Ps = mul_(T(0.5), add_(Pi, Pj));
-      vs = mul_(T(0.5), add_(vi, vj));
+      vs = mul_(T(0.5), add_(wi, wj));
     }
     const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * add_(Ai.w, Aj.w);
     const T dW = MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij)
@@ -365,9 +416,12 @@ constexpr int kWarps = kPairBlock / 32;
 constexpr int kRow = kListCap + 2;   // padded row stride (16-bit entries): lane rows fall in distinct banks
 
 template <bool MIXED, int DIM, int MODE>
-__global__ void __launch_bounds__(kPairBlock, MODE == kModeVjp ? (MIXED ? 4 : 2) : (MIXED ? 6 : 4)) k_pair(PairArgs a) {
+__global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kModeFwd2) ? (MIXED ? 4 : 2)
+                                                 : (MODE == kModeGrad ? (MIXED ? 5 : 3) : (MIXED ? 6 : 4)))
+    k_pair(PairArgs a) {
   constexpr bool VJP = MODE == kModeVjp;
   constexpr bool LIST = MODE == kModeList;
+  constexpr bool GRAD = MODE == kModeGrad;
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
   using V4 = typename P::V4;
@@ -451,8 +505,51 @@ __global__ void __launch_bounds__(kPairBlock, MODE == kModeVjp ? (MIXED ? 4 : 2)
     if constexpr (VJP) { Gi = Gp[ii]; Ri = Rp[ii]; }
     Kahan<T> s_bx[3], s_bv[3], s_bP, s_bZ, s_bV, s_bd, s_brho;
 
-    FwdAcc<MIXED, DIM> fw;
+    FwdAcc<MIXED, DIM, MODE == kModeFwd2> fw;
+    if constexpr (MODE == kModeFwd2) {
+      fw.gPi = reinterpret_cast<const V4*>(a.gP)[ii];
+      const V4* GV = reinterpret_cast<const V4*>(a.gV);
+      fw.gVi[0] = GV[ii];
+      if (DIM >= 2) fw.gVi[1] = GV[a.n + ii];
+      if (DIM >= 3) fw.gVi[2] = GV[2 * a.n + ii];
+    }
     auto pair_flux = [&](int64_t j, T sx, T sy, T sz) { fw.pair(a, i, Ai, Bi, Ci, ui, j, sx, sy, sz); };
+
+    // SPH gradients (GRAD): grad q_i = sum_j V_j (q_j - q_i) (-W'_ij) e^R for q = P, v_x, v_y, v_z
+    T gP[3] = {T(0), T(0), T(0)}, gV[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+    auto pair_grad = [&](int64_t j, T sx, T sy, T sz) {
+      if (j == i) return;
+      const V4 Aj = A[j];
+      const V4 Bj = B[j];
+      const V2 Cj = C[j];
+      T dx, dy, dz;
+      if (MIXED) {
+        dx = (Aj.x - Ai.x) + sx;
+        dy = DIM >= 2 ? (Aj.y - Ai.y) + sy : T(0);
+        dz = DIM >= 3 ? (Aj.z - Ai.z) + sz : T(0);
+      } else {
+        dx = __dsub_rn(Aj.x, Ai.x);
+        dy = DIM >= 2 ? __dsub_rn(Aj.y, Ai.y) : 0.0;
+        dz = DIM >= 3 ? __dsub_rn(Aj.z, Ai.z) : 0.0;
+      }
+      const T r2 = P::r2_of(dx, dy, dz);
+      if (!(r2 > T(0))) return;
+      const T ir = rsqrt_(r2);
+      const T r = r2 * ir;
+      const T e[3] = {dx * ir, dy * ir, dz * ir};
+      const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * (Ai.w + Aj.w);
+      const T w = -(MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij)
+                          : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij));
+      const T f = Bj.w * w;
+      const T dP = Cj.x - Ci.x;
+      const T dv[3] = {Bj.x - Bi.x, Bj.y - Bi.y, Bj.z - Bi.z};
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        gP[b] += f * dP * e[b];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) gV[c][b] += f * dv[c] * e[b];
+      }
+    };
 
     // Reverse mode of the pair's contributions (VJP = true): the derivative of
     // the pair's terms in a, drho, dE of both i and j, contracted with their
@@ -553,6 +650,8 @@ __global__ void __launch_bounds__(kPairBlock, MODE == kModeVjp ? (MIXED ? 4 : 2)
           }
         } else if constexpr (VJP) {
           pair_vjp(j, (T)t.y, (T)t.z, (T)t.w);
+        } else if constexpr (GRAD) {
+          pair_grad(j, (T)t.y, (T)t.z, (T)t.w);
         } else {
           pair_flux(j, (T)t.y, (T)t.z, (T)t.w);
         }
@@ -628,6 +727,23 @@ __global__ void __launch_bounds__(kPairBlock, MODE == kModeVjp ? (MIXED ? 4 : 2)
     }
     if (act) flush();
 
+    if constexpr (GRAD) {
+      if (act) {
+        V4* GP = reinterpret_cast<V4*>(a.gP);
+        V4* GV = reinterpret_cast<V4*>(a.gV);
+        V4 q{};
+        q.x = gP[0]; q.y = gP[1]; q.z = gP[2];
+        GP[i] = q;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          V4 g{};
+          g.x = gV[c][0]; g.y = gV[c][1]; g.z = gV[c][2];
+          GV[(int64_t)c * a.n + i] = g;
+        }
+      }
+      __syncwarp();
+      continue;
+    }
     if constexpr (LIST) {
       if (act) {
         if (vc > a.vcap) set_status(a.status, SPH_ERR_CAPACITY);
@@ -955,6 +1071,8 @@ PairArgs make_args(sph_handle* h, const sph_state& s) {
   a.vref = h->vref;
   a.vflag = h->vflag;
   a.vcap = h->vcap;
+  a.gP = h->grad_p;
+  a.gV = h->grad_v;
   return a;
 }
 
@@ -1018,9 +1136,24 @@ cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(&h->counters[4], 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  if (h->order2) {
+    // SPH gradients first (their own pass over the same pair set), then the rates
+    a.gP = h->grad_p;
+    a.gV = h->grad_v;
+    e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, kModeGrad>(h, a, st)
+                                          : launch_dim<false, kModeGrad>(h, a, st);
+    h->launches += 1;
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(&h->counters[5], 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
   if ((e = prof_record(h, true, st)) != cudaSuccess) return e;
-  e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, kModeFwd>(h, a, st)
-                                        : launch_dim<false, kModeFwd>(h, a, st);
+  if (h->order2)
+    e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, kModeFwd2>(h, a, st)
+                                          : launch_dim<false, kModeFwd2>(h, a, st);
+  else
+    e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, kModeFwd>(h, a, st)
+                                          : launch_dim<false, kModeFwd>(h, a, st);
   h->launches += 1;
   if (e == cudaSuccess) e = prof_record(h, false, st);
   return e;

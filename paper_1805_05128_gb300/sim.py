@@ -30,7 +30,7 @@ class Simulation:
     def __init__(self, problems, precision: str = "mixed", units: int | None = None,
                  generators=None, n_upd: int | None = None, theta: float = 0.25, sigma: float = 0.5,
                  gamma_b: float = 1.0, beta_sh: float = 0.45, cell_cap: int = 1 << 24, cell_beta: float = 0.0,
-                 pair_blocks_per_sm: int = 0,
+                 pair_blocks_per_sm: int = 0, order: int = 1,
                  device: str | torch.device = "cuda:0"):
         if not isinstance(problems, (list, tuple)):
             problems = [problems]
@@ -92,6 +92,7 @@ class Simulation:
         prm.n_upd = (p0.n_upd if n_upd is None else n_upd) if self.K > 0 else 0
         prm.theta, prm.sigma, prm.gamma_b, prm.beta_sh = theta, sigma, gamma_b, beta_sh
         prm.pair_blocks_per_sm = pair_blocks_per_sm
+        prm.order = order
         prm.generators = self.gen.data_ptr() if self.gen is not None else None
         self.params = prm
         self.precision = precision

@@ -44,7 +44,7 @@ def test_struct_layouts_match_header(lib, tmp_path):
     gives the structs of include/csph.h."""
     import subprocess
     prog = tmp_path / "layout.c"
-    fields = {"sph_params": ["dim", "kappa", "cell_cap", "mat", "n_units", "pair_blocks_per_sm", "theta", "generators", "materials"],
+    fields = {"sph_params": ["dim", "kappa", "cell_cap", "mat", "n_units", "pair_blocks_per_sm", "theta", "generators", "materials", "order"],
               "sph_state": ["n", "x", "mat", "ax", "d", "id", "unit"],
               "sph_material": ["eos", "gamma", "s_a"]}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "csph.h"', "int main(void){"]
