@@ -221,7 +221,7 @@ __device__ __forceinline__ void rotate3(const double ax[3], double alpha, const 
 }
 
 // ---------------------------------------------------------------------------
-// Balancing update (single block, thread k = generator k):
+// Balancing update (one block per generator k, then one block to apply):
 //   eq. (BalancingOffset)       two-body, g_kl = g_k - g_l
 //   eq. (BalancingOffsetRot)    three-body for 2D decompositions, each
 //                               triangle of mutually adjacent units once,
@@ -230,103 +230,120 @@ __device__ __forceinline__ void rotate3(const double ax[3], double alpha, const 
 // D^sh_kl = max(rmax_k, rmax_l) (eq. Horizon).  Loads: caller's, else half
 // the accumulated full-list pair counts.  Resets the accumulators.
 // ---------------------------------------------------------------------------
-__global__ void k_balance(int K, int gdim, double* gen, const double* __restrict__ load_in,
-                          unsigned long long* load_acc, uint32_t* adj_bits, int adj_words,
-                          const double* __restrict__ stats, double theta, double sigma, double gamma_b,
-                          double* shift_out) {
+// Unit k's update (one block per unit, the arithmetic on thread 0): the
+// balancing offsets of unit k and its new generator, into scratch
+// (3 coordinates, then the shift length, per unit).
+__global__ void k_balance_unit(int K, int gdim, const double* __restrict__ gen, const double* __restrict__ load_in,
+                               const unsigned long long* __restrict__ load_acc,
+                               const uint32_t* __restrict__ adj_bits, int adj_words,
+                               const double* __restrict__ stats, double theta, double sigma, double gamma_b,
+                               double* scratch) {
   __shared__ double L[SPH_MAX_UNITS];
   __shared__ double G[SPH_MAX_UNITS * 3];
-  __shared__ double NG[SPH_MAX_UNITS * 3];
-  __shared__ double SH[SPH_MAX_UNITS];
+  __shared__ uint32_t AB[SPH_MAX_UNITS * (SPH_MAX_UNITS / 32)];   // the adjacency bitmap, staged
   const double pi = 3.14159265358979323846;
-  int k = threadIdx.x;
-  if (k < K) {
-    L[k] = load_in ? load_in[k] : 0.5 * (double)load_acc[k];
-    for (int a = 0; a < 3; ++a) G[k * 3 + a] = a < gdim ? gen[k * gdim + a] : 0.0;
+  for (int q = threadIdx.x; q < K; q += blockDim.x) {
+    L[q] = load_in ? load_in[q] : 0.5 * (double)load_acc[q];
+    for (int a = 0; a < 3; ++a) G[q * 3 + a] = a < gdim ? gen[q * gdim + a] : 0.0;
   }
+  for (int q = threadIdx.x; q < K * adj_words; q += blockDim.x) AB[q] = adj_bits[q];
   __syncthreads();
+  const int k = blockIdx.x;
+  if (threadIdx.x != 0 || k >= K) return;
   double sig = (gdim == 2) ? sigma : 0.0;
-  auto adj = [&](int r, int c) -> bool { return (adj_bits[r * adj_words + (c >> 5)] >> (c & 31)) & 1u; };
+  // The neighbours of a unit are walked as the set bits of its bitmap row, in
+  // increasing index order: the same terms in the same order as a scan of all
+  // indices that skips the non-adjacent ones.
   auto dsh = [&](int r, int c) -> double {
     double a = stats[r * 5 + 4], b = stats[c * 5 + 4];
     return a > b ? a : b;
   };
-  if (k < K) {
-    const double* gk = &G[k * 3];
-    double dg2[3] = {0, 0, 0}, dg3[3] = {0, 0, 0};
-    double maxd = 0.0;
-    for (int l = 0; l < K; ++l) {
-      if (l == k || !adj(k, l)) continue;
-      double D = dsh(k, l);
-      if (D > maxd) maxd = D;
-      double den = L[k] + L[l];
-      if (!(den > 0.0)) continue;
-      double gkl[3] = {gk[0] - G[l * 3], gk[1] - G[l * 3 + 1], gk[2] - G[l * 3 + 2]};
-      double nrm = sqrt(gkl[0] * gkl[0] + gkl[1] * gkl[1] + gkl[2] * gkl[2]);
-      if (nrm == 0.0) continue;
-      double f = D * ((L[k] - L[l]) / den) / nrm;
-      for (int a = 0; a < 3; ++a) dg2[a] += f * gkl[a];
-    }
-    if (sig != 0.0) {
-      for (int l = 0; l < K; ++l) {
-        if (l == k || !adj(k, l)) continue;
-        for (int m = l + 1; m < K; ++m) {
-          if (m == k || !adj(k, m) || !adj(l, m)) continue;
-          const double* gl = &G[l * 3];
-          const double* gm = &G[m * 3];
-          double ax = gl[0] - gk[0], ay = gl[1] - gk[1];
-          double bx = gm[0] - gk[0], by = gm[1] - gk[1];
-          double a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
-          double crs = ax * by - ay * bx;
-          double scale2 = a2 > b2 ? a2 : b2;
-          if (fabs(crs) < 1e-12 * scale2) continue;
-          double Dd = 2.0 * crs;
-          double ox = gk[0] + (by * a2 - ay * b2) / Dd;
-          double oy = gk[1] + (ax * b2 - bx * a2) / Dd;
-          double Ls = L[k] + L[l] + L[m];
-          if (!(Ls > 0.0)) continue;
-          double al = pi / 3.0 * (L[l] - L[k]) / Ls;
-          double am = pi / 3.0 * (L[m] - L[k]) / Ls;
-          double ck[3] = {gk[0] - ox, gk[1] - oy, 0.0};
-          double cl[3] = {gl[0] - ox, gl[1] - oy, 0.0};
-          double cm[3] = {gm[0] - ox, gm[1] - oy, 0.0};
-          double axl[3], axm[3], r1[3], r2[3];
-          cross3(ck, cl, axl);
-          cross3(ck, cm, axm);
-          rotate3(axl, al, ck, r1);
-          rotate3(axm, am, r1, r2);
-          for (int a = 0; a < 3; ++a) dg3[a] += r2[a] - ck[a];
-        }
-      }
-      double n3 = sqrt(dg3[0] * dg3[0] + dg3[1] * dg3[1] + dg3[2] * dg3[2]);
-      if (n3 > maxd && n3 > 0.0) {
-        double f = maxd / n3;
-        for (int a = 0; a < 3; ++a) dg3[a] *= f;
-      }
-    }
-    double cnt = stats[k * 5 + 3];
-    double dist2 = 0.0;
-    for (int a = 0; a < gdim; ++a) {
-      double dg = (1.0 - sig) * dg2[a] + sig * dg3[a];
-      double rc = cnt > 0.0 ? stats[k * 5 + a] : gk[a];
-      double ng = (1.0 - theta) * (gk[a] + gamma_b * dg) + theta * rc;
-      NG[k * 3 + a] = ng;
-      dist2 += (ng - gk[a]) * (ng - gk[a]);
-    }
-    SH[k] = sqrt(dist2);
+  const double* gk = &G[k * 3];
+  double dg2[3] = {0, 0, 0}, dg3[3] = {0, 0, 0};
+  double maxd = 0.0;
+  for (int w = 0; w < adj_words; ++w)
+  for (uint32_t bits = AB[k * adj_words + w]; bits; bits &= bits - 1) {
+    const int l = w * 32 + __ffs(bits) - 1;
+    if (l == k || l >= K) continue;
+    double D = dsh(k, l);
+    if (D > maxd) maxd = D;
+    double den = L[k] + L[l];
+    if (!(den > 0.0)) continue;
+    double gkl[3] = {gk[0] - G[l * 3], gk[1] - G[l * 3 + 1], gk[2] - G[l * 3 + 2]};
+    double nrm = sqrt(gkl[0] * gkl[0] + gkl[1] * gkl[1] + gkl[2] * gkl[2]);
+    if (nrm == 0.0) continue;
+    double f = D * ((L[k] - L[l]) / den) / nrm;
+    for (int a = 0; a < 3; ++a) dg2[a] += f * gkl[a];
   }
-  __syncthreads();
-  if (k < K)
-    for (int a = 0; a < gdim; ++a) gen[k * gdim + a] = NG[k * 3 + a];
-  if (k == 0) {
-    double s = 0.0;
-    for (int q = 0; q < K; ++q) s += SH[q];
-    if (shift_out) *shift_out = s;
+  if (sig != 0.0) {
+    for (int wl = 0; wl < adj_words; ++wl)
+    for (uint32_t bl = AB[k * adj_words + wl]; bl; bl &= bl - 1) {
+      const int l = wl * 32 + __ffs(bl) - 1;
+      if (l == k || l >= K) continue;
+      for (int wm = (l + 1) >> 5; wm < adj_words; ++wm)
+      for (uint32_t bm = AB[k * adj_words + wm] & AB[l * adj_words + wm] &
+                         (wm == ((l + 1) >> 5) ? (~0u << ((l + 1) & 31)) : ~0u);
+           bm; bm &= bm - 1) {
+        const int m = wm * 32 + __ffs(bm) - 1;
+        if (m == k || m >= K) continue;
+        const double* gl = &G[l * 3];
+        const double* gm = &G[m * 3];
+        double ax = gl[0] - gk[0], ay = gl[1] - gk[1];
+        double bx = gm[0] - gk[0], by = gm[1] - gk[1];
+        double a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
+        double crs = ax * by - ay * bx;
+        double scale2 = a2 > b2 ? a2 : b2;
+        if (fabs(crs) < 1e-12 * scale2) continue;
+        double Dd = 2.0 * crs;
+        double ox = gk[0] + (by * a2 - ay * b2) / Dd;
+        double oy = gk[1] + (ax * b2 - bx * a2) / Dd;
+        double Ls = L[k] + L[l] + L[m];
+        if (!(Ls > 0.0)) continue;
+        double al = pi / 3.0 * (L[l] - L[k]) / Ls;
+        double am = pi / 3.0 * (L[m] - L[k]) / Ls;
+        double ck[3] = {gk[0] - ox, gk[1] - oy, 0.0};
+        double cl[3] = {gl[0] - ox, gl[1] - oy, 0.0};
+        double cm[3] = {gm[0] - ox, gm[1] - oy, 0.0};
+        double axl[3], axm[3], r1[3], r2[3];
+        cross3(ck, cl, axl);
+        cross3(ck, cm, axm);
+        rotate3(axl, al, ck, r1);
+        rotate3(axm, am, r1, r2);
+        for (int a = 0; a < 3; ++a) dg3[a] += r2[a] - ck[a];
+      }
+    }
+    double n3 = sqrt(dg3[0] * dg3[0] + dg3[1] * dg3[1] + dg3[2] * dg3[2]);
+    if (n3 > maxd && n3 > 0.0) {
+      double f = maxd / n3;
+      for (int a = 0; a < 3; ++a) dg3[a] *= f;
+    }
   }
-  __syncthreads();
+  double cnt = stats[k * 5 + 3];
+  double dist2 = 0.0;
+  for (int a = 0; a < gdim; ++a) {
+    double dg = (1.0 - sig) * dg2[a] + sig * dg3[a];
+    double rc = cnt > 0.0 ? stats[k * 5 + a] : gk[a];
+    double ng = (1.0 - theta) * (gk[a] + gamma_b * dg) + theta * rc;
+    scratch[k * 4 + a] = ng;
+    dist2 += (ng - gk[a]) * (ng - gk[a]);
+  }
+  scratch[k * 4 + 3] = sqrt(dist2);
+}
+
+// New generators, the summed shift (fixed order) and the reset of the load
+// and adjacency accumulators.
+__global__ void k_balance_apply(int K, int gdim, double* gen, const double* __restrict__ scratch,
+                                unsigned long long* load_acc, uint32_t* adj_bits, int adj_words, double* shift_out) {
+  const int k = threadIdx.x;
   if (k < K) {
+    for (int a = 0; a < gdim; ++a) gen[k * gdim + a] = scratch[k * 4 + a];
     load_acc[k] = 0ull;
     for (int w = 0; w < adj_words; ++w) adj_bits[k * adj_words + w] = 0u;
+  }
+  if (k == 0) {
+    double s = 0.0;
+    for (int q = 0; q < K; ++q) s += scratch[q * 4 + 3];
+    if (shift_out) *shift_out = s;
   }
 }
 
@@ -365,9 +382,12 @@ cudaError_t launch_balance(sph_handle* h, const sph_state& s, double* gen, int K
   double* stats = h->unit_stats;
   k_unit_stats<<<K, kBlock, 0, st>>>(h->unit_off, h->unit_list, s.x, s.y, s.z, s.d, h->dmax_nbr, dim, h->dp.kh,
                                      bp.beta_sh, stats);
-  k_balance<<<1, SPH_MAX_UNITS, 0, st>>>(K, dim, gen, load, h->load_acc, h->adj_bits, (K + 31) / 32, stats,
-                                         bp.theta, bp.sigma, bp.gamma_b, shift_out);
-  h->launches += 2;
+  double* scratch = stats + (size_t)5 * K;
+  k_balance_unit<<<K, 32, 0, st>>>(K, dim, gen, load, h->load_acc, h->adj_bits, (K + 31) / 32, stats, bp.theta,
+                                   bp.sigma, bp.gamma_b, scratch);
+  k_balance_apply<<<1, SPH_MAX_UNITS, 0, st>>>(K, dim, gen, scratch, h->load_acc, h->adj_bits, (K + 31) / 32,
+                                               shift_out);
+  h->launches += 3;
   return cudaGetLastError();
 }
 
