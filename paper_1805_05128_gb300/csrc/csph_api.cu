@@ -159,6 +159,7 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   dp.kh = (0.5 * p->kappa) * p->eta;
   dp.n = s->n;
   dp.vref = nullptr;
+  dp.vscale = 1.0;
   for (int k = 0; k < p->n_mat; ++k) {
     const sph_material& m = mats[k];
     h->mat_h.push_back(Mat{m.eos, m.gamma, m.rho0, m.c0, m.p_inf, m.s_a});
@@ -311,6 +312,32 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   if (status != 0) {
     fail(h, SPH_ERR_NONFINITE, "state holds a non-finite or non-positive value");
     return bail(SPH_ERR_NONFINITE);
+  }
+  if (p->precision == SPH_PREC_MIXED && n > 0) {
+    // Scales of the FP32 pair arithmetic (powers of two, so they change no
+    // rounding): the packed volume V vscale is ~1 for the largest particle and
+    // W' wscale ~1 for its smoothing length, which keeps 2 V_i V_j P* W' in the
+    // normal FP32 range at any length scale (at 0.1 um spacing V_i V_j ~ 1e-42
+    // is below it).  The FP64 rate formation divides them out.
+    unsigned long long* mx = reinterpret_cast<unsigned long long*>(h->counters + 6);
+    CKI(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
+    CKI(launch_max_volume(h, *s, mx, st));
+    unsigned long long bits = 0;
+    CKI(cudaMemcpyAsync(&bits, mx, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    CKI(cudaStreamSynchronize(st));
+    double vmax = 0.0;
+    std::memcpy(&vmax, &bits, sizeof(vmax));
+    if (vmax > 0.0) {
+      int ev = 0;
+      std::frexp(vmax, &ev);                               // vmax in [2^(ev-1), 2^ev)
+      h->vscale = std::ldexp(1.0, -ev);
+      const double href = p->eta * std::pow(vmax, 1.0 / p->dim);
+      const int eh = (int)std::lround((p->dim + 1) * std::log2(href));
+      h->wscale = std::ldexp(1.0, eh);
+      dp.vscale = h->vscale;
+    }
+  } else {
+    dp.vscale = 1.0;
   }
 #undef CKI
   *out = h;

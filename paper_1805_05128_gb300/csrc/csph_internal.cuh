@@ -53,6 +53,7 @@ struct DevParams {
   const Mat* mat;                         // device table of n_mat materials
   const double* vref;                     // Verlet lists: x, y, z, d at the last build (4 arrays of n), or NULL
   int64_t n;                              // particles of the handle (stride of vref)
+  double vscale;                          // mixed precision: packed volume = (m / rho) vscale (a power of two)
 };
 constexpr int kMaxMaterials = 65536;
 
@@ -165,6 +166,11 @@ struct sph_handle {
   // order-2 reconstruction (sph_params.order = 2): SPH gradients in slot order,
   // the pair kernel's precision: grad P, then grad v_x, grad v_y, grad v_z
   bool order2 = false;
+
+  // mixed precision: scales (powers of two) of the packed volume and of W', set
+  // by sph_init from the largest particle volume (1 in FP64 mode)
+  double vscale = 1.0;
+  double wscale = 1.0;
   void* grad_p = nullptr;             // [n] float4 / D4
   void* grad_v = nullptr;             // [3 n] float4 / D4
 };
@@ -263,6 +269,7 @@ cudaError_t launch_exclusive_scan(int32_t* cnt, const int64_t* total, int32_t* s
                                   int64_t n_total, int64_t cap, cudaStream_t st);
 cudaError_t launch_conservation(sph_handle* h, const sph_state& s, double* out, cudaStream_t st);
 cudaError_t launch_check_finite(sph_handle* h, const sph_state& s, cudaStream_t st);
+cudaError_t launch_max_volume(sph_handle* h, const sph_state& s, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st);
 cudaError_t launch_pair_vjp(sph_handle* h, const sph_state& s, const void* G, const void* GR2, double* out,
                             cudaStream_t st);

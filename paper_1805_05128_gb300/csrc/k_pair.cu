@@ -79,6 +79,13 @@ struct PairArgs {
   // gP: grad P; gV: grad v_x, grad v_y, grad v_z (three arrays of n, consecutive)
   void* gP;
   void* gV;
+  // mixed precision: the packed volume is V' = V vscale and W' is used as
+  // W'' = W' wscale (both powers of two chosen by sph_init), so that the FP32
+  // products stay in the normal range at any length scale; fscale =
+  // 1 / (vscale^2 wscale) and rscale = 1 / (vscale wscale) undo them in FP64,
+  // vinv = 1 / vscale.  All 1 in FP64 mode.
+  float wscale_f;
+  double fscale, rscale, vinv;
 };
 
 constexpr int kModeFwd = 0;    // rates
@@ -341,9 +348,9 @@ struct FwdAcc {
       vs = mul_(T(0.5), add_(wi, wj));
     }
     const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * add_(Ai.w, Aj.w);
-    const T dW = MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij)
+    const T dW = MIXED ? mul_(dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij), (T)a.wscale_f)
                        : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij);
-    const T F = mul_(mul_(mul_(T(2), mul_(Bi.w, Bj.w)), Ps), dW);   // momentum flux along e
+    const T F = mul_(mul_(mul_(T(2), mul_(Bi.w, Bj.w)), Ps), dW);   // momentum flux along e (scaled)
     s_rho.add(Bj.w * (vi - vs) * (-dW));
     s_fx.add(mul_(F, ex));
     if (DIM >= 2) s_fy.add(mul_(F, ey));
@@ -368,8 +375,8 @@ struct FwdAcc {
   // Rates of home slot i (particle perm[i]) from the sums; nfull: its interacting pairs.
   __device__ __forceinline__ void write(const PairArgs& a, int64_t i, unsigned nfull) const {
     const int64_t p = a.perm[i];
-    a.drho[p] = 2.0 * a.rho_slot[i] * (double)s_rho.s;
-    const double im = 1.0 / a.m[p];
+    a.drho[p] = 2.0 * a.rho_slot[i] * ((double)s_rho.s * a.rscale);
+    const double im = a.fscale / a.m[p];
     a.ax[p] = (double)s_fx.s * im;
     if (DIM >= 2) a.ay[p] = (double)s_fy.s * im;
     if (DIM >= 3) a.az[p] = (double)s_fz.s * im;
@@ -538,7 +545,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
       const T r = r2 * ir;
       const T e[3] = {dx * ir, dy * ir, dz * ir};
       const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * (Ai.w + Aj.w);
-      const T w = -(MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij)
+      const T w = -(MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij) * (T)a.wscale_f
                           : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij));
       const T f = Bj.w * w;
       const T dP = Cj.x - Ci.x;
@@ -596,7 +603,8 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
       const T hij = eh * (Ai.w + Aj.w);
       T W, Wr, Wh;
       cubic_dw3<T, DIM>(r, hij, W, Wr, Wh);
-      const T Vi = Bi.w, Vj = Bj.w, GRi = Ri.x, rhoi = Ri.y, GRj = Rj.x, rhoj = Rj.y;
+      const T Vi = Bi.w * (T)a.vinv, Vj = Bj.w * (T)a.vinv;     // the packed volumes are scaled
+      const T GRi = Ri.x, rhoi = Ri.y, GRj = Rj.x, rhoj = Rj.y;
       const T F = T(2) * Vi * Vj * Ps * W;
       const T dA[3] = {Gi.x - Gj.x, Gi.y - Gj.y, Gi.z - Gj.z};
       const T dB = Gi.w - Gj.w;
@@ -731,13 +739,14 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
       if (act) {
         V4* GP = reinterpret_cast<V4*>(a.gP);
         V4* GV = reinterpret_cast<V4*>(a.gV);
+        const T rs = (T)a.rscale;                      // undo the volume and W' scales (powers of two)
         V4 q{};
-        q.x = gP[0]; q.y = gP[1]; q.z = gP[2];
+        q.x = gP[0] * rs; q.y = gP[1] * rs; q.z = gP[2] * rs;
         GP[i] = q;
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
           V4 g{};
-          g.x = gV[c][0]; g.y = gV[c][1]; g.z = gV[c][2];
+          g.x = gV[c][0] * rs; g.y = gV[c][1] * rs; g.z = gV[c][2] * rs;
           GV[(int64_t)c * a.n + i] = g;
         }
       }
@@ -944,8 +953,8 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair_lists(PairAr
           else return res64[warp][qv][lane];
         };
         const int64_t p = a.perm[i];
-        a.drho[p] = 2.0 * a.rho_slot[i] * rv(0);
-        const double im = 1.0 / a.m[p];
+        a.drho[p] = 2.0 * a.rho_slot[i] * (rv(0) * a.rscale);
+        const double im = a.fscale / a.m[p];
         a.ax[p] = rv(1) * im;
         if (DIM >= 2) a.ay[p] = rv(2) * im;
         if (DIM >= 3) a.az[p] = rv(3) * im;
@@ -1073,6 +1082,10 @@ PairArgs make_args(sph_handle* h, const sph_state& s) {
   a.vcap = h->vcap;
   a.gP = h->grad_p;
   a.gV = h->grad_v;
+  a.wscale_f = (float)h->wscale;
+  a.fscale = 1.0 / (h->vscale * h->vscale * h->wscale);
+  a.rscale = 1.0 / (h->vscale * h->wscale);
+  a.vinv = 1.0 / h->vscale;
   return a;
 }
 

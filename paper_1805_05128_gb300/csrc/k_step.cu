@@ -495,7 +495,7 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
     for (int a = 0; a < P.dim; ++a) off[a] = (float)(X[a] - (g.x0[a] + (double)cc[a] * g.dc));
     reinterpret_cast<float4*>(packA)[sl] = make_float4(off[0], off[1], off[2], (float)d);
     reinterpret_cast<float4*>(packB)[sl] =
-        make_float4((float)v[0], (float)v[1], (float)v[2], (float)(m / rho));
+        make_float4((float)v[0], (float)v[1], (float)v[2], (float)((m / rho) * P.vscale));
     reinterpret_cast<float2*>(packC)[sl] = make_float2((float)Pp, (float)(rho * cp));
   } else {
     reinterpret_cast<D4*>(packA)[sl] = D4{X[0], X[1], X[2], d};
@@ -711,6 +711,30 @@ cudaError_t launch_exclusive_scan(int32_t* cnt, const int64_t* total, int32_t* s
 
 cudaError_t launch_conservation(sph_handle* h, const sph_state& s, double* out, cudaStream_t st) {
   k_conservation<<<h->n_inst, kBlock, 0, st>>>(s, h->inst_off, out);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+// Largest particle volume m / rho (positive doubles order like their bit patterns).
+__global__ void k_max_volume(int64_t n, const double* __restrict__ m, const double* __restrict__ rho,
+                             unsigned long long* out) {
+  unsigned long long b = 0ull;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const double v = m[p] / rho[p];
+    if (v > 0.0 && v < 1e300) {
+      const unsigned long long q = (unsigned long long)__double_as_longlong(v);
+      b = q > b ? q : b;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long q = __shfl_xor_sync(0xffffffffu, b, o);
+    b = q > b ? q : b;
+  }
+  if ((threadIdx.x & 31) == 0 && b) atomicMax(out, b);
+}
+
+cudaError_t launch_max_volume(sph_handle* h, const sph_state& s, unsigned long long* out, cudaStream_t st) {
+  k_max_volume<<<capped_grid(grid_for(h->n, kBlock)), kBlock, 0, st>>>(h->n, s.m, s.rho, out);
   h->launches += 1;
   return cudaGetLastError();
 }

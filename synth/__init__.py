@@ -170,6 +170,61 @@ def ensemble(n_inst: int = 256, seed: int = 2018, n_min: int = 5000, n_max: int 
     return probs
 
 
+def lead() -> MaterialSpec:
+    """Lead as in the ejecta test of Sec. 7: Mie-Grueneisen with rho0 = 11.35
+    g/cc, c_a = 2.58 km/s, s_a = 1.26, Gamma = 1.7 (SI units)."""
+    return MaterialSpec("mie_gruneisen", 1.7, rho0=11350.0, c0=2580.0, s_a=1.26)
+
+
+def ejecta(nx: int = 100, periods: int = 2, lam: int = 40, nz: int = 10, a: float = 1e-7,
+           up: float = 1000.0, units: int = 64, n_steps: int = 200) -> Problem:
+    """Grooved lead sample driven onto a rigid wall (the ejecta test of Sec. 7,
+    synthetic): a cubic lattice of spacing a, nx layers along x, `periods`
+    grooves of period lam spacings along y, nz layers along z; the free face
+    at x = nx a carries 90-degree V-grooves (depth lam/2 spacings at the
+    groove centre, none at the ridges).  The rigid wall is the symmetry plane
+    of a mirror copy: the sample at x >= 0 moves at -up, its mirror image
+    (x -> -x - a) at +up, so the plane x = -a/2 stays at rest as a wall
+    would.  Lead at rho0 and e = 0 (P = 0), mass rho0 a^3.  The lateral faces
+    are free (no periodic images)."""
+    ny = periods * lam
+    i, j, k = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    ym = (j % lam) + 0.5 - lam / 2.0                      # offset from the groove centre, in spacings
+    depth = lam / 2.0 - np.abs(ym)                        # V-groove: lam/2 at the centre, 0 at the ridges
+    keep = i < nx - depth
+    i, j, k = i[keep], j[keep], k[keep]
+    x = i * a
+    y = (j - (ny - 1) / 2.0) * a
+    z = (k - (nz - 1) / 2.0) * a
+    n1 = len(x)
+    x = np.concatenate([x, -x - a]); y = np.concatenate([y, y]); z = np.concatenate([z, z])
+    vx = np.concatenate([np.full(n1, -up), np.full(n1, up)])
+    mat = lead()
+    n = 2 * n1
+    arrays = dict(x=x, y=y, z=z, vx=vx, vy=np.zeros(n), vz=np.zeros(n), rho=np.full(n, mat.rho0),
+                  E=0.5 * vx * vx, m=np.full(n, mat.rho0 * a ** 3))
+    return Problem(f"ejecta_{n}", 3, arrays, [mat], kernel="cubic", kappa=2.0, eta=1.3, cfl=0.3,
+                   n_steps=n_steps, units=units, unit_dim=2, n_upd=10,
+                   meta=dict(a=a, up=up, lam=lam, nx=nx, n_half=n1))
+
+
+def water_block(side: int = 8, a: float = 1e-3, seed: int = 29) -> Problem:
+    """A cube of Tait water (rho0 = 1000, c0 = 1500, exponent 7) with a
+    seeded random velocity field and +-1 % density perturbations."""
+    g = np.meshgrid(*[np.arange(side, dtype=float)] * 3, indexing="ij")
+    n = side ** 3
+    u = uniform(seed, 4 * n).reshape(4, n)
+    x, y, z = (gi.ravel() * a for gi in g)
+    rho = 1000.0 * (1.0 + 0.02 * (u[3] - 0.5))
+    v = 5.0 * (u[:3] - 0.5)
+    arrays = dict(x=x, y=y, z=z, vx=v[0], vy=v[1], vz=v[2], rho=rho,
+                  E=2.0e3 + 0.5 * (v ** 2).sum(axis=0), m=np.full(n, 1000.0 * a ** 3))
+    mat = MaterialSpec("tait", 7.0, rho0=1000.0, c0=1500.0)
+    return Problem(f"water_{n}", 3, arrays, [mat], kernel="cubic", kappa=2.0, eta=1.3, cfl=0.3,
+                   n_steps=20, units=0, unit_dim=2, n_upd=10)
+
+
 # ---------------------------------------------------------------------------
 # Voronoi generator seeding
 # ---------------------------------------------------------------------------
