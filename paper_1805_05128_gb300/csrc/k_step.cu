@@ -121,8 +121,40 @@ __device__ __forceinline__ double size_of(int dim, double m, double rho) {
   return dim == 1 ? vol : (dim == 2 ? sqrt(vol) : cbrt_fast(vol));
 }
 
+// Sound speed in FP32 from an FP64 specific internal energy (the closures of
+// eos() written in single precision; the stiffened gas in the form
+// c^2 = gamma (gamma - 1)(rho e - P_inf) / rho, without the P + P_inf
+// cancellation).  For the CFL bound of a mixed-precision step only.
+__device__ __forceinline__ float sound_speed_f32(const Mat& m, float rho, float e) {
+  const float g = (float)m.gamma;
+  float c2;
+  if (m.eos == SPH_EOS_IDEAL) {
+    c2 = g * (g - 1.0f) * e;
+  } else if (m.eos == SPH_EOS_STIFFENED) {
+    c2 = g * (g - 1.0f) * (rho * e - (float)m.p_inf) / rho;
+  } else if (m.eos == SPH_EOS_TAIT) {
+    const float c0 = (float)m.c0;
+    c2 = c0 * c0 * powf(rho / (float)m.rho0, g - 1.0f);
+  } else {
+    const float ca = (float)m.c0, sa = (float)m.s_a, r0 = (float)m.rho0;
+    const float x = r0 / rho, u = 1.0f - x, D = 1.0f - sa * u, iD2 = 1.0f / (D * D);
+    const float Pr = r0 * ca * ca * u * iD2, er = 0.5f * ca * ca * u * u * iD2;
+    const float du = x / rho;
+    const float dPr = r0 * ca * ca * (1.0f + sa * u) * iD2 / D * du;
+    const float der = ca * ca * u * iD2 / D * du;
+    const float P = Pr + g * rho * (e - er);
+    c2 = dPr + g * (e - er) - g * rho * der + g * P / rho;
+  }
+  return c2 > 0.0f ? sqrtf(c2) : 0.0f;
+}
+
 // ---------------------------------------------------------------------------
 // d, P, c at the current state, dt_i = eta d_i / (c_i + |v_i|), optional bbox.
+// Inside a mixed-precision step (no bbox, nothing written back) the CFL
+// bound is evaluated in FP32 from the FP64 state (e = E - v^2/2 in FP64): it
+// is a stability bound, the step then uses that dt exactly in FP64, and the
+// FP64 divisions, roots and cube root of every particle are what bound this
+// kernel on GB300.  FP64 handles keep the FP64 expression (bit parity of dt).
 // ---------------------------------------------------------------------------
 __global__ void k_derive(DevParams P, sph_state s, const int64_t* __restrict__ blk_start,
                          const int64_t* __restrict__ blk_end, BlockPart* part, int write_derived,
@@ -130,7 +162,17 @@ __global__ void k_derive(DevParams P, sph_state s, const int64_t* __restrict__ b
   int64_t p = blk_start[blockIdx.x] + threadIdx.x;
   Red r;
   red_init(r);
-  if (p < blk_end[blockIdx.x]) {
+  if (p < blk_end[blockIdx.x] && !with_bbox && !write_derived && P.precision == SPH_PREC_MIXED) {
+    const double vx = ld(s.vx, p), vy = ld(s.vy, p), vz = ld(s.vz, p);
+    const double v2 = vx * vx + vy * vy + vz * vz;
+    const double e = s.E[p] - 0.5 * v2;
+    const int mi = s.mat ? s.mat[p] : 0;
+    const float rho = (float)s.rho[p];
+    const float c = sound_speed_f32(P.mat[mi], rho, (float)e);
+    const float vol = (float)s.m[p] / rho;
+    const float d = P.dim == 1 ? vol : (P.dim == 2 ? sqrtf(vol) : cbrtf(vol));
+    r.dtmin = dkey((double)((float)P.eta * d / (c + sqrtf((float)v2))));
+  } else if (p < blk_end[blockIdx.x]) {
     double vx = ld(s.vx, p), vy = ld(s.vy, p), vz = ld(s.vz, p);
     double v2 = vx * vx + vy * vy + vz * vz;
     double e = s.E[p] - 0.5 * v2;

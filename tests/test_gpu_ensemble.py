@@ -68,12 +68,13 @@ def test_ensemble_matches_oracle_per_instance():
     sim = Simulation(probs, precision="mixed", units=0)
     sim.step(3)
     _check_oracle(sim, probs, 3, 1e-4)
-    # per-instance dt: the time of each instance is its own
+    # per-instance dt: the time of each instance is its own (a mixed step takes
+    # the CFL bound in FP32, so it agrees with the FP64 bound to ~1e-7)
     t = sim.time.cpu().numpy()
     for b, prob in enumerate(probs):
         p, s = O.from_problem(prob)
         _, dts = O.step(p, s, 3)
-        assert t[b] == pytest.approx(float(np.sum(dts)), rel=1e-12)
+        assert t[b] == pytest.approx(float(np.sum(dts)), rel=1e-6)
     sim.close()
 
 
