@@ -514,7 +514,19 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
   double e = E - 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
   int mi = s.mat ? s.mat[p] : 0;
   double Pp, cp;
-  eos(P.mat[mi], rho, e, Pp, cp);
+  float cf = 0.0f;
+  const Mat& mt = P.mat[mi];
+  const bool fast = MIXED && predict && (mt.eos == SPH_EOS_IDEAL || mt.eos == SPH_EOS_STIFFENED);
+  if (fast) {
+    // a mixed step packs FP32 operands: P in FP64 (the stiffened-gas difference
+    // of two large terms, the expression of eos()), c in FP32
+    Pp = (mt.gamma - 1.0) * rho * e - (mt.eos == SPH_EOS_STIFFENED ? mt.gamma * mt.p_inf : 0.0);
+    cf = sound_speed_f32(mt, (float)rho, (float)e);
+    cp = (double)cf;
+  } else {
+    eos(mt, rho, e, Pp, cp);
+    cf = (float)cp;
+  }
   s.P[p] = Pp;
   s.c[p] = cp;
   double d = s.d[p];
@@ -536,9 +548,9 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
     float off[3] = {0.f, 0.f, 0.f};
     for (int a = 0; a < P.dim; ++a) off[a] = (float)(X[a] - (g.x0[a] + (double)cc[a] * g.dc));
     reinterpret_cast<float4*>(packA)[sl] = make_float4(off[0], off[1], off[2], (float)d);
-    reinterpret_cast<float4*>(packB)[sl] =
-        make_float4((float)v[0], (float)v[1], (float)v[2], (float)((m / rho) * P.vscale));
-    reinterpret_cast<float2*>(packC)[sl] = make_float2((float)Pp, (float)(rho * cp));
+    const float Vp = fast ? ((float)m / (float)rho) * (float)P.vscale : (float)((m / rho) * P.vscale);
+    reinterpret_cast<float4*>(packB)[sl] = make_float4((float)v[0], (float)v[1], (float)v[2], Vp);
+    reinterpret_cast<float2*>(packC)[sl] = make_float2((float)Pp, fast ? (float)rho * cf : (float)(rho * cp));
   } else {
     reinterpret_cast<D4*>(packA)[sl] = D4{X[0], X[1], X[2], d};
     reinterpret_cast<D4*>(packB)[sl] = D4{v[0], v[1], v[2], m / rho};
