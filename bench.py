@@ -294,7 +294,8 @@ def run_extras(args, dev) -> dict:
     """The other forms on the same GPU: precision (FP64 vs mixed step on the
     benchmark plate, no work units, mesh and search every step), neighbour
     search (per-step mesh and search vs Verlet lists on the benchmark
-    configuration), batching (256-instance ensemble, 100 steps in one CUDA
+    configuration), a second 3D workload (the Mie-Grueneisen lead ejecta
+    sample), batching (256-instance ensemble, 100 steps in one CUDA
     graph, autotuned, vs 256 sequential single-instance runs) and
     differentiation (forward + reverse mode of a 203k-particle plate, 100
     steps, checkpoints every 10)."""
@@ -363,7 +364,28 @@ def run_extras(args, dev) -> dict:
         sim.close()
     out["neighbour_search"] = ns
 
-    # (3) batching
+    # (3) a second 3D workload: the grooved lead sample (Mie-Grueneisen) on a rigid wall
+    q = synth.ejecta(nx=100, periods=2, lam=40, nz=60, a=1e-7, units=64)
+    gen = synth.problem_generators(q)
+    sim = Simulation(q, precision="mixed", generators=gen, n_upd=10, cell_beta=BETA, device=dev)
+    sim.assign()
+    sim.build_cells()
+    sim.step(10)
+    b0 = sim.list_builds()[0]
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    sim.step(100)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["mg_ejecta"] = {"workload": f"grooved lead sample on a rigid wall (mirror copy), Mie-Grueneisen lead, "
+                                    f"{q.n} particles, 0.1 um spacing, 64 units, beta {BETA}",
+                        "value": q.n * 100 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / 100,
+                        "list_builds_per_100_steps": sim.list_builds()[0] - b0, "status": sim.read_status()}
+    sim.close()
+
+    # (4) batching
     probs = synth.ensemble()
     n_tot = sum(q.n for q in probs)
     tune = ens.autotune(probs, cell_betas=(0.0, 0.15, 0.3), pair_blocks=(3, 0), n_steps=5, reps=1, device=dev)
@@ -385,7 +407,7 @@ def run_extras(args, dev) -> dict:
         "tuning": {"cell_beta": tune.cell_beta, "pair_blocks_per_sm": tune.pair_blocks,
                    "ms_per_step": {f"{k[0]}/{k[1]}": v for k, v in tune.timings.items()}}}
 
-    # (4) differentiation
+    # (5) differentiation
     from paper_1805_05128_gb300.adjoint import RunSpec, csph_run
     q = synth.plate_impact(25, (120, 120, 13), a=1e-4, v=1000.0, units=0)
     A = q.arrays

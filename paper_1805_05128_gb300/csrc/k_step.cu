@@ -450,14 +450,16 @@ __global__ void k_kick_drift(DevParams P, sph_state s, const int64_t* __restrict
       // Verlet-list validity: a listed superset of the pairs within kappa h_ij holds as long
       // as |x_i - x_i^b| + kh max(0, d_i - d_i^b) <= beta kh d_i^b for every particle (b: the
       // last build; summing the bounds of i and j covers the pair), kept with a 5 % margin
-      double dsq = 0.0;
+      // (differences in FP64, the bound itself in FP32: the 5 % margin dwarfs its rounding)
+      float dsq = 0.0f;
       for (int a = 0; a < P.dim; ++a) {
-        const double dx = X[a][p] - P.vref[(int64_t)a * P.n + p];
+        const float dx = (float)(X[a][p] - P.vref[(int64_t)a * P.n + p]);
         dsq += dx * dx;
       }
       const double db = P.vref[3 * P.n + p];
-      const double crit = sqrt(dsq) + P.kh * fmax(d - db, 0.0) - 0.95 * P.cell_beta * P.kh * db;
-      r.viol = dkey(crit);
+      const float kh = (float)P.kh;
+      const float crit = sqrtf(dsq) + kh * fmaxf((float)(d - db), 0.0f) - 0.95f * (float)P.cell_beta * kh * (float)db;
+      r.viol = dkey((double)crit);
     }
     if (!finite || !isfinite(d)) set_status(status, SPH_ERR_NONFINITE);
   }
