@@ -629,10 +629,65 @@ static void cross3(const double a[3], const double b[3], double o[3]) {
  *              the last term the current centroid (g_k for an empty unit).
  * Returns sum_k |g^_k - g_k| (eq. VDConvergence).  gen is updated in place. */
 /* ------------------------------------------------------------------------ */
+/* Four-body term for 3D decompositions (Sec. 3.3 names it, "a rotation on
+ * the circumsphere of four generators", without a formula).  Reading: for
+ * each set {k, l, m, n} of mutually adjacent units (each once per k,
+ * l < m < n) with o the centre of the sphere through g_k, g_l, g_m, g_n,
+ *   dg_klmn = -c_k + M(w, |w|) c_k,  w = sum_{p = l, m, n} a_p unit(c_k x c_p),
+ *   c_p = g_p - o,  a_p = (T/2) (L_p - L_k) / (L_k + L_l + L_m + L_n),
+ * T = arccos(-1/3), the angle between the generators of a regular
+ * tetrahedron seen from its centre: the 2D form's pi/3 is half of the 120
+ * degrees of three subdomains around a point.  One rotation about the summed
+ * rotation vector: in 2D all the axes are the plane normal and this is the
+ * product of the paper's rotations; in 3D rotations do not commute, and a
+ * product would depend on the labels of l, m, n.  The rotation keeps |c_k|,
+ * so the generator stays on the sphere and o stays the common point; the
+ * summed term is length-limited like the 2D one.  Skipped when the four
+ * generators are (nearly) coplanar. */
+static void four_body(const double gk[3], const double gl[3], const double gm[3], const double gn[3],
+                      double Lk, double Ll, double Lm, double Ln, double dg[3]) {
+  double a[3], b[3], c[3];
+  for (int q = 0; q < 3; ++q) { a[q] = gl[q] - gk[q]; b[q] = gm[q] - gk[q]; c[q] = gn[q] - gk[q]; }
+  double bc[3], ca[3], ab[3];
+  cross3(b, c, bc);
+  cross3(c, a, ca);
+  cross3(a, b, ab);
+  double det = a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2];
+  double a2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+  double b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+  double s2 = a2 > b2 ? a2 : b2;
+  s2 = s2 > c2 ? s2 : c2;
+  if (fabs(det) < 1e-12 * s2 * sqrt(s2)) return;        /* coplanar: no circumsphere */
+  double Ls = Lk + Ll + Lm + Ln;
+  if (!(Ls > 0.0)) return;
+  double o[3];
+  for (int q = 0; q < 3; ++q) o[q] = gk[q] + (a2 * bc[q] + b2 * ca[q] + c2 * ab[q]) / (2.0 * det);
+  double half_t = 0.5 * acos(-1.0 / 3.0);
+  double al = half_t * (Ll - Lk) / Ls, am = half_t * (Lm - Lk) / Ls, an = half_t * (Ln - Lk) / Ls;
+  double ck[3], cl[3], cm[3], cn[3];
+  for (int q = 0; q < 3; ++q) { ck[q] = gk[q] - o[q]; cl[q] = gl[q] - o[q]; cm[q] = gm[q] - o[q]; cn[q] = gn[q] - o[q]; }
+  const double* cp[3] = {cl, cm, cn};
+  const double ap[3] = {al, am, an};
+  double w[3] = {0.0, 0.0, 0.0};
+  for (int t = 0; t < 3; ++t) {
+    double ax[3];
+    cross3(ck, cp[t], ax);
+    double na = sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
+    if (na == 0.0) continue;
+    for (int q = 0; q < 3; ++q) w[q] += ap[t] * ax[q] / na;
+  }
+  double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  if (nw == 0.0) return;
+  double r[3];
+  rotate3(w, nw, ck, r);
+  for (int q = 0; q < 3; ++q) dg[q] += r[q] - ck[q];
+}
+
 double orc_balance(int K, int gdim, double* gen, const double* load, const uint8_t* adj,
                    const double* dsh, const double* centroid, const int64_t* count,
                    double theta, double sigma, double gamma_b, double* dg_out) {
-  double sig = (gdim == 2) ? sigma : 0.0;
+  double sig = (gdim >= 2) ? sigma : 0.0;   /* three-body terms in 2D, four-body terms in 3D */
   double* newg = (double*)malloc(sizeof(double) * (size_t)K * (size_t)gdim);
   double shift = 0.0;
   for (int k = 0; k < K; ++k) {
@@ -652,7 +707,23 @@ double orc_balance(int K, int gdim, double* gen, const double* load, const uint8
       double f = dsh[k * K + l] * ((load[k] - load[l]) / den) / nrm;
       for (int a = 0; a < 3; ++a) dg2[a] += f * gkl[a];
     }
-    if (sig != 0.0) {
+    if (sig != 0.0 && gdim == 3) {
+      for (int l = 0; l < K; ++l) {
+        if (l == k || !adj[k * K + l]) continue;
+        for (int m = l + 1; m < K; ++m) {
+          if (m == k || !adj[k * K + m] || !adj[l * K + m]) continue;
+          for (int n4 = m + 1; n4 < K; ++n4) {
+            if (n4 == k || !adj[k * K + n4] || !adj[l * K + n4] || !adj[m * K + n4]) continue;
+            four_body(gk, &gen[l * 3], &gen[m * 3], &gen[n4 * 3], load[k], load[l], load[m], load[n4], dg3);
+          }
+        }
+      }
+      double n3 = sqrt(dg3[0] * dg3[0] + dg3[1] * dg3[1] + dg3[2] * dg3[2]);
+      if (n3 > maxd && n3 > 0.0) {
+        double f = maxd / n3;
+        for (int a = 0; a < 3; ++a) dg3[a] *= f;
+      }
+    } else if (sig != 0.0) {
       for (int l = 0; l < K; ++l) {
         if (l == k || !adj[k * K + l]) continue;
         for (int m = l + 1; m < K; ++m) {

@@ -225,7 +225,12 @@ __device__ __forceinline__ void rotate3(const double ax[3], double alpha, const 
 //   eq. (BalancingOffset)       two-body, g_kl = g_k - g_l
 //   eq. (BalancingOffsetRot)    three-body for 2D decompositions, each
 //                               triangle of mutually adjacent units once,
-//                               length limited to max_l D^sh_kl
+//                               length limited to max_l D^sh_kl; for 3D
+//                               decompositions four-body terms instead:
+//                               -c_k + M(w, |w|) c_k about the centre of the
+//                               sphere through g_k, g_l, g_m, g_n, with
+//                               w = sum_p a_p unit(c_k x c_p) and
+//                               a_p = (arccos(-1/3)/2)(L_p - L_k)/(L_k+L_l+L_m+L_n)
 //   eq. (BalancingOffsetPlusRot), eq. (TotalOffset)
 // D^sh_kl = max(rmax_k, rmax_l) (eq. Horizon).  Loads: caller's, else half
 // the accumulated full-list pair counts.  Resets the accumulators.
@@ -250,7 +255,7 @@ __global__ void k_balance_unit(int K, int gdim, const double* __restrict__ gen, 
   __syncthreads();
   const int k = blockIdx.x;
   if (threadIdx.x != 0 || k >= K) return;
-  double sig = (gdim == 2) ? sigma : 0.0;
+  double sig = (gdim >= 2) ? sigma : 0.0;   // three-body terms in 2D, four-body terms in 3D
   // The neighbours of a unit are walked as the set bits of its bitmap row, in
   // increasing index order: the same terms in the same order as a scan of all
   // indices that skips the non-adjacent ones.
@@ -275,7 +280,75 @@ __global__ void k_balance_unit(int K, int gdim, const double* __restrict__ gen, 
     double f = D * ((L[k] - L[l]) / den) / nrm;
     for (int a = 0; a < 3; ++a) dg2[a] += f * gkl[a];
   }
-  if (sig != 0.0) {
+  if (sig != 0.0 && gdim == 3) {
+    // four-body terms: each set {k, l, m, n} of mutually adjacent units once
+    // (l < m < n), a rotation of c_k on the circumsphere of the four generators
+    const double half_t = 0.5 * acos(-1.0 / 3.0);
+    for (int wl = 0; wl < adj_words; ++wl)
+    for (uint32_t bl = AB[k * adj_words + wl]; bl; bl &= bl - 1) {
+      const int l = wl * 32 + __ffs(bl) - 1;
+      if (l == k || l >= K) continue;
+      for (int wm = (l + 1) >> 5; wm < adj_words; ++wm)
+      for (uint32_t bm = AB[k * adj_words + wm] & AB[l * adj_words + wm] &
+                         (wm == ((l + 1) >> 5) ? (~0u << ((l + 1) & 31)) : ~0u);
+           bm; bm &= bm - 1) {
+        const int m = wm * 32 + __ffs(bm) - 1;
+        if (m == k || m >= K) continue;
+        for (int wn = (m + 1) >> 5; wn < adj_words; ++wn)
+        for (uint32_t bn = AB[k * adj_words + wn] & AB[l * adj_words + wn] & AB[m * adj_words + wn] &
+                           (wn == ((m + 1) >> 5) ? (~0u << ((m + 1) & 31)) : ~0u);
+             bn; bn &= bn - 1) {
+          const int n4 = wn * 32 + __ffs(bn) - 1;
+          if (n4 == k || n4 >= K) continue;
+          const double* gl = &G[l * 3];
+          const double* gm = &G[m * 3];
+          const double* gn = &G[n4 * 3];
+          double a[3], b[3], c[3];
+          for (int q = 0; q < 3; ++q) { a[q] = gl[q] - gk[q]; b[q] = gm[q] - gk[q]; c[q] = gn[q] - gk[q]; }
+          double bc[3], ca[3], ab[3];
+          cross3(b, c, bc);
+          cross3(c, a, ca);
+          cross3(a, b, ab);
+          const double det = a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2];
+          const double a2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+          const double b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+          const double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+          double s2 = a2 > b2 ? a2 : b2;
+          s2 = s2 > c2 ? s2 : c2;
+          if (fabs(det) < 1e-12 * s2 * sqrt(s2)) continue;          // coplanar: no circumsphere
+          const double Ls = L[k] + L[l] + L[m] + L[n4];
+          if (!(Ls > 0.0)) continue;
+          double o[3];
+          for (int q = 0; q < 3; ++q) o[q] = gk[q] + (a2 * bc[q] + b2 * ca[q] + c2 * ab[q]) / (2.0 * det);
+          const double al = half_t * (L[l] - L[k]) / Ls, am = half_t * (L[m] - L[k]) / Ls;
+          const double an = half_t * (L[n4] - L[k]) / Ls;
+          double ck[3], cl[3], cm[3], cn[3];
+          for (int q = 0; q < 3; ++q) { ck[q] = gk[q] - o[q]; cl[q] = gl[q] - o[q]; cm[q] = gm[q] - o[q]; cn[q] = gn[q] - o[q]; }
+          // one rotation about the summed rotation vector (label independent)
+          const double* cp[3] = {cl, cm, cn};
+          const double ap[3] = {al, am, an};
+          double w[3] = {0.0, 0.0, 0.0};
+          for (int t = 0; t < 3; ++t) {
+            double ax[3];
+            cross3(ck, cp[t], ax);
+            const double na = sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
+            if (na == 0.0) continue;
+            for (int q = 0; q < 3; ++q) w[q] += ap[t] * ax[q] / na;
+          }
+          const double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+          if (nw == 0.0) continue;
+          double rr[3];
+          rotate3(w, nw, ck, rr);
+          for (int q = 0; q < 3; ++q) dg3[q] += rr[q] - ck[q];
+        }
+      }
+    }
+    double n3 = sqrt(dg3[0] * dg3[0] + dg3[1] * dg3[1] + dg3[2] * dg3[2]);
+    if (n3 > maxd && n3 > 0.0) {
+      double f = maxd / n3;
+      for (int a = 0; a < 3; ++a) dg3[a] *= f;
+    }
+  } else if (sig != 0.0) {
     for (int wl = 0; wl < adj_words; ++wl)
     for (uint32_t bl = AB[k * adj_words + wl]; bl; bl &= bl - 1) {
       const int l = wl * 32 + __ffs(bl) - 1;

@@ -262,6 +262,33 @@ def test_balance_parity(sigma, theta):
     assert float(shift[0]) == pytest.approx(rshift, rel=1e-10, abs=1e-15)
 
 
+@pytest.mark.parametrize("sigma", [0.0, 0.5])
+def test_balance_parity_3d(sigma):
+    """3D decomposition (unit_dim = 3): two-body, and the four-body terms of
+    mutually adjacent quadruples (rotation on their circumsphere)."""
+    prob = PROBLEMS["plate"]()
+    prob.unit_dim = 3
+    K = prob.units
+    gen = synth.problem_generators(prob) + np.array([[3e-4, -2e-4, 1e-4]])
+    sim = _sim(prob, "fp64", units=K, generators=gen.copy())
+    sim.assign()
+    gi, gj = sim.pair_list()
+    load_g, adj_g = sim.unit_stats()
+    shift = sim.balance(theta=0.25, sigma=sigma, gamma_b=1.0, beta_sh=0.45)
+    g = sim.numpy()
+    newgen = sim.gen.cpu().numpy()
+    p, s = _oracle_state(prob, g)
+    st = O.unit_stats(p, s, g["unit"], K, 3, gi, gj, 0.45)
+    assert np.array_equal(adj_g, st["adj"])
+    ref, rshift, _ = O.balance(gen, st["load"], st["adj"], st["dsh"], st["centroid"], st["count"], 0.25, sigma, 1.0)
+    scale = np.max(np.abs(gen))
+    assert np.max(np.abs(newgen - ref)) <= 1e-12 * scale
+    assert float(shift[0]) == pytest.approx(rshift, rel=1e-10, abs=1e-15)
+    if sigma > 0:   # the four-body terms took part
+        ref0, _, _ = O.balance(gen, st["load"], st["adj"], st["dsh"], st["centroid"], st["count"], 0.25, 0.0, 1.0)
+        assert np.max(np.abs(ref - ref0)) > 1e-9 * scale
+
+
 def test_step_with_rebalancing_runs_and_conserves():
     prob = PROBLEMS["plate"]()
     sim = _sim(prob, "mixed", units=prob.units, n_upd=5)

@@ -119,13 +119,18 @@ def test_three_body_length_limit():
     assert np.linalg.norm(dg[1]) == pytest.approx(0.001, rel=1e-12)
 
 
-def test_three_body_off_in_3d():
+def test_no_three_body_term_in_3d():
+    """3D decompositions use four-body terms (quadruples of mutually adjacent
+    units) instead of the three-body ones: with three units there is none, so
+    eq. (BalancingOffsetPlusRot) leaves (1 - sigma) times the two-body sum."""
     gen = np.array([[0.0, 0.2, 0.0], [-0.2, -0.1, 0.0], [0.2, -0.1, 0.0]])
     _, load, adj, D, _, _ = _three()
     cen, cnt = np.zeros((3, 3)), np.zeros(3, dtype=np.int64)
-    _, _, dg1 = O.balance(gen, load, adj, D, cen, cnt, theta=0.0, sigma=1.0, gamma_b=1.0)
     _, _, dg0 = O.balance(gen, load, adj, D, cen, cnt, theta=0.0, sigma=0.0, gamma_b=1.0)
-    assert np.array_equal(dg1, dg0)
+    _, _, dg5 = O.balance(gen, load, adj, D, cen, cnt, theta=0.0, sigma=0.5, gamma_b=1.0)
+    _, _, dg1 = O.balance(gen, load, adj, D, cen, cnt, theta=0.0, sigma=1.0, gamma_b=1.0)
+    assert np.max(np.abs(dg0)) > 0
+    assert np.allclose(dg5, 0.5 * dg0, rtol=1e-15, atol=0) and np.max(np.abs(dg1)) == 0.0
 
 
 # ------------------------------------------------- disk test of Sec. 5 ---
