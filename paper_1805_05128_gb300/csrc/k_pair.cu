@@ -838,7 +838,20 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair_lists(PairAr
     int unit_run = -1;
     unsigned unit_load = 0;
     unsigned tf = 0, tc = 0, te = 0;
+    // The list reads are software-pipelined: the next chunk of entries (and,
+    // across slots, the next slot's first chunk and count) is requested
+    // before the current one is tested, so the DRAM latency of the lists
+    // overlaps the L2 gathers and the arithmetic.  vcap >= 32, so the first
+    // chunk of any row is in bounds.
+    uint32_t e_pre = a.vlist[g0 * (int64_t)a.vcap + lane];
+    int cnt_pre = a.vcnt[g0];
     for (int64_t i = g0; i < g1; ++i) {                 // warp-uniform
+      const int cnt = cnt_pre;
+      uint32_t e_cur = e_pre;
+      if (i + 1 < g1) {
+        e_pre = a.vlist[(i + 1) * (int64_t)a.vcap + lane];
+        cnt_pre = a.vcnt[i + 1];
+      }
       int b = 0;
       if (a.n_inst > 1) {
         int lo = 0, hi = a.n_inst;
@@ -856,7 +869,6 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair_lists(PairAr
       const V2 Ci = reinterpret_cast<const V2*>(a.C)[i];
       const T khdi = MIXED ? (T)a.kh_f * Ai.w : T(0);
       const int ui = a.K > 0 ? a.slot_unit[i] : 0;
-      const int cnt = a.vcnt[i];
       const uint32_t* __restrict__ row = a.vlist + i * (int64_t)a.vcap;
       FwdAcc<MIXED, DIM> fw;
       int qn = 0;          // queued pairs (warp-uniform)
@@ -878,7 +890,8 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair_lists(PairAr
       for (int base = 0; base < cnt; base += 32) {
         const int k = base + lane;
         const bool kv = k < cnt;
-        const uint32_t e = kv ? row[k] : 0u;
+        const uint32_t e = kv ? e_cur : 0u;
+        if (base + 32 < cnt) e_cur = (k + 32 < cnt) ? row[k + 32] : 0u;   // next chunk, requested now
         const int64_t j = e >> 5;
         const V4 S = A[kv ? j : i];
         bool acc = false;
