@@ -295,7 +295,8 @@ def run_extras(args, dev) -> dict:
     benchmark plate, no work units, mesh and search every step), neighbour
     search (per-step mesh and search vs Verlet lists on the benchmark
     configuration), a second 3D workload (the Mie-Grueneisen lead ejecta
-    sample), batching (256-instance ensemble, 100 steps in one CUDA
+    sample), the 10M-particle droplet collision at 1:1000 density (mixed vs
+    FP64), batching (256-instance ensemble, 100 steps in one CUDA
     graph, autotuned, vs 256 sequential single-instance runs) and
     differentiation (forward + reverse mode of a 203k-particle plate, 100
     steps, checkpoints every 10)."""
@@ -385,7 +386,32 @@ def run_extras(args, dev) -> dict:
                         "list_builds_per_100_steps": sim.list_builds()[0] - b0, "status": sim.read_status()}
     sim.close()
 
-    # (4) batching
+    # (4) the droplet collision with a 1:1000 density contrast (10.1M particles): the
+    # mixed step with lists against the plain FP64 GPU step on the same inputs
+    q = synth.droplets()
+    gen = synth.problem_generators(q)
+    dro = {"workload": f"two Tait droplets (4M particles each, radius 1 mm, 300 m/s) in ideal gas at 1:1000 "
+                       f"density, {q.n} particles, 256 units (3D)"}
+    for prec, beta, steps in (("mixed", BETA, 20), ("fp64", 0.0, 2)):
+        sim = Simulation(q, precision=prec, generators=gen, n_upd=10, cell_beta=beta, device=dev)
+        sim.assign()
+        sim.build_cells()
+        sim.step(2)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        sim.step(steps)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        dro[prec] = {"value": q.n * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+                     "verlet_beta": beta, "status": sim.read_status()}
+        sim.close()
+    dro["speedup_mixed_over_fp64"] = dro["mixed"]["value"] / dro["fp64"]["value"]
+    out["droplets"] = dro
+    del q
+
+    # (5) batching
     probs = synth.ensemble()
     n_tot = sum(q.n for q in probs)
     tune = ens.autotune(probs, cell_betas=(0.0, 0.15, 0.3), pair_blocks=(3, 0), n_steps=5, reps=1, device=dev)
@@ -407,7 +433,7 @@ def run_extras(args, dev) -> dict:
         "tuning": {"cell_beta": tune.cell_beta, "pair_blocks_per_sm": tune.pair_blocks,
                    "ms_per_step": {f"{k[0]}/{k[1]}": v for k, v in tune.timings.items()}}}
 
-    # (5) differentiation
+    # (6) differentiation
     from paper_1805_05128_gb300.adjoint import RunSpec, csph_run
     q = synth.plate_impact(25, (120, 120, 13), a=1e-4, v=1000.0, units=0)
     A = q.arrays

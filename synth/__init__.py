@@ -225,6 +225,58 @@ def water_block(side: int = 8, a: float = 1e-3, seed: int = 29) -> Problem:
                    n_steps=20, units=0, unit_dim=2, n_upd=10)
 
 
+def droplets(n_sphere: int = 4_000_000, n_gas: int = 2_000_000, radius: float = 1e-3,
+             speed: float = 300.0, gap: float = 5.0, jitter: float = 0.05, seed: int = 2019,
+             units: int = 256, n_steps: int = 100) -> Problem:
+    """Two Tait water droplets (rho0 = 1000, c0 = 1500, exponent 7) of
+    n_sphere particles each and radius `radius`, approaching at relative
+    speed `speed`, in an ambient ideal gas (gamma = 1.4) at 1/1000 of the
+    water density.  All particles sit on one cubic lattice of spacing
+    a = (4/3 pi radius^3 / n_sphere)^(1/3) with seeded +-jitter a offsets, so
+    the density contrast is carried by the particle masses (1:1000) and the
+    particle sizes d = (m / rho)^(1/3) agree across the interface.  The gas
+    fills a shell around each droplet, thick enough for about n_gas gas
+    particles in all.  The spheres' surfaces are `gap` spacings apart along x.
+    Pressure equilibrium: the gas at 1e5 Pa, the water compressed to the
+    same Tait pressure."""
+    a = (4.0 / 3.0 * np.pi * radius ** 3 / n_sphere) ** (1.0 / 3.0)
+    shell = (n_gas / 2.0) * a ** 3 / (4.0 * np.pi * radius ** 2)      # gas thickness around each sphere
+    cx = radius + 0.5 * gap * a
+    ext = radius + shell + 2 * a
+    nx = int(np.ceil((cx + ext) / a)); ny = int(np.ceil(ext / a))
+    i = np.arange(-nx, nx + 1) * a
+    j = np.arange(-ny, ny + 1) * a
+    X, Y, Z = np.meshgrid(i, j, j, indexing="ij")
+    X, Y, Z = X.ravel(), Y.ravel(), Z.ravel()
+    r1 = np.sqrt((X + cx) ** 2 + Y ** 2 + Z ** 2)
+    r2 = np.sqrt((X - cx) ** 2 + Y ** 2 + Z ** 2)
+    water = (r1 <= radius) | (r2 <= radius)
+    gas = ~water & ((r1 <= radius + shell) | (r2 <= radius + shell))
+    keep = water | gas
+    X, Y, Z, water = X[keep], Y[keep], Z[keep], water[keep]
+    n = len(X)
+    u = uniform(seed, 3 * n)
+    X = X + jitter * a * (2 * u[0::3] - 1)
+    Y = Y + jitter * a * (2 * u[1::3] - 1)
+    Z = Z + jitter * a * (2 * u[2::3] - 1)
+    w_mat = MaterialSpec("tait", 7.0, rho0=1000.0, c0=1500.0)
+    g_mat = MaterialSpec("ideal", 1.4)
+    p0 = 1e5
+    B = w_mat.rho0 * w_mat.c0 ** 2 / w_mat.gamma
+    rho_w = w_mat.rho0 * (1.0 + p0 / B) ** (1.0 / w_mat.gamma)
+    rho_g = w_mat.rho0 / 1000.0
+    e_g = p0 / ((g_mat.gamma - 1.0) * rho_g)
+    rho = np.where(water, rho_w, rho_g)
+    vx = np.where(water, np.where(X < 0, 0.5 * speed, -0.5 * speed), 0.0)
+    e = np.where(water, 0.0, e_g)
+    arrays = dict(x=X, y=Y, z=Z, vx=vx, vy=np.zeros(n), vz=np.zeros(n), rho=rho, E=e + 0.5 * vx * vx,
+                  m=rho * a ** 3)
+    mat = np.where(water, 0, 1).astype(np.int32)
+    return Problem(f"droplets_{n}", 3, arrays, [w_mat, g_mat], mat=mat, kernel="cubic", kappa=2.0, eta=1.3,
+                   cfl=0.3, n_steps=n_steps, units=units, unit_dim=3, n_upd=10,
+                   meta=dict(a=a, radius=radius, shell=shell, n_water=int(water.sum()), n_gas=int((~water).sum())))
+
+
 # ---------------------------------------------------------------------------
 # Voronoi generator seeding
 # ---------------------------------------------------------------------------

@@ -1,8 +1,9 @@
 """GPU parity for the Tait and Mie-Grueneisen closures (the workloads of the
 other tests use ideal and stiffened gases): rates to 1e-10 (FP64) and 1e-4
 (mixed) against the oracle, FP64 steps to 1e-10 with the per-step search and
-with Verlet lists, on a Tait water block and on the grooved lead ejecta
-sample (Mie-Grueneisen lead, symmetric impact at 1 km/s)."""
+with Verlet lists, on a Tait water block, on the grooved lead ejecta sample
+(Mie-Grueneisen lead, symmetric impact at 1 km/s) and on colliding Tait
+droplets in an ideal gas at 1:1000 density (two materials in one instance)."""
 import numpy as np
 import pytest
 
@@ -28,6 +29,8 @@ def _rel(a, b):
 PROBLEMS = {
     "water_tait": lambda: synth.water_block(side=8),
     "lead_ejecta": lambda: synth.ejecta(nx=16, periods=2, lam=8, nz=3, units=0),
+    # Tait droplets in ideal gas, 1:1000 density (mass) contrast, two materials in one instance
+    "droplets": lambda: synth.droplets(n_sphere=3000, n_gas=1500, units=0),
 }
 
 
