@@ -444,7 +444,7 @@ def run_extras(args, dev) -> dict:
     rho0, c0v, gv = 2700.0, 5300.0, 2.0
     adj = {}
 
-    def grad_run(prec, n_steps, every):
+    def grad_run(prec, n_steps, every, reverse="fp64"):
         v = torch.tensor(1000.0, dtype=torch.float64, device=dev, requires_grad=True)
         c0 = torch.tensor(c0v, dtype=torch.float64, device=dev, requires_grad=True)
         g = torch.tensor(gv, dtype=torch.float64, device=dev, requires_grad=True)
@@ -452,7 +452,7 @@ def run_extras(args, dev) -> dict:
         vel = vel + torch.stack([torch.zeros_like(m), torch.zeros_like(m), -v * proj], dim=1)
         rho = torch.full((q.n,), rho0, dtype=torch.float64, device=dev)
         E = c0 * c0 / (g - 1.0) + 0.5 * vel[:, 2] ** 2
-        spec = RunSpec(m=m, n_steps=n_steps, every=every, precision=prec, rho0=rho0)
+        spec = RunSpec(m=m, n_steps=n_steps, every=every, precision=prec, rho0=rho0, reverse=reverse)
         torch.cuda.synchronize()
         e0, e1, e2 = ev(), ev(), ev()
         e0.record()
@@ -464,14 +464,18 @@ def run_extras(args, dev) -> dict:
         e2.synchronize()
         return e0.elapsed_time(e1), e1.elapsed_time(e2), [v.grad.item(), c0.grad.item(), g.grad.item()]
 
-    for prec in ("fp64", "mixed"):
-        grad_run(prec, 10, 5)                      # warm-up: first-use costs of the reverse path
-        fwd, bwd, grad = grad_run(prec, 100, 10)
-        adj[prec] = {"forward_ms": fwd, "backward_ms": bwd,
+    # fp64: FP64 forward and reverse; mixed: FP32 forward with FP64 adjoint accumulation (the pair
+    # derivatives in FP64); mixed_fp32_reverse: the pair derivatives in FP32 with Kahan sums
+    for name, prec, rev in (("fp64", "fp64", "fp64"), ("mixed", "mixed", "fp64"), ("mixed_fp32_reverse", "mixed", "fp32")):
+        grad_run(prec, 10, 5, rev)                 # warm-up: first-use costs of the reverse path
+        fwd, bwd, grad = grad_run(prec, 100, 10, rev)
+        adj[name] = {"forward_ms": fwd, "backward_ms": bwd,
                      "value": q.n * 100 / ((fwd + bwd) * 1e-3), "unit": UNIT + " (forward + reverse)",
                      "grad": grad}
-    gm, g64 = np.array(adj["mixed"]["grad"]), np.array(adj["fp64"]["grad"])
-    adj["mixed_vs_fp64_grad_max_rel"] = float(np.max(np.abs(gm - g64) / np.abs(g64)))
+    g64 = np.array(adj["fp64"]["grad"])
+    adj["mixed_vs_fp64_grad_max_rel"] = float(np.max(np.abs(np.array(adj["mixed"]["grad"]) - g64) / np.abs(g64)))
+    adj["mixed_fp32_reverse_vs_fp64_grad_max_rel"] = float(
+        np.max(np.abs(np.array(adj["mixed_fp32_reverse"]["grad"]) - g64) / np.abs(g64)))
     adj["workload"] = f"plate impact {q.n} particles, 100 steps, checkpoints every 10, d(rear-face v_z)/d(v, c0, gamma)"
     out["adjoint"] = adj
     return out

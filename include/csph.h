@@ -121,7 +121,8 @@ typedef struct sph_ckpt {
                                  as recorded with sph_last_dt during the forward run */
   int32_t rates_from_state;   /* 1 if the held rates were evaluated at this very state
                                  (the run's first checkpoint), else 0 */
-  int32_t pad_;
+  int32_t reverse_fp64;       /* mixed-precision handle: 1 = pair derivatives in FP64 (FP32 forward
+                                 replay, FP64 adjoint), 0 = in FP32 with Kahan sums; ignored in FP64 */
 } sph_ckpt;
 
 /* Create a handle for `s->n` particles split into n_instances independent

@@ -55,7 +55,7 @@ class sph_state(C.Structure):
 
 
 class sph_ckpt(C.Structure):
-    _fields_ = [("state", sph_state), ("dt", C.c_void_p), ("rates_from_state", C.c_int32), ("pad_", C.c_int32)]
+    _fields_ = [("state", sph_state), ("dt", C.c_void_p), ("rates_from_state", C.c_int32), ("reverse_fp64", C.c_int32)]
 
 
 class sph_balance_params(C.Structure):

@@ -8,9 +8,11 @@ CSPHRun.apply(pos, vel, rho, E, c0, gamma, spec) -> (pos, vel, rho, E)
   parameters of material 0; spec: RunSpec (fixed problem data).
 The time steps of the forward run are recorded and held fixed in the
 backward pass (dt is a stop-gradient), as is the pair set of each step.
-spec.precision sets both passes: "mixed" runs the pair fluxes and the pair
-derivatives in FP32 (Kahan sums), "fp64" runs both in FP64; the chain through
-the EOS and the kick-drift-kick algebra is FP64 in both.
+spec.precision sets the forward replay ("mixed": FP32 pair fluxes, "fp64");
+spec.reverse sets the pair derivatives of a mixed run ("fp64": FP32 forward
+with FP64 adjoint accumulation; "fp32": FP32 with Kahan sums, several times
+faster); the chain through the EOS and the kick-drift-kick algebra is FP64
+in all cases.
 """
 from __future__ import annotations
 
@@ -36,6 +38,7 @@ class RunSpec:
     kappa: float = 2.0
     cfl: float = 0.3
     precision: str = "mixed"
+    reverse: str = "fp64"            # mixed precision: pair derivatives in "fp64" or "fp32" (Kahan sums)
     cell_cap: int = 1 << 24
     record: dict = field(default_factory=dict)   # filled by forward: dts, loss bookkeeping
 
@@ -145,6 +148,7 @@ class CSPHRun(torch.autograd.Function):
             ck.state = run.state(snap)
             ck.dt = ctx.dts[k0:].data_ptr()
             ck.rates_from_state = 1 if k0 == 0 else 0
+            ck.reverse_fp64 = 1 if spec.reverse == "fp64" else 0
             abi.sph_step_adjoint(run.handle, ck, length, adj_s, adj_s, par.data_ptr(), st)
         gpos = torch.stack([adj[k] for k in ("x", "y", "z")[:dim]], dim=1)
         gvel = torch.stack([adj[k] for k in ("vx", "vy", "vz")[:dim]], dim=1)

@@ -43,7 +43,8 @@ void free_all(sph_handle* h) {
                   h->load_acc, h->adj_bits, h->unit_off, h->unit_list, h->unit_work, h->unit_total, h->unit_stats,
                   h->status, h->counters, h->scratch, h->adj_G,
                   h->adj_GR, h->adj_pair, h->adj_par, h->adj_W, h->adj_store, h->mat_dev, h->vlist, h->vcnt,
-                  h->vref, h->vflag, h->grad_p, h->grad_v};
+                  h->vref, h->vflag, h->grad_p, h->grad_v, h->adj64_A, h->adj64_B, h->adj64_C,
+                  h->adj64_rho};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -653,6 +654,14 @@ int sph_step_adjoint(sph_handle* h, const sph_ckpt* ck, int n_steps, const sph_s
     CK(h, dalloc(&h->adj_W, (size_t)kAdjW * n));
     CK(h, cudaMemsetAsync(h->adj_W, 0, sizeof(double) * kAdjW * n, st));
   }
+  // FP64 pair derivatives on a mixed-precision handle (the forward replay stays mixed)
+  const bool rev64 = h->dp.precision == SPH_PREC_MIXED && ck->reverse_fp64 != 0;
+  if (rev64 && !h->adj64_A) {
+    CK(h, dalloc(reinterpret_cast<D4**>(&h->adj64_A), n));
+    CK(h, dalloc(reinterpret_cast<D4**>(&h->adj64_B), n));
+    CK(h, dalloc(reinterpret_cast<D2**>(&h->adj64_C), n));
+    CK(h, dalloc(&h->adj64_rho, n));
+  }
   if (n_steps > h->adj_store_steps) {
     if (h->adj_store) CK(h, cudaFree(h->adj_store));
     h->adj_store = nullptr;
@@ -678,16 +687,26 @@ int sph_step_adjoint(sph_handle* h, const sph_ckpt* ck, int n_steps, const sph_s
     CK(h, cudaMemcpyAsync(h->dt, ck->dt + k, sizeof(double), cudaMemcpyDeviceToDevice, st));
     CK(h, launch_kick_drift(h, W, st));
     CK(h, launch_build_grid(h, W, st));
-    CK(h, launch_pack(h, W, true, st));
-    CK(h, launch_rates_vjp(h, W, *adj_in, ck->dt + k, 1, adj_params, st));
+    if (rev64) {
+      CK(h, launch_pack_fp64(h, W, true, h->adj64_A, h->adj64_B, h->adj64_C, h->adj64_rho, st));
+      CK(h, launch_rates_vjp(h, W, *adj_in, ck->dt + k, 1, adj_params, st, true));
+    } else {
+      CK(h, launch_pack(h, W, true, st));
+      CK(h, launch_rates_vjp(h, W, *adj_in, ck->dt + k, 1, adj_params, st));
+    }
   }
   if (ck->rates_from_state) {
     // the held rates at the checkpoint were evaluated at its own state
     CK(h, copy_dynamic(W, ck->state, n, st));
     CK(h, launch_derive_dt(h, W, true, st));
     CK(h, launch_build_grid(h, W, st));
-    CK(h, launch_pack(h, W, false, st));
-    CK(h, launch_rates_vjp(h, W, *adj_in, h->dt, 0, adj_params, st));
+    if (rev64) {
+      CK(h, launch_pack_fp64(h, W, false, h->adj64_A, h->adj64_B, h->adj64_C, h->adj64_rho, st));
+      CK(h, launch_rates_vjp(h, W, *adj_in, h->dt, 0, adj_params, st, true));
+    } else {
+      CK(h, launch_pack(h, W, false, st));
+      CK(h, launch_rates_vjp(h, W, *adj_in, h->dt, 0, adj_params, st));
+    }
   }
   return SPH_OK;
 }

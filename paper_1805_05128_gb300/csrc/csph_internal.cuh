@@ -144,6 +144,10 @@ struct sph_handle {
   size_t scratch_bytes = 0;
 
   // reverse mode (sph_step_adjoint), allocated on first use
+  void* adj64_A = nullptr;            // FP64 operands of a mixed handle's FP64 reverse pass (D4, D4, D2)
+  void* adj64_B = nullptr;
+  void* adj64_C = nullptr;
+  double* adj64_rho = nullptr;
   csph::D4* adj_G = nullptr;          // rate adjoints / m, slot order (float4 in mixed mode)
   csph::D2* adj_GR = nullptr;         // (dL/ddrho, rho) of the slot (float2 in mixed mode)
   double* adj_pair = nullptr;         // 11 per particle: own-side pair derivatives
@@ -260,9 +264,12 @@ cudaError_t launch_verlet_flag(sph_handle* h, cudaStream_t st);
 cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st);
 cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st);
 cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st);
-// rates VJP at the state packed by launch_pack (k_adjoint.cu)
+// rates VJP at the state packed by launch_pack (k_adjoint.cu); fp64_pairs: the
+// operands were packed in FP64 by launch_pack_fp64 into adj64_* (mixed handle)
 cudaError_t launch_rates_vjp(sph_handle* h, const sph_state& W, sph_state& adj, const double* dt, int predicted,
-                             double* par, cudaStream_t st);
+                             double* par, cudaStream_t st, bool fp64_pairs = false);
+cudaError_t launch_pack_fp64(sph_handle* h, const sph_state& s, bool predict, void* A, void* B, void* C,
+                             double* rho_out, cudaStream_t st);
 // Exclusive scan of cnt[0, *total) into start[0, *total], start[*total] = n_total;
 // cnt is zeroed; launched for up to `cap` elements.
 cudaError_t launch_exclusive_scan(int32_t* cnt, const int64_t* total, int32_t* sums, int32_t* start,
@@ -271,8 +278,10 @@ cudaError_t launch_conservation(sph_handle* h, const sph_state& s, double* out, 
 cudaError_t launch_check_finite(sph_handle* h, const sph_state& s, cudaStream_t st);
 cudaError_t launch_max_volume(sph_handle* h, const sph_state& s, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_pair(sph_handle* h, const sph_state& s, cudaStream_t st);
+// A64/B64/C64: FP64 operands replacing the handle's packs (FP64 kernel on a mixed handle)
 cudaError_t launch_pair_vjp(sph_handle* h, const sph_state& s, const void* G, const void* GR2, double* out,
-                            cudaStream_t st);
+                            cudaStream_t st, const void* A64 = nullptr, const void* B64 = nullptr,
+                            const void* C64 = nullptr);
 // Verlet lists: build (k_pair over the (1 + beta) radius, returns at once unless vflag[0]) and
 // the pair evaluation over the lists
 cudaError_t launch_list_build(sph_handle* h, const sph_state& s, cudaStream_t st);

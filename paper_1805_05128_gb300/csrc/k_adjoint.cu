@@ -168,9 +168,21 @@ __global__ void k_sum_params(int64_t n, const double* __restrict__ par, double* 
 // launch_build_grid and launch_pack in the handle's precision), given the
 // adjoint in adj; updates adj and adds the parameter gradient to par.
 cudaError_t launch_rates_vjp(sph_handle* h, const sph_state& W, sph_state& adj, const double* dt, int predicted,
-                             double* par, cudaStream_t st) {
+                             double* par, cudaStream_t st, bool fp64_pairs) {
   const int64_t n = h->n;
   const int g = grid_for(n, kBlock);
+  if (fp64_pairs) {
+    k_adj_pack<double, D4, D2><<<g, kBlock, 0, st>>>(n, h->dp.dim, h->perm, adj, W.m, h->adj64_rho, dt, predicted,
+                                                      h->adj_G, h->adj_GR);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_pair_vjp(h, W, h->adj_G, h->adj_GR, h->adj_pair, st, h->adj64_A, h->adj64_B, h->adj64_C);
+    if (e != cudaSuccess) return e;
+    k_vjp_chain<<<g, kBlock, 0, st>>>(n, h->dp, W, adj, h->adj_pair, dt, predicted, h->adj_par);
+    k_sum_params<<<1, 1024, 0, st>>>(n, h->adj_par, par);
+    h->launches += 3;
+    return cudaGetLastError();
+  }
   if (h->dp.precision == SPH_PREC_MIXED)
     k_adj_pack<float, float4, float2><<<g, kBlock, 0, st>>>(n, h->dp.dim, h->perm, adj, W.m, h->rho_slot, dt,
                                                              predicted, reinterpret_cast<float4*>(h->adj_G),

@@ -1108,7 +1108,7 @@ PairArgs make_args(sph_handle* h, const sph_state& s) {
 // (k_pack of the handle's precision) and the adjoint operands G, GR2 (slot
 // order, same precision) must be in place; writes 11 doubles per particle.
 cudaError_t launch_pair_vjp(sph_handle* h, const sph_state& s, const void* G, const void* GR2, double* out,
-                            cudaStream_t st) {
+                            cudaStream_t st, const void* A64, const void* B64, const void* C64) {
   PairArgs a = make_args(h, s);
   a.K = 0;
   a.collect_adj = 0;
@@ -1116,10 +1116,16 @@ cudaError_t launch_pair_vjp(sph_handle* h, const sph_state& s, const void* G, co
   a.G = G;
   a.GR2 = GR2;
   a.vjp_out = out;
+  const bool fp64 = A64 != nullptr || h->dp.precision != SPH_PREC_MIXED;
+  if (A64) {                       // FP64 operands of a mixed handle: unscaled volumes
+    a.A = A64;
+    a.B = B64;
+    a.C = C64;
+    a.vinv = 1.0;
+  }
   cudaError_t e = cudaMemsetAsync(&h->counters[5], 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, kModeVjp>(h, a, st)
-                                        : launch_dim<false, kModeVjp>(h, a, st);
+  e = fp64 ? launch_dim<false, kModeVjp>(h, a, st) : launch_dim<true, kModeVjp>(h, a, st);
   h->launches += 1;
   return e;
 }

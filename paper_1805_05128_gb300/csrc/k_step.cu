@@ -726,6 +726,17 @@ cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStr
 }
 
 
+// k_pack's FP64 variant into the given operand arrays (the FP64 reverse pass
+// of a mixed-precision handle).
+cudaError_t launch_pack_fp64(sph_handle* h, const sph_state& s, bool predict, void* A, void* B, void* C,
+                             double* rho_out, cudaStream_t st) {
+  k_pack<false><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->grid, h->dt,
+                                            predict ? 1 : 0, h->perm, h->cell_of, A, B, C, rho_out, h->slot_cell,
+                                            h->slot_unit, h->K, h->status);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st) {
   k_kick2<<<h->nblk, kBlock, 0, st>>>(h->dp.dim, s, h->blk_start, h->blk_end, h->blk_inst, h->inst_blk, h->dt,
                                       t_dev);

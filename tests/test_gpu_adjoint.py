@@ -35,7 +35,7 @@ def _geometry(proj, target):
     return prob, pos, proj_mask, rear, m
 
 
-def _loss_and_grads(proj, target, n_steps, every, precision, v0=1000.0):
+def _loss_and_grads(proj, target, n_steps, every, precision, v0=1000.0, reverse="fp64"):
     from paper_1805_05128_gb300.adjoint import RunSpec, csph_run
     prob, pos, proj_mask, rear, m = _geometry(proj, target)
     v = torch.tensor(v0, dtype=torch.float64, device="cuda", requires_grad=True)
@@ -46,7 +46,7 @@ def _loss_and_grads(proj, target, n_steps, every, precision, v0=1000.0):
     vel = vel + torch.stack([torch.zeros_like(m), torch.zeros_like(m), -v * proj_mask.double()], dim=1)
     rho = torch.full((n,), RHO0, dtype=torch.float64, device="cuda")
     E = c0 * c0 / (g - 1.0) + 0.5 * vel[:, 2] ** 2          # P = 0 at rho0 for the stiffened gas
-    spec = RunSpec(m=m, n_steps=n_steps, every=every, precision=precision, rho0=RHO0)
+    spec = RunSpec(m=m, n_steps=n_steps, every=every, precision=precision, rho0=RHO0, reverse=reverse)
     p1, v1, r1, E1 = csph_run(pos, vel, rho, E, c0, g, spec)
     loss = v1[rear, 2].mean()
     loss.backward()
@@ -100,8 +100,10 @@ def test_adjoint_matches_central_differences(proj, target, n_steps, every):
         assert grads[k] == pytest.approx(fd, rel=1e-5), (name, grads[k], fd)
 
 
-def test_mixed_forward_gradient_close_to_fp64():
-    """FP32 pair fluxes in the forward replay, FP64 adjoint accumulation."""
+@pytest.mark.parametrize("reverse,tol", [("fp64", 1e-4), ("fp32", 1e-3)])
+def test_mixed_forward_gradient_close_to_fp64(reverse, tol):
+    """FP32 pair fluxes in the forward replay; pair derivatives in FP64 (FP64
+    adjoint accumulation) or in FP32 with Kahan sums."""
     _, g64, _, _ = _loss_and_grads(4, (10, 10, 4), 20, 5, "fp64")
-    _, g32, _, _ = _loss_and_grads(4, (10, 10, 4), 20, 5, "mixed")
-    assert np.allclose(g32, g64, rtol=1e-3), (g32, g64)
+    _, g32, _, _ = _loss_and_grads(4, (10, 10, 4), 20, 5, "mixed", reverse=reverse)
+    assert np.allclose(g32, g64, rtol=tol), (g32, g64)
