@@ -165,6 +165,23 @@ def run_reference(args, rank: int):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of the ranks' values of x (the slowest rank's time); x
+    itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_per_rank: int, world: int, steps: int, ms: float) -> float:
+    """Whole-job particle-steps/s of `world` replicas of an n_per_rank-particle
+    workload, each advanced `steps` steps, the slowest taking ms."""
+    return n_per_rank * world * steps / (ms * 1e-3)
+
+
 def run_gpu(args, rank: int, world: int, local_rank: int):
     import torch
     import synth
@@ -206,12 +223,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     half_pairs, candidates, fp64_checks = sim.pair_counts()
     builds = (sim.list_builds()[0] - builds0) if args.beta > 0 else args.steps
     status = sim.read_status()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     n_total = prob.n * world
-    value = n_total * args.steps / (ms * 1e-3)
+    value = job_value(prob.n, world, args.steps, ms)
 
     # ---- end to end: host state in pinned memory, copied in and out every step
     e2e_value, e2e_steps, h2d, d2h = None, 0, 0, 0
@@ -237,11 +251,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         f1.record()
         torch.cuda.synchronize()
         e2e_ms = f0.elapsed_time(f1)
-        if dist:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e_value = n_total * e2e_steps / (e2e_ms * 1e-3)
+        e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+        e2e_value = job_value(prob.n, world, e2e_steps, e2e_ms)
 
     if rank != 0:
         return None
