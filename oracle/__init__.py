@@ -22,6 +22,7 @@ _SO = os.path.join(_OUT_DIR, "liboracle.so")
 
 KERNEL_CUBIC, KERNEL_WENDLAND_C2 = 0, 1
 EOS_IDEAL, EOS_STIFFENED, EOS_TAIT, EOS_MIE_GRUNEISEN = 0, 1, 2, 3
+SOLVER_ACOUSTIC, SOLVER_HLL = 0, 1
 MAX_MAT = 4
 
 
@@ -48,7 +49,7 @@ class _Params(C.Structure):
     _fields_ = [("dim", C.c_int), ("kernel", C.c_int), ("kappa", C.c_double),
                 ("eta", C.c_double), ("cfl", C.c_double), ("cell_beta", C.c_double),
                 ("cell_cap", C.c_int64), ("n_mat", C.c_int), ("mat", _Material * MAX_MAT),
-                ("order", C.c_int)]
+                ("order", C.c_int), ("solver", C.c_int)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -136,12 +137,14 @@ class Params:
     cell_cap: int = 1 << 26
     materials: list = field(default_factory=lambda: [Material()])
     order: int = 1              # 2: states reconstructed to the pair midpoint (see orc_rates)
+    solver: int = 0             # 0: acoustic, 1: HLL with Davis wave speeds (see orc_riemann_hll)
 
     def cs(self) -> _Params:
         p = _Params()
         p.dim, p.kernel, p.kappa, p.eta, p.cfl = self.dim, self.kernel, self.kappa, self.eta, self.cfl
         p.cell_beta, p.cell_cap, p.n_mat = self.cell_beta, self.cell_cap, len(self.materials)
         p.order = self.order
+        p.solver = self.solver
         for i, m in enumerate(self.materials):
             p.mat[i].eos, p.mat[i].gamma, p.mat[i].rho0 = m.eos, m.gamma, m.rho0
             p.mat[i].c0, p.mat[i].p_inf, p.mat[i].s_a = m.c0, m.p_inf, m.s_a
@@ -214,6 +217,15 @@ def eos(mat: Material, rho: float, e: float):
 def riemann_acoustic(Pi, Pj, Zi, Zj, vRi, vRj):
     P, v = C.c_double(), C.c_double()
     lib().orc_riemann_acoustic(Pi, Pj, Zi, Zj, vRi, vRj, C.byref(P), C.byref(v))
+    return P.value, v.value
+
+
+def riemann_hll(Pi, Pj, Zi, Zj, vRi, vRj):
+    L = lib()
+    L.orc_riemann_hll.restype = None
+    L.orc_riemann_hll.argtypes = [C.c_double] * 6 + [_DP, _DP]
+    P, v = C.c_double(), C.c_double()
+    L.orc_riemann_hll(Pi, Pj, Zi, Zj, vRi, vRj, C.byref(P), C.byref(v))
     return P.value, v.value
 
 
@@ -356,11 +368,11 @@ _EOS_IDS = {"ideal": EOS_IDEAL, "stiffened": EOS_STIFFENED, "tait": EOS_TAIT,
 _KERNEL_IDS = {"cubic": KERNEL_CUBIC, "wendland_c2": KERNEL_WENDLAND_C2}
 
 
-def from_problem(prob, cell_cap: int = 1 << 26, order: int = 1):
+def from_problem(prob, cell_cap: int = 1 << 26, order: int = 1, solver: int = 0):
     """Oracle Params and State for a ``synth.Problem``."""
     mats = [Material(_EOS_IDS[m.eos], m.gamma, m.rho0, m.c0, m.p_inf, m.s_a) for m in prob.materials]
     p = Params(dim=prob.dim, kernel=_KERNEL_IDS[prob.kernel], kappa=prob.kappa, eta=prob.eta,
-               cfl=prob.cfl, cell_beta=0.0, cell_cap=cell_cap, materials=mats, order=order)
+               cfl=prob.cfl, cell_beta=0.0, cell_cap=cell_cap, materials=mats, order=order, solver=solver)
     return p, State(prob.dim, prob.arrays, prob.mat)
 
 

@@ -151,6 +151,22 @@ void orc_riemann_acoustic(double Pi, double Pj, double Zi, double Zj, double vRi
   *vstar = (Zi * vRi + Zj * vRj + Pi - Pj) / zs;
 }
 
+/* Alternative pair solver ("acoustic/HLL" in the specification of the
+ * workloads; Sec. 4.1 names no solver form).  Reading: the two-wave HLL
+ * state of the linearised Lagrangian acoustic system, d v/dt + dP/dm = 0,
+ * dP/dt + C^2 dv/dm = 0 along e^R, with the Davis wave-speed estimate
+ * S_L = -C, S_R = +C, C = max(Z_i, Z_j):
+ *   P* = (P_i + P_j)/2 + C (v_i^R - v_j^R)/2,
+ *   v* = (v_i^R + v_j^R)/2 + (P_i - P_j) / (2 C).
+ * Equal impedances give the acoustic solution; otherwise it is the more
+ * dissipative of the two.  Exchange-symmetric like the acoustic form.       */
+void orc_riemann_hll(double Pi, double Pj, double Zi, double Zj, double vRi, double vRj,
+                     double* Pstar, double* vstar) {
+  double C = Zi > Zj ? Zi : Zj;
+  *Pstar = 0.5 * (Pi + Pj) + 0.5 * C * (vRi - vRj);
+  *vstar = 0.5 * (vRi + vRj) + (Pi - Pj) / (2.0 * C);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Derived per-particle quantities: e = E - v^2/2 (Sec. 4.1, below
  * eq. SPH:Energy), P and c from the EOS, d = (m/rho)^(1/dim)
@@ -405,7 +421,10 @@ void orc_rates(const orc_params* p, orc_state* s, int64_t npairs, const int32_t*
       vR = vRj - 0.5 * minmod(r * svj, dv);
     }
     double Ps, vs;
-    if (Zi + Zj > 0.0) orc_riemann_acoustic(PL, PR, Zi, Zj, vL, vR, &Ps, &vs);
+    if (Zi + Zj > 0.0) {
+      if (p->solver == ORC_SOLVER_HLL) orc_riemann_hll(PL, PR, Zi, Zj, vL, vR, &Ps, &vs);
+      else orc_riemann_acoustic(PL, PR, Zi, Zj, vL, vR, &Ps, &vs);
+    }
     else { Ps = 0.5 * (PL + PR); vs = 0.5 * (vL + vR); }
     double hij = p->eta * (s->d[i] + s->d[j]) * 0.5;
     double dW = orc_kernel_dw(p->kernel, p->dim, p->kappa, r, hij);   /* W'_ij <= 0 */
@@ -809,7 +828,7 @@ static void cubic_dw_derivs(int dim, double r, double h, double* dw, double* dwd
 int orc_rates_vjp(const orc_params* p, const orc_state* s, int64_t npairs, const int32_t* pi, const int32_t* pj,
                   const double* ga, const double* gr, const double* gE,
                   double* bx, double* bv, double* brho, double* bE, double* bpar) {
-  if (p->order == 2) return -2;   /* the reverse mode covers the first-order scheme only */
+  if (p->order == 2 || p->solver == ORC_SOLVER_HLL) return -2;   /* first order, acoustic solver only */
   int64_t n = s->n;
   int dim = p->dim;
   if (p->kernel != ORC_KERNEL_CUBIC) return -1;
@@ -985,7 +1004,7 @@ int orc_step_replay(const orc_params* p, orc_state* s, int n_steps, int rates_va
  * bpar (2) accumulates dL/d(c0, gamma). */
 int orc_step_vjp(const orc_params* p, const orc_state* s, double dt, double* yx, double* yv, double* yrho,
                  double* yE, double* ya, double* ydrho, double* ydE, double* bpar) {
-  if (p->order == 2) return -2;   /* first-order scheme only */
+  if (p->order == 2 || p->solver == ORC_SOLVER_HLL) return -2;   /* first order, acoustic solver only */
   int64_t n = s->n;
   int dim = p->dim;
   double hdt = 0.5 * dt;

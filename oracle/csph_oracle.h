@@ -30,6 +30,7 @@ extern "C" {
 enum { ORC_KERNEL_CUBIC = 0, ORC_KERNEL_WENDLAND_C2 = 1 };
 enum { ORC_EOS_IDEAL = 0, ORC_EOS_STIFFENED = 1, ORC_EOS_TAIT = 2, ORC_EOS_MIE_GRUNEISEN = 3 };
 enum { ORC_MAX_MAT = 4 };
+enum { ORC_SOLVER_ACOUSTIC = 0, ORC_SOLVER_HLL = 1 };
 
 typedef struct {
   int eos;        /* ORC_EOS_* */
@@ -52,6 +53,7 @@ typedef struct {
   orc_material mat[ORC_MAX_MAT];
   int order;      /* 1 (particle-centre states, Sec. 4.1 as written) or 2 (states reconstructed
                      to the pair midpoint, the NEXT variant; see orc_rates) */
+  int solver;     /* ORC_SOLVER_ACOUSTIC (default) or ORC_SOLVER_HLL */
 } orc_params;
 
 /* Particle state, structure of arrays, host memory.  For dim < 3 the unused
@@ -82,6 +84,10 @@ double orc_kernel_dw(int kernel, int dim, double kappa, double r, double h);
 int orc_eos(const orc_material* mat, double rho, double e, double* P, double* c);
 void orc_riemann_acoustic(double Pi, double Pj, double Zi, double Zj, double vRi, double vRj,
                           double* Pstar, double* vstar);
+/* The two-wave HLL state of the same linearised problem with Davis wave
+ * speeds +-max(Z_i, Z_j) (see the .c file). */
+void orc_riemann_hll(double Pi, double Pj, double Zi, double Zj, double vRi, double vRj,
+                     double* Pstar, double* vstar);
 
 /* ---- per-particle derived quantities: e, P, c, d ---- */
 int64_t orc_derive(const orc_params* p, orc_state* s);
