@@ -49,6 +49,10 @@ extern "C" {
 #define SPH_PREC_MIXED 1  /* FP32 pair fluxes on local-origin offsets, Kahan-compensated
                              per-particle sums; FP64 positions, time, integration */
 
+#define SPH_SOLVER_ACOUSTIC 0  /* pair Riemann solver: linearised acoustic, impedance-weighted (Sec. 4.1) */
+#define SPH_SOLVER_HLL 1       /* two-wave HLL state of the same linearised problem with Davis speeds
+                                  -+max(Z_i, Z_j): the acoustic formula with both Z set to max(Z_i, Z_j) */
+
 #define SPH_MAX_MAT 4
 #define SPH_MAX_UNITS 256
 
@@ -90,7 +94,7 @@ typedef struct sph_params {
   int32_t order;      /* 1 (or 0): the particles' own P, v^R feed the pair Riemann solver (Sec. 4.1);
                          2: P and v^R extrapolated to the pair midpoint with SPH gradients, minmod-
                          limited against the pair jump (an extension; needs cell_beta = 0, no adjoint) */
-  int32_t pad2_;
+  int32_t solver;     /* SPH_SOLVER_*: the pair Riemann solver (HLL: no adjoint) */
 } sph_params;
 
 /* Particle state: structure of arrays in device memory, n elements each.

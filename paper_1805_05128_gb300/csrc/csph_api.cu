@@ -120,6 +120,8 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   if (p->order < 0 || p->order > 2) return fail(nullptr, SPH_ERR_INVALID, "order must be 1 or 2");
   if (p->order == 2 && p->cell_beta > 0.0)
     return fail(nullptr, SPH_ERR_INVALID, "order 2 runs with the per-step neighbour search (cell_beta = 0)");
+  if (p->solver != SPH_SOLVER_ACOUSTIC && p->solver != SPH_SOLVER_HLL)
+    return fail(nullptr, SPH_ERR_INVALID, "unknown pair solver");
   if (p->n_mat < 1 || p->n_mat > kMaxMaterials || (p->n_mat > SPH_MAX_MAT && !p->materials))
     return fail(nullptr, SPH_ERR_INVALID, "n_mat out of range (more than SPH_MAX_MAT need params.materials)");
   const sph_material* mats = p->materials ? p->materials : p->mat;
@@ -273,6 +275,7 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
 
   // order-2 reconstruction: SPH gradients of P and v in slot order
   h->order2 = p->order == 2;
+  h->solver = p->solver;
   if (h->order2) {
     if (p->precision == SPH_PREC_MIXED) {
       CKI(dalloc(reinterpret_cast<float4**>(&h->grad_p), n));
@@ -633,6 +636,7 @@ int sph_step_adjoint(sph_handle* h, const sph_ckpt* ck, int n_steps, const sph_s
   if (n_steps < 0 || (n_steps > 0 && !ck->dt)) return fail(h, SPH_ERR_INVALID, "need n_steps >= 0 and the dt record");
   if (h->n_inst != 1) return fail(h, SPH_ERR_INVALID, "the adjoint supports a single instance");
   if (h->order2) return fail(h, SPH_ERR_INVALID, "the adjoint covers the first-order scheme (order 1)");
+  if (h->solver != SPH_SOLVER_ACOUSTIC) return fail(h, SPH_ERR_INVALID, "the adjoint covers the acoustic pair solver");
   if (h->dp.kernel != SPH_KERNEL_CUBIC) return fail(h, SPH_ERR_INVALID, "the adjoint supports the cubic spline");
   for (int k = 0; k < h->dp.n_mat; ++k)
     if (h->mat_h[k].eos != SPH_EOS_IDEAL && h->mat_h[k].eos != SPH_EOS_STIFFENED)

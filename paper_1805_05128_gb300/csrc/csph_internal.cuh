@@ -170,6 +170,7 @@ struct sph_handle {
   // order-2 reconstruction (sph_params.order = 2): SPH gradients in slot order,
   // the pair kernel's precision: grad P, then grad v_x, grad v_y, grad v_z
   bool order2 = false;
+  int solver = SPH_SOLVER_ACOUSTIC;
 
   // mixed precision: scales (powers of two) of the packed volume and of W', set
   // by sph_init from the largest particle volume (1 in FP64 mode)

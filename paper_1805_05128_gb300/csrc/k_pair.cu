@@ -63,6 +63,7 @@ struct PairArgs {
   float kh_f, eta_half_f, kappa_f;
   double eta_half, kappa;
   int kernel;
+  int hll;           // pair solver: 0 acoustic, 1 HLL (Z_i = Z_j = max(Z_i, Z_j))
   // reverse mode (k_pair<..., VJP = true>): adjoint operands in slot order,
   // G = ((dL/da)/m, (dL/ddE)/m), GR2 = (dL/ddrho, rho), and the 11 own-side
   // derivatives per particle (particle order) it writes
@@ -320,7 +321,11 @@ struct FwdAcc {
     T vi = Bi.x * ex, vj = Bj.x * ex;
     if (DIM >= 2) { vi = fma_(Bi.y, ey, vi); vj = fma_(Bj.y, ey, vj); }
     if (DIM >= 3) { vi = fma_(Bi.z, ez, vi); vj = fma_(Bj.z, ez, vj); }
-    const T Zi = Ci.y, Zj = Cj.y;
+    T Zi = Ci.y, Zj = Cj.y;
+    // HLL with Davis speeds -+max(Z_i, Z_j) is the acoustic state with both
+    // impedances set to that maximum (exchange-symmetric, so the flux keeps
+    // its bitwise antisymmetry)
+    if (a.hll) { const T Zm = Zi > Zj ? Zi : Zj; Zi = Zm; Zj = Zm; }
     T Pi = Ci.x, Pj = Cj.x, wi = vi, wj = vj;   // states fed to the solver
     if constexpr (ORDER2) {
       const V4* __restrict__ GP = reinterpret_cast<const V4*>(a.gP);
@@ -1088,6 +1093,7 @@ PairArgs make_args(sph_handle* h, const sph_state& s) {
   a.kappa = h->dp.kappa;
   a.kappa_f = (float)h->dp.kappa;
   a.kernel = h->dp.kernel;
+  a.hll = h->solver == SPH_SOLVER_HLL;
   a.vlist = h->vlist;
   a.vcnt = h->vcnt;
   a.vref = h->vref;
