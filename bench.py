@@ -211,8 +211,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     with ClockSampler(gpu_index) as clk:
         sim.profile(True)
         e0.record()
-        for _ in range(args.steps):
-            sim.step(1)
+        sim.step(args.steps)            # one sph_step call runs the K steps, as a simulation does
         e1.record()
         torch.cuda.synchronize()
     if dist:

@@ -380,7 +380,10 @@ int sph_step(sph_handle* h, sph_state* s, int n_steps, double* t_dev, void* stre
   const bool vd3 = h->K > 0 && h->p.n_upd > 0;
   sph_balance_params bp{h->p.theta, h->p.sigma, h->p.gamma_b, h->p.beta_sh};
   for (int k = 0; k < n_steps; ++k) {
-    CK(h, launch_derive_dt(h, *s, false, st));
+    // the CFL minima of the step's start state: from the previous step's second
+    // kick inside this call (renumbering permutes an instance's particles and
+    // leaves its minimum unchanged), else a k_derive pass
+    if (k == 0) CK(h, launch_derive_dt(h, *s, false, st));
     CK(h, launch_reduce_dt(h, st));
     CK(h, launch_kick_drift(h, *s, st));
     if (h->verlet) {
@@ -401,7 +404,7 @@ int sph_step(sph_handle* h, sph_state* s, int n_steps, double* t_dev, void* stre
       CK(h, launch_pair(h, *s, st));
     }
     h->collect_adj = true;
-    CK(h, launch_kick2(h, *s, t_dev, st));
+    CK(h, launch_kick2(h, *s, t_dev, st, k + 1 < n_steps));
     if (vd3 && ++h->steps_since_balance >= h->p.n_upd) {
       // Alg. 1 outer loop: shift generators, reassign, renumber
       h->steps_since_balance = 0;

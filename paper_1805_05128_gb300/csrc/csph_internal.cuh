@@ -263,7 +263,9 @@ cudaError_t launch_kick_drift(sph_handle* h, const sph_state& s, cudaStream_t st
 cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st, const int* gate = nullptr);
 cudaError_t launch_verlet_flag(sph_handle* h, cudaStream_t st);
 cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st);
-cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st);
+// next_dt: also leave the CFL block minima of the new state in h->part (the next
+// step's dt without a k_derive pass)
+cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st, bool next_dt = false);
 cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st);
 // rates VJP at the state packed by launch_pack (k_adjoint.cu); fp64_pairs: the
 // operands were packed in FP64 by launch_pack_fp64 into adj64_* (mixed handle)

@@ -63,7 +63,6 @@ struct PairArgs {
   float kh_f, eta_half_f, kappa_f;
   double eta_half, kappa;
   int kernel;
-  int hll;           // pair solver: 0 acoustic, 1 HLL (Z_i = Z_j = max(Z_i, Z_j))
   // reverse mode (k_pair<..., VJP = true>): adjoint operands in slot order,
   // G = ((dL/da)/m, (dL/ddE)/m), GR2 = (dL/ddrho, rho), and the 11 own-side
   // derivatives per particle (particle order) it writes
@@ -267,7 +266,7 @@ __device__ __forceinline__ T minmod(T a, T b) {
   return (a > T(0) && b > T(0)) ? (a < b ? a : b) : ((a < T(0) && b < T(0)) ? (a > b ? a : b) : T(0));
 }
 
-template <bool MIXED, int DIM, bool ORDER2 = false>
+template <bool MIXED, int DIM, bool ORDER2 = false, bool HLL = false>
 struct FwdAcc {
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
@@ -325,7 +324,7 @@ struct FwdAcc {
     // HLL with Davis speeds -+max(Z_i, Z_j) is the acoustic state with both
     // impedances set to that maximum (exchange-symmetric, so the flux keeps
     // its bitwise antisymmetry)
-    if (a.hll) { const T Zm = Zi > Zj ? Zi : Zj; Zi = Zm; Zj = Zm; }
+    if constexpr (HLL) { const T Zm = Zi > Zj ? Zi : Zj; Zi = Zm; Zj = Zm; }
     T Pi = Ci.x, Pj = Cj.x, wi = vi, wj = vj;   // states fed to the solver
     if constexpr (ORDER2) {
       const V4* __restrict__ GP = reinterpret_cast<const V4*>(a.gP);
@@ -427,7 +426,7 @@ __device__ __forceinline__ void warp_counters(const PairArgs& a, bool act, unsig
 constexpr int kWarps = kPairBlock / 32;
 constexpr int kRow = kListCap + 2;   // padded row stride (16-bit entries): lane rows fall in distinct banks
 
-template <bool MIXED, int DIM, int MODE>
+template <bool MIXED, int DIM, int MODE, bool HLL = false>
 __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kModeFwd2) ? (MIXED ? 4 : 2)
                                                  : (MODE == kModeGrad ? (MIXED ? 5 : 3) : (MIXED ? 6 : 4)))
     k_pair(PairArgs a) {
@@ -517,7 +516,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
     if constexpr (VJP) { Gi = Gp[ii]; Ri = Rp[ii]; }
     Kahan<T> s_bx[3], s_bv[3], s_bP, s_bZ, s_bV, s_bd, s_brho;
 
-    FwdAcc<MIXED, DIM, MODE == kModeFwd2> fw;
+    FwdAcc<MIXED, DIM, MODE == kModeFwd2, HLL> fw;
     if constexpr (MODE == kModeFwd2) {
       fw.gPi = reinterpret_cast<const V4*>(a.gP)[ii];
       const V4* GV = reinterpret_cast<const V4*>(a.gV);
@@ -820,7 +819,7 @@ __device__ __forceinline__ T warp_sum(const Kahan<T>& k) {
   return v;
 }
 
-template <bool MIXED, int DIM>
+template <bool MIXED, int DIM, bool HLL = false>
 __global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair_lists(PairArgs a) {
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
@@ -830,6 +829,15 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair_lists(PairAr
   __shared__ float res[kWarps][6][32];            // per slot of the group: sums of rho, a (3), E, and dmax
   __shared__ double res64[kWarps][6][MIXED ? 1 : 32];
   __shared__ unsigned res_n[kWarps][32];
+  // unit shifts (-1, 0, 1) per axis of each neighbour-cell code; a table read
+  // and three multiplies are cheaper than the integer divisions and
+  // conversions of the decode, and give the same FP32 shifts bit for bit
+  __shared__ float4 unit_shift[32];
+  if (threadIdx.x < 32) {
+    const int c = threadIdx.x;
+    unit_shift[c] = make_float4((float)(c % 3 - 1), (float)((c / 3) % 3 - 1), (float)(c / 9 - 1), 0.f);
+  }
+  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
@@ -875,16 +883,17 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair_lists(PairAr
       const T khdi = MIXED ? (T)a.kh_f * Ai.w : T(0);
       const int ui = a.K > 0 ? a.slot_unit[i] : 0;
       const uint32_t* __restrict__ row = a.vlist + i * (int64_t)a.vcap;
-      FwdAcc<MIXED, DIM> fw;
+      FwdAcc<MIXED, DIM, false, HLL> fw;
       int qn = 0;          // queued pairs (warp-uniform)
       unsigned nacc = 0;   // accepted pairs of i (warp-uniform)
       auto drain = [&](int m) {                        // one flux per lane over the first m queued pairs
         if (lane < m) {
           const uint32_t e = q[lane];
           const int code = (int)(e & 31u);
-          const T sx = MIXED ? (T)(code % 3 - 1) * dcs : T(0);
-          const T sy = MIXED ? (T)((code / 3) % 3 - 1) * dcs : T(0);
-          const T sz = MIXED ? (T)(code / 9 - 1) * dcs : T(0);
+          const float4 U = unit_shift[code];
+          const T sx = MIXED ? (T)U.x * dcs : T(0);
+          const T sy = MIXED ? (T)U.y * dcs : T(0);
+          const T sz = MIXED ? (T)U.z * dcs : T(0);
           fw.pair(a, i, Ai, Bi, Ci, ui, (int64_t)(e >> 5), sx, sy, sz);
         }
         __syncwarp();
@@ -903,7 +912,8 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair_lists(PairAr
         if (kv) {
           if (MIXED) {
             const int code = (int)(e & 31u);
-            const T sx = (T)(code % 3 - 1) * dcs, sy = (T)((code / 3) % 3 - 1) * dcs, sz = (T)(code / 9 - 1) * dcs;
+            const float4 U = unit_shift[code];
+            const T sx = (T)U.x * dcs, sy = (T)U.y * dcs, sz = (T)U.z * dcs;
             const T dx = (S.x + sx) - Ai.x;
             const T dy = DIM >= 2 ? (S.y + sy) - Ai.y : T(0);
             const T dz = DIM >= 3 ? (S.z + sz) - Ai.z : T(0);
@@ -992,53 +1002,70 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair_lists(PairAr
 
 // Persistent grid: SMs x resident CTAs per SM, capped by the handle's
 // pair_blocks_per_sm (0 = as many as fit).
-template <bool MIXED, int DIM, int MODE>
+template <bool MIXED, int DIM, int MODE, bool HLL>
 cudaError_t launch_one(const PairArgs& args, int blocks_per_sm, cudaStream_t st) {
   static int sms = 0, per_sm = 0;
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<MIXED, DIM, MODE>, kPairBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<MIXED, DIM, MODE, HLL>, kPairBlock, 0);
     if (per_sm < 1) per_sm = 1;
   }
   const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
-  k_pair<MIXED, DIM, MODE><<<sms * b, kPairBlock, 0, st>>>(args);
+  k_pair<MIXED, DIM, MODE, HLL><<<sms * b, kPairBlock, 0, st>>>(args);
   return cudaGetLastError();
 }
 
+// The pair solver is a template parameter of the flux modes (the HLL select
+// costs about 1 % of the pair kernel when left as a run-time branch).
 template <bool MIXED, int MODE>
 cudaError_t launch_dim(sph_handle* h, const PairArgs& args, cudaStream_t st) {
   const int b = h->p.pair_blocks_per_sm;
+  constexpr bool kFlux = MODE == kModeFwd || MODE == kModeFwd2;
+  if (kFlux && h->solver == SPH_SOLVER_HLL) {
+    switch (h->dp.dim) {
+      case 1: return launch_one<MIXED, 1, MODE, kFlux>(args, b, st);
+      case 2: return launch_one<MIXED, 2, MODE, kFlux>(args, b, st);
+      default: return launch_one<MIXED, 3, MODE, kFlux>(args, b, st);
+    }
+  }
   switch (h->dp.dim) {
-    case 1: return launch_one<MIXED, 1, MODE>(args, b, st);
-    case 2: return launch_one<MIXED, 2, MODE>(args, b, st);
-    default: return launch_one<MIXED, 3, MODE>(args, b, st);
+    case 1: return launch_one<MIXED, 1, MODE, false>(args, b, st);
+    case 2: return launch_one<MIXED, 2, MODE, false>(args, b, st);
+    default: return launch_one<MIXED, 3, MODE, false>(args, b, st);
   }
 }
 
-template <bool MIXED, int DIM>
+template <bool MIXED, int DIM, bool HLL>
 cudaError_t launch_lists_one(const PairArgs& args, int blocks_per_sm, cudaStream_t st) {
   static int sms = 0, per_sm = 0;
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_lists<MIXED, DIM>, kPairBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_lists<MIXED, DIM, HLL>, kPairBlock, 0);
     if (per_sm < 1) per_sm = 1;
   }
   const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
-  k_pair_lists<MIXED, DIM><<<sms * b, kPairBlock, 0, st>>>(args);
+  k_pair_lists<MIXED, DIM, HLL><<<sms * b, kPairBlock, 0, st>>>(args);
   return cudaGetLastError();
 }
 
 template <bool MIXED>
 cudaError_t launch_lists_dim(sph_handle* h, const PairArgs& args, cudaStream_t st) {
   const int b = h->p.pair_blocks_per_sm;
+  if (h->solver == SPH_SOLVER_HLL) {
+    switch (h->dp.dim) {
+      case 1: return launch_lists_one<MIXED, 1, true>(args, b, st);
+      case 2: return launch_lists_one<MIXED, 2, true>(args, b, st);
+      default: return launch_lists_one<MIXED, 3, true>(args, b, st);
+    }
+  }
   switch (h->dp.dim) {
-    case 1: return launch_lists_one<MIXED, 1>(args, b, st);
-    case 2: return launch_lists_one<MIXED, 2>(args, b, st);
-    default: return launch_lists_one<MIXED, 3>(args, b, st);
+    case 1: return launch_lists_one<MIXED, 1, false>(args, b, st);
+    case 2: return launch_lists_one<MIXED, 2, false>(args, b, st);
+    default: return launch_lists_one<MIXED, 3, false>(args, b, st);
   }
 }
 
@@ -1093,7 +1120,6 @@ PairArgs make_args(sph_handle* h, const sph_state& s) {
   a.kappa = h->dp.kappa;
   a.kappa_f = (float)h->dp.kappa;
   a.kernel = h->dp.kernel;
-  a.hll = h->solver == SPH_SOLVER_HLL;
   a.vlist = h->vlist;
   a.vcnt = h->vcnt;
   a.vref = h->vref;

@@ -121,6 +121,42 @@ __device__ __forceinline__ double size_of(int dim, double m, double rho) {
   return dim == 1 ? vol : (dim == 2 ? sqrt(vol) : cbrt_fast(vol));
 }
 
+// d = (m / rho)^(1/D) for a mixed-precision step, with a third of the FP64
+// work of size_of: FP32 seeds for 1/rho and the root, each refined by one
+// FP64 Newton step (the error squares: ~1e-7 -> ~1e-14 relative).  The step's
+// pair decisions take this d as given and its FP32 fluxes are far coarser.
+__device__ __forceinline__ double size_of_mixed(int dim, double m, double rho) {
+  const float rf = (float)rho;
+  double r = (double)__frcp_rn(rf);
+  r = r * __fma_rn(-rho, r, 2.0);
+  const double vol = m * r;
+  if (dim == 1) return vol;
+  const float vf = (float)vol;
+  if (dim == 2) {
+    const float y0 = sqrtf(vf);
+    const double y = (double)y0;
+    return __fma_rn(__fma_rn(-y, y, vol), (double)(0.5f / y0), y);
+  }
+  if (!(vf > 1e-30f && vf < 1e30f)) return cbrt(vol);   // outside the FP32 seed's comfortable range
+  const float y0 = cbrtf(vf);
+  const double y = (double)y0;
+  return __fma_rn(-__fma_rn(y * y, y, -vol), (double)__frcp_rn(3.0f * y0 * y0), y);
+}
+
+// Half kick / drift y + a x: the oracle's correctly rounded product and sum
+// for an FP64 handle; one fused multiply-add for a mixed handle (FP64 is the
+// narrow pipe on this GPU and these kernels are bound by it).
+template <bool MIXED>
+__device__ __forceinline__ double axpy(double a, double x, double y) {
+  if constexpr (MIXED) return __fma_rn(a, x, y);
+  else return __dadd_rn(y, __dmul_rn(a, x));
+}
+
+// isfinite on the bits (integer ALU, not the FP64 pipe)
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+
 // Sound speed in FP32 from an FP64 specific internal energy (the closures of
 // eos() written in single precision; the stiffened gas in the form
 // c^2 = gamma (gamma - 1)(rho e - P_inf) / rho, without the P + P_inf
@@ -156,22 +192,36 @@ __device__ __forceinline__ float sound_speed_f32(const Mat& m, float rho, float 
 // FP64 divisions, roots and cube root of every particle are what bound this
 // kernel on GB300.  FP64 handles keep the FP64 expression (bit parity of dt).
 // ---------------------------------------------------------------------------
+// CFL order key of one particle's bound dt_i = eta d_i / (c_i + |v_i|) at the
+// given state: FP32 in a mixed-precision handle (see above), FP64 otherwise.
+__device__ __forceinline__ long long cfl_key(const DevParams& P, double vx, double vy, double vz, double E,
+                                             double rho, double m, int mi) {
+  const double v2 = vx * vx + vy * vy + vz * vz;
+  const double e = E - 0.5 * v2;
+  if (P.precision == SPH_PREC_MIXED) {
+    const float rf = (float)rho;
+    const float c = sound_speed_f32(P.mat[mi], rf, (float)e);
+    const float vol = (float)m / rf;
+    const float d = P.dim == 1 ? vol : (P.dim == 2 ? sqrtf(vol) : cbrtf(vol));
+    return dkey((double)((float)P.eta * d / (c + sqrtf((float)v2))));
+  }
+  double Pp, cp;
+  eos(P.mat[mi], rho, e, Pp, cp);
+  return dkey((P.eta * size_of(P.dim, m, rho)) / (cp + sqrt(v2)));
+}
+
 __global__ void k_derive(DevParams P, sph_state s, const int64_t* __restrict__ blk_start,
                          const int64_t* __restrict__ blk_end, BlockPart* part, int write_derived,
                          int with_bbox) {
   int64_t p = blk_start[blockIdx.x] + threadIdx.x;
   Red r;
   red_init(r);
-  if (p < blk_end[blockIdx.x] && !with_bbox && !write_derived && P.precision == SPH_PREC_MIXED) {
+  if (p < blk_end[blockIdx.x] && !with_bbox && !write_derived) {
+    // a step's CFL bound only (every load issued before the arithmetic)
     const double vx = ld(s.vx, p), vy = ld(s.vy, p), vz = ld(s.vz, p);
-    const double v2 = vx * vx + vy * vy + vz * vz;
-    const double e = s.E[p] - 0.5 * v2;
+    const double E = s.E[p], rho = s.rho[p], m = s.m[p];
     const int mi = s.mat ? s.mat[p] : 0;
-    const float rho = (float)s.rho[p];
-    const float c = sound_speed_f32(P.mat[mi], rho, (float)e);
-    const float vol = (float)s.m[p] / rho;
-    const float d = P.dim == 1 ? vol : (P.dim == 2 ? sqrtf(vol) : cbrtf(vol));
-    r.dtmin = dkey((double)((float)P.eta * d / (c + sqrtf((float)v2))));
+    r.dtmin = cfl_key(P, vx, vy, vz, E, rho, m, mi);
   } else if (p < blk_end[blockIdx.x]) {
     double vx = ld(s.vx, p), vy = ld(s.vy, p), vz = ld(s.vz, p);
     double v2 = vx * vx + vy * vy + vz * vz;
@@ -418,6 +468,7 @@ __global__ void k_cell_sort(const int64_t* __restrict__ total, const int32_t* __
 // Kick-drift: v <- v + dt/2 a, x <- x + dt v, rho, E half kicks; predicted
 // size d~ from rho~ = rho^h + dt/2 drho; bounding box and sizes for the mesh.
 // ---------------------------------------------------------------------------
+template <bool MIXED>
 __global__ void k_kick_drift(DevParams P, sph_state s, const int64_t* __restrict__ blk_start,
                              const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst,
                              const double* __restrict__ dt, BlockPart* part, int* status) {
@@ -425,25 +476,44 @@ __global__ void k_kick_drift(DevParams P, sph_state s, const int64_t* __restrict
   Red r;
   red_init(r);
   if (p < blk_end[blockIdx.x]) {
-    double h = dt[blk_inst[blockIdx.x]];
-    double hdt = 0.5 * h;
+    const int dim = P.dim;
+    const double h = dt[blk_inst[blockIdx.x]];
+    const double hdt = 0.5 * h;
     double* X[3] = {s.x, s.y, s.z};
     double* V[3] = {s.vx, s.vy, s.vz};
-    double* A[3] = {s.ax, s.ay, s.az};
+    const double* A[3] = {s.ax, s.ay, s.az};
+    // Every load is issued before the first store: the state arrays may alias
+    // as far as the compiler can tell, so a load placed after a store would
+    // wait for it, one memory round trip per component.
+    double x[3] = {0.0, 0.0, 0.0}, v[3] = {0.0, 0.0, 0.0}, acc[3] = {0.0, 0.0, 0.0}, xb[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a < dim) {
+        x[a] = X[a][p];
+        v[a] = V[a][p];
+        acc[a] = A[a][p];
+        if (P.vref) xb[a] = P.vref[(int64_t)a * P.n + p];
+      }
+    const double rho0 = s.rho[p], drho = s.drho[p], E0 = s.E[p], dE = s.dE[p], m = s.m[p];
+    const double db = P.vref ? P.vref[3 * P.n + p] : 0.0;
     bool finite = true;
-    for (int a = 0; a < P.dim; ++a) {
-      double vh = __dadd_rn(V[a][p], __dmul_rn(hdt, A[a][p]));
-      double xn = __dadd_rn(X[a][p], __dmul_rn(h, vh));
-      V[a][p] = vh;
-      X[a][p] = xn;
-      r.lo[a] = r.hi[a] = dkey(xn);
-      finite = finite && isfinite(xn);
-    }
-    double rh = __dadd_rn(s.rho[p], __dmul_rn(hdt, s.drho[p]));
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a < dim) {
+        v[a] = axpy<MIXED>(hdt, acc[a], v[a]);
+        x[a] = axpy<MIXED>(h, v[a], x[a]);
+        r.lo[a] = r.hi[a] = dkey(x[a]);
+        finite = finite && finite_bits(x[a]);
+      }
+    const double rh = axpy<MIXED>(hdt, drho, rho0);
+    const double En = axpy<MIXED>(hdt, dE, E0);
+    const double rp = axpy<MIXED>(hdt, drho, rh);
+    const double d = MIXED ? size_of_mixed(dim, m, rp) : size_of(dim, m, rp);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a < dim) { V[a][p] = v[a]; X[a][p] = x[a]; }
     s.rho[p] = rh;
-    s.E[p] = __dadd_rn(s.E[p], __dmul_rn(hdt, s.dE[p]));
-    double rp = __dadd_rn(rh, __dmul_rn(hdt, s.drho[p]));
-    double d = size_of(P.dim, s.m[p], rp);
+    s.E[p] = En;
     s.d[p] = d;
     r.d1 = dkey(d);
     if (P.vref) {
@@ -452,35 +522,63 @@ __global__ void k_kick_drift(DevParams P, sph_state s, const int64_t* __restrict
       // last build; summing the bounds of i and j covers the pair), kept with a 5 % margin
       // (differences in FP64, the bound itself in FP32: the 5 % margin dwarfs its rounding)
       float dsq = 0.0f;
-      for (int a = 0; a < P.dim; ++a) {
-        const float dx = (float)(X[a][p] - P.vref[(int64_t)a * P.n + p]);
-        dsq += dx * dx;
-      }
-      const double db = P.vref[3 * P.n + p];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (a < dim) {
+          const float dx = (float)(x[a] - xb[a]);
+          dsq += dx * dx;
+        }
       const float kh = (float)P.kh;
       const float crit = sqrtf(dsq) + kh * fmaxf((float)(d - db), 0.0f) - 0.95f * (float)P.cell_beta * kh * (float)db;
       r.viol = dkey((double)crit);
     }
-    if (!finite || !isfinite(d)) set_status(status, SPH_ERR_NONFINITE);
+    if (!finite || !finite_bits(d)) set_status(status, SPH_ERR_NONFINITE);
   }
   block_reduce(r);
   if (threadIdx.x == 0) write_part(part, r);
 }
 
 // Second half kick with the rates of the predicted state; instance time.
-__global__ void k_kick2(int dim, sph_state s, const int64_t* __restrict__ blk_start,
+// With part, also the block minima of the CFL keys at the new state, which
+// the next step of the same sph_step call takes instead of a k_derive pass.
+template <bool MIXED>
+__global__ void k_kick2(DevParams P, sph_state s, const int64_t* __restrict__ blk_start,
                         const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst,
-                        const int32_t* __restrict__ inst_blk, const double* __restrict__ dt, double* t_dev) {
-  int64_t p = blk_start[blockIdx.x] + threadIdx.x;
-  int b = blk_inst[blockIdx.x];
+                        const int32_t* __restrict__ inst_blk, const double* __restrict__ dt, double* t_dev,
+                        BlockPart* part) {
+  const int64_t p = blk_start[blockIdx.x] + threadIdx.x;
+  const int b = blk_inst[blockIdx.x];
   if (t_dev && threadIdx.x == 0 && inst_blk[b] == (int)blockIdx.x) t_dev[b] += dt[b];
-  if (p >= blk_end[blockIdx.x]) return;
-  double hdt = 0.5 * dt[b];
-  double* V[3] = {s.vx, s.vy, s.vz};
-  double* A[3] = {s.ax, s.ay, s.az};
-  for (int a = 0; a < dim; ++a) V[a][p] = __dadd_rn(V[a][p], __dmul_rn(hdt, A[a][p]));
-  s.rho[p] = __dadd_rn(s.rho[p], __dmul_rn(hdt, s.drho[p]));
-  s.E[p] = __dadd_rn(s.E[p], __dmul_rn(hdt, s.dE[p]));
+  long long key = LLONG_MAX;
+  if (p < blk_end[blockIdx.x]) {
+    const int dim = P.dim;
+    const double hdt = 0.5 * dt[b];
+    double* V[3] = {s.vx, s.vy, s.vz};
+    const double* A[3] = {s.ax, s.ay, s.az};
+    double v[3] = {0.0, 0.0, 0.0}, acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a < dim) { v[a] = V[a][p]; acc[a] = A[a][p]; }
+    const double rho0 = s.rho[p], drho = s.drho[p], E0 = s.E[p], dE = s.dE[p];
+    double m = 0.0;
+    int mi = 0;
+    if (part) { m = s.m[p]; mi = s.mat ? s.mat[p] : 0; }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a < dim) v[a] = axpy<MIXED>(hdt, acc[a], v[a]);
+    const double rho = axpy<MIXED>(hdt, drho, rho0);
+    const double E = axpy<MIXED>(hdt, dE, E0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a < dim) V[a][p] = v[a];
+    s.rho[p] = rho;
+    s.E[p] = E;
+    if (part) key = cfl_key(P, v[0], v[1], v[2], E, rho, m, mi);
+  }
+  if (part) {   // uniform over the grid: every thread reaches the block barrier
+    const long long k = block_min_key(key);
+    if (threadIdx.x == 0) part[blockIdx.x].dtmin = k;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -504,17 +602,33 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
   if (sl >= blk_end[blockIdx.x]) return;
   int b = blk_inst[blockIdx.x];
   int64_t p = perm[sl];
-  double hdt = predict ? 0.5 * dt[b] : 0.0;
+  // every load of the gathered particle first (the stores to P and c below
+  // would otherwise hold back the loads placed after them)
+  const bool pr = predict != 0;
   double v[3] = {ld(s.vx, p), ld(s.vy, p), ld(s.vz, p)};
-  if (predict) {
-    v[0] = __dadd_rn(v[0], __dmul_rn(hdt, s.ax[p]));
-    if (P.dim >= 2) v[1] = __dadd_rn(v[1], __dmul_rn(hdt, s.ay[p]));
-    if (P.dim >= 3) v[2] = __dadd_rn(v[2], __dmul_rn(hdt, s.az[p]));
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (pr) {
+    acc[0] = s.ax[p];
+    if (P.dim >= 2) acc[1] = s.ay[p];
+    if (P.dim >= 3) acc[2] = s.az[p];
   }
-  double rho = predict ? __dadd_rn(s.rho[p], __dmul_rn(hdt, s.drho[p])) : s.rho[p];
-  double E = predict ? __dadd_rn(s.E[p], __dmul_rn(hdt, s.dE[p])) : s.E[p];
+  const double rho0 = s.rho[p], E0 = s.E[p];
+  const double drho = pr ? s.drho[p] : 0.0, dE = pr ? s.dE[p] : 0.0;
+  const int mi = s.mat ? s.mat[p] : 0;
+  const double d = s.d[p];
+  const double m = s.m[p];
+  const double X[3] = {s.x[p], P.dim >= 2 ? s.y[p] : 0.0, P.dim >= 3 ? s.z[p] : 0.0};
+  const int32_t gc = cell_of[p];
+  int32_t u = s.unit ? s.unit[p] : 0;
+  const double hdt = pr ? 0.5 * dt[b] : 0.0;
+  if (pr) {
+    v[0] = axpy<MIXED>(hdt, acc[0], v[0]);
+    if (P.dim >= 2) v[1] = axpy<MIXED>(hdt, acc[1], v[1]);
+    if (P.dim >= 3) v[2] = axpy<MIXED>(hdt, acc[2], v[2]);
+  }
+  double rho = pr ? axpy<MIXED>(hdt, drho, rho0) : rho0;
+  double E = pr ? axpy<MIXED>(hdt, dE, E0) : E0;
   double e = E - 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-  int mi = s.mat ? s.mat[p] : 0;
   double Pp, cp;
   float cf = 0.0f;
   const Mat& mt = P.mat[mi];
@@ -531,12 +645,7 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
   }
   s.P[p] = Pp;
   s.c[p] = cp;
-  double d = s.d[p];
-  double m = s.m[p];
-  double X[3] = {s.x[p], P.dim >= 2 ? s.y[p] : 0.0, P.dim >= 3 ? s.z[p] : 0.0};
-  int32_t gc = cell_of[p];
   slot_cell[sl] = gc;
-  int32_t u = s.unit ? s.unit[p] : 0;
   if (u < 0 || u >= n_units) { if (n_units > 0) set_status(status, SPH_ERR_INVALID); u = 0; }
   slot_unit[sl] = u;
   rho_slot[sl] = rho;
@@ -663,8 +772,12 @@ cudaError_t launch_reduce_dt(sph_handle* h, cudaStream_t st) {
 }
 
 cudaError_t launch_kick_drift(sph_handle* h, const sph_state& s, cudaStream_t st) {
-  k_kick_drift<<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->dt, h->part,
-                                           h->status);
+  if (h->dp.precision == SPH_PREC_MIXED)
+    k_kick_drift<true><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->dt, h->part,
+                                                   h->status);
+  else
+    k_kick_drift<false><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->dt, h->part,
+                                                    h->status);
   h->launches += 1;
   return cudaGetLastError();
 }
@@ -737,9 +850,14 @@ cudaError_t launch_pack_fp64(sph_handle* h, const sph_state& s, bool predict, vo
   return cudaGetLastError();
 }
 
-cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st) {
-  k_kick2<<<h->nblk, kBlock, 0, st>>>(h->dp.dim, s, h->blk_start, h->blk_end, h->blk_inst, h->inst_blk, h->dt,
-                                      t_dev);
+cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st, bool next_dt) {
+  BlockPart* part = next_dt ? h->part : nullptr;
+  if (h->dp.precision == SPH_PREC_MIXED)
+    k_kick2<true><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->inst_blk, h->dt,
+                                              t_dev, part);
+  else
+    k_kick2<false><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->inst_blk, h->dt,
+                                               t_dev, part);
   h->launches += 1;
   return cudaGetLastError();
 }
