@@ -302,6 +302,14 @@ struct FwdAcc {
     const V4 Bj = B[j];
     const V2 Cj = C[j];
     T dx, dy, dz;
+    separation(Ai, Aj, sx, sy, sz, dx, dy, dz);
+    flux_at(a, i, Ai, Bi, Ci, ui, j, Aj, Bj, Cj, dx, dy, dz, P::r2_of(dx, dy, dz));
+  }
+
+  // x_j - x_i of the flux (mixed: FP32 offsets plus the cell shift, in an
+  // order that j's side negates exactly)
+  static __device__ __forceinline__ void separation(const V4& Ai, const V4& Aj, T sx, T sy, T sz, T& dx, T& dy,
+                                                    T& dz) {
     if (MIXED) {
       dx = (Aj.x - Ai.x) + sx;
       dy = DIM >= 2 ? (Aj.y - Ai.y) + sy : T(0);
@@ -311,7 +319,47 @@ struct FwdAcc {
       dy = DIM >= 2 ? __dsub_rn(Aj.y, Ai.y) : 0.0;
       dz = DIM >= 3 ? __dsub_rn(Aj.z, Ai.z) : 0.0;
     }
+  }
+
+  // A listed candidate j of slot i (never i itself): the interaction test of
+  // the scan, then the flux of an interacting pair.  Mixed: FP32 test on the
+  // flux's own separation, decided in FP64 (oracle order) within the band
+  // |r^2 - (kappa h_ij)^2| <= band, where FP32 rounding could flip it; FP64:
+  // the oracle's test.  Returns whether the pair interacts.
+  __device__ __forceinline__ bool pair_listed(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi,
+                                              const V2& Ci, int ui, int64_t j, T sx, T sy, T sz, T khdi,
+                                              float band, unsigned& nexact) {
+    const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
+    const V4* __restrict__ B = reinterpret_cast<const V4*>(a.B);
+    const V2* __restrict__ C = reinterpret_cast<const V2*>(a.C);
+    const V4 Aj = A[j];
+    const V4 Bj = B[j];       // requested with A[j]: most candidates interact
+    const V2 Cj = C[j];
+    T dx, dy, dz;
+    separation(Ai, Aj, sx, sy, sz, dx, dy, dz);
     const T r2 = P::r2_of(dx, dy, dz);
+    bool acc;
+    if (MIXED) {
+      const T R = fmaf((T)a.kh_f, Aj.w, khdi);
+      const T diff = fmaf(-R, R, r2);
+      acc = diff < T(0);
+      if (fabsf(diff) <= band) {
+        ++nexact;
+        acc = exact_accept(a, DIM, a.perm[i], a.perm[j]);
+      }
+    } else {
+      T ex, ey, ez;
+      P::sep(true, Ai, Aj, T(0), T(0), T(0), ex, ey, ez);   // x_j - x_i, oracle order
+      const double R = __dmul_rn(a.kh, __dadd_rn(Ai.w, Aj.w));
+      acc = P::r2_of(ex, ey, ez) < __dmul_rn(R, R);
+    }
+    if (acc) flux_at(a, i, Ai, Bi, Ci, ui, j, Aj, Bj, Cj, dx, dy, dz, r2);
+    return acc;
+  }
+
+  __device__ __forceinline__ void flux_at(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi, const V2& Ci,
+                                          int ui, int64_t j, const V4& Aj, const V4& Bj, const V2& Cj, T dx, T dy,
+                                          T dz, T r2) {
     dmax = Aj.w > dmax ? Aj.w : dmax;
     if (!(r2 > T(0))) return;  // coincident particles: no direction, no flux
     const T ir = rsqrt_(r2);
@@ -797,18 +845,18 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
 
 // Pair evaluation over the Verlet lists: one warp per slot i, taken in
 // groups of 32 consecutive slots from a global counter.  The warp reads i's
-// list 32 entries at a time (particle-major, so the reads are contiguous),
-// decides each entry as k_pair does (FP32 test outside the band of
-// 2^-12 D^c^2, FP64 in the oracle's operation order inside it), and appends
-// the accepted ones to a per-warp queue in shared memory (ballot + prefix
-// popcount, list order kept).  Whenever the queue holds 32 pairs, every lane
-// evaluates one flux with FwdAcc; the lanes' Kahan sums (a few pairs each)
-// are combined by a fixed butterfly, and the FP64 scaling of the rates is
-// done for the 32 slots of the group at once, one slot per lane.  Offsets stay relative to the cells of
-// the build and each pair's shift comes from its neighbour-cell code, so the
-// fluxes keep their bitwise antisymmetry; every order is fixed, so results
-// are reproducible bit for bit.
-constexpr int kListQueue = 64;
+// list 32 entries at a time (particle-major, so the reads are contiguous);
+// each lane decides its entry as k_pair does (FP32 test outside the band of
+// 2^-12 D^c^2, FP64 in the oracle's operation order inside it) and, if the
+// pair interacts, adds its flux to the lane's Kahan sums (FwdAcc).  Test and
+// flux share the loads and the separation; about 86 % of the entries of a
+// list built with beta = 0.15 interact, so the lanes whose entry does not
+// are cheaper than compacting the accepted ones first.  The lanes' sums are
+// combined by a fixed butterfly, and the FP64 scaling of the rates is done
+// for the 32 slots of the group at once, one slot per lane.  Offsets stay
+// relative to the cells of the build and each pair's shift comes from its
+// neighbour-cell code, so the fluxes keep their bitwise antisymmetry; every
+// order is fixed, so results are reproducible bit for bit.
 
 // Sum over the warp's lanes of their Kahan sums (s - c), by a fixed butterfly.
 template <typename T>
@@ -820,12 +868,11 @@ __device__ __forceinline__ T warp_sum(const Kahan<T>& k) {
 }
 
 template <bool MIXED, int DIM, bool HLL = false>
-__global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair_lists(PairArgs a) {
+__global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairArgs a) {
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
   using V4 = typename P::V4;
   using V2 = typename P::V2;
-  __shared__ uint32_t queue[kWarps][kListQueue];
   __shared__ float res[kWarps][6][32];            // per slot of the group: sums of rho, a (3), E, and dmax
   __shared__ double res64[kWarps][6][MIXED ? 1 : 32];
   __shared__ unsigned res_n[kWarps][32];
@@ -839,9 +886,7 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair_lists(PairAr
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
   const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
-  uint32_t* q = queue[warp];
   for (;;) {
     int64_t g0 = 0;
     if (lane == 0) g0 = (int64_t)atomicAdd(a.work_counter, 32ull);
@@ -884,63 +929,25 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 8 : 4) k_pair_lists(PairAr
       const int ui = a.K > 0 ? a.slot_unit[i] : 0;
       const uint32_t* __restrict__ row = a.vlist + i * (int64_t)a.vcap;
       FwdAcc<MIXED, DIM, false, HLL> fw;
-      int qn = 0;          // queued pairs (warp-uniform)
       unsigned nacc = 0;   // accepted pairs of i (warp-uniform)
-      auto drain = [&](int m) {                        // one flux per lane over the first m queued pairs
-        if (lane < m) {
-          const uint32_t e = q[lane];
-          const int code = (int)(e & 31u);
-          const float4 U = unit_shift[code];
-          const T sx = MIXED ? (T)U.x * dcs : T(0);
-          const T sy = MIXED ? (T)U.y * dcs : T(0);
-          const T sz = MIXED ? (T)U.z * dcs : T(0);
-          fw.pair(a, i, Ai, Bi, Ci, ui, (int64_t)(e >> 5), sx, sy, sz);
-        }
-        __syncwarp();
-        if (lane + m < qn) q[lane] = q[lane + m];      // keep the rest (fewer than 32) in order
-        __syncwarp();
-        qn -= m;
-      };
       for (int base = 0; base < cnt; base += 32) {
         const int k = base + lane;
         const bool kv = k < cnt;
         const uint32_t e = kv ? e_cur : 0u;
         if (base + 32 < cnt) e_cur = (k + 32 < cnt) ? row[k + 32] : 0u;   // next chunk, requested now
-        const int64_t j = e >> 5;
-        const V4 S = A[kv ? j : i];
         bool acc = false;
         if (kv) {
+          T sx = T(0), sy = T(0), sz = T(0);
           if (MIXED) {
-            const int code = (int)(e & 31u);
-            const float4 U = unit_shift[code];
-            const T sx = (T)U.x * dcs, sy = (T)U.y * dcs, sz = (T)U.z * dcs;
-            const T dx = (S.x + sx) - Ai.x;
-            const T dy = DIM >= 2 ? (S.y + sy) - Ai.y : T(0);
-            const T dz = DIM >= 3 ? (S.z + sz) - Ai.z : T(0);
-            const T r2 = P::r2_of(dx, dy, dz);
-            const T R = fmaf((T)a.kh_f, S.w, khdi);
-            const T diff = fmaf(-R, R, r2);
-            acc = diff < T(0);
-            if (fabsf(diff) <= band) {
-              ++te;
-              acc = exact_accept(a, DIM, a.perm[i], a.perm[j]);
-            }
-          } else {
-            T dx, dy, dz;
-            P::sep(true, Ai, S, T(0), T(0), T(0), dx, dy, dz);   // x_j - x_i, oracle order
-            const T r2 = P::r2_of(dx, dy, dz);
-            const double R = __dmul_rn(a.kh, __dadd_rn(Ai.w, S.w));
-            acc = r2 < __dmul_rn(R, R);
+            const float4 U = unit_shift[e & 31u];
+            sx = (T)U.x * dcs;
+            sy = (T)U.y * dcs;
+            sz = (T)U.z * dcs;
           }
+          acc = fw.pair_listed(a, i, Ai, Bi, Ci, ui, (int64_t)(e >> 5), sx, sy, sz, khdi, band, te);
         }
-        const unsigned mask = __ballot_sync(0xffffffffu, acc);
-        if (acc) q[qn + __popc(mask & lt)] = e;
-        __syncwarp();
-        qn += __popc(mask);
-        nacc += __popc(mask);
-        if (qn >= 32) drain(32);
+        nacc += __popc(__ballot_sync(0xffffffffu, acc));
       }
-      if (qn > 0) drain(qn);
       // combine the lanes' sums (fixed butterfly order); the rates are scaled below, per lane
       const T srho = warp_sum(fw.s_rho), sfx = warp_sum(fw.s_fx);
       const T sfy = DIM >= 2 ? warp_sum(fw.s_fy) : T(0), sfz = DIM >= 3 ? warp_sum(fw.s_fz) : T(0);
