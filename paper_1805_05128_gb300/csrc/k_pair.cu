@@ -697,18 +697,42 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
       s_bd.add(gW * Wh * eh);
     };
 
+    // List build: the warp writes each home particle's new entries together,
+    // 32 consecutive entries of one row per store (the self pair dropped by
+    // a ballot, list order kept), instead of one entry of 32 rows per store.
+    auto flush_lists = [&]() {
+      nfull += (unsigned)cnt;
+      for (int hp = 0; hp < nh; ++hp) {
+        const int n = __shfl_sync(0xffffffffu, cnt, hp);
+        int v0 = __shfl_sync(0xffffffffu, vc, hp);
+        const int64_t ih = h0 + hp;
+        for (int k0 = 0; k0 < n; k0 += 32) {
+          const int k = k0 + lane;
+          uint32_t word = 0;
+          bool w = false;
+          if (k < n) {
+            const unsigned ent = list[warp][hp][k];
+            const int64_t j = (int64_t)__float_as_int(nb_tab[warp][ent >> 11].x) + (ent & 2047u);
+            w = j != ih;
+            word = ((uint32_t)j << 5) | (ent >> 11);
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, w);
+          const int pos = v0 + __popc(m & lt);
+          if (w && pos < a.vcap) a.vlist[ih * a.vcap + pos] = word;
+          v0 += __popc(m);
+        }
+        if (lane == hp) vc = v0;
+      }
+      cnt = 0;
+    };
+
     auto flush = [&]() {
       nfull += (unsigned)cnt;
       for (int k = 0; k < cnt; ++k) {
         const unsigned ent = list[warp][lane][k];
         const float4 t = nb_tab[warp][ent >> 11];
         const int64_t j = (int64_t)__float_as_int(t.x) + (ent & 2047u);
-        if constexpr (LIST) {
-          if (j != i) {
-            if (vc < a.vcap) a.vlist[(int64_t)i * a.vcap + vc] = ((uint32_t)j << 5) | (ent >> 11);
-            ++vc;
-          }
-        } else if constexpr (VJP) {
+        if constexpr (VJP) {
           pair_vjp(j, (T)t.y, (T)t.z, (T)t.w);
         } else if constexpr (GRAD) {
           pair_grad(j, (T)t.y, (T)t.z, (T)t.w);
@@ -734,7 +758,8 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
         for (int base = r0; base < r1; base += 32) {
           // a chunk adds at most 32 entries to a list: flush first if one could overflow
           if (__any_sync(0xffffffffu, cnt > kListCap - 32)) {
-            if (act) flush();
+            if constexpr (LIST) flush_lists();
+            else if (act) flush();
           }
           const int j = base + lane;
           const bool jv = j < r1;
@@ -785,7 +810,8 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
         }
       }
     }
-    if (act) flush();
+    if constexpr (LIST) flush_lists();
+    else if (act) flush();
 
     if constexpr (GRAD) {
       if (act) {
@@ -843,32 +869,33 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
   }
 }
 
-// Pair evaluation over the Verlet lists: one warp per slot i, taken in
-// groups of 32 consecutive slots from a global counter.  The warp reads i's
-// list 32 entries at a time (particle-major, so the reads are contiguous);
+// Pair evaluation over the Verlet lists: one half warp per slot i (two slots
+// per warp, which halves the per-slot reductions and set-up), taken in
+// groups of 32 consecutive slots from a global counter.  The half warp reads
+// i's list 16 entries at a time (particle-major, so the reads are contiguous);
 // each lane decides its entry as k_pair does (FP32 test outside the band of
 // 2^-12 D^c^2, FP64 in the oracle's operation order inside it) and, if the
 // pair interacts, adds its flux to the lane's Kahan sums (FwdAcc).  Test and
 // flux share the loads and the separation; about 86 % of the entries of a
 // list built with beta = 0.15 interact, so the lanes whose entry does not
-// are cheaper than compacting the accepted ones first.  The lanes' sums are
-// combined by a fixed butterfly, and the FP64 scaling of the rates is done
+// are cheaper than compacting the accepted ones first.  The half warp's sums
+// are combined by a fixed butterfly, and the FP64 scaling of the rates is done
 // for the 32 slots of the group at once, one slot per lane.  Offsets stay
 // relative to the cells of the build and each pair's shift comes from its
 // neighbour-cell code, so the fluxes keep their bitwise antisymmetry; every
 // order is fixed, so results are reproducible bit for bit.
 
-// Sum over the warp's lanes of their Kahan sums (s - c), by a fixed butterfly.
+// Sum over a half warp's lanes of their Kahan sums (s - c), by a fixed butterfly.
 template <typename T>
-__device__ __forceinline__ T warp_sum(const Kahan<T>& k) {
+__device__ __forceinline__ T half_sum(const Kahan<T>& k) {
   T v = k.s - k.c;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
 template <bool MIXED, int DIM, bool HLL = false>
-__global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairArgs a) {
+__global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair_lists(PairArgs a) {
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
   using V4 = typename P::V4;
@@ -886,6 +913,8 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairAr
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int half = lane >> 4, hl = lane & 15;      // two slots per warp, one per half warp
+  const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
   const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
   for (;;) {
     int64_t g0 = 0;
@@ -896,45 +925,55 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairAr
     int unit_run = -1;
     unsigned unit_load = 0;
     unsigned tf = 0, tc = 0, te = 0;
-    // The list reads are software-pipelined: the next chunk of entries (and,
-    // across slots, the next slot's first chunk and count) is requested
-    // before the current one is tested, so the DRAM latency of the lists
-    // overlaps the L2 gathers and the arithmetic.  vcap >= 32, so the first
-    // chunk of any row is in bounds.
-    uint32_t e_pre = a.vlist[g0 * (int64_t)a.vcap + lane];
-    int cnt_pre = a.vcnt[g0];
-    for (int64_t i = g0; i < g1; ++i) {                 // warp-uniform
-      const int cnt = cnt_pre;
+    // Half h of the warp takes slots g0 + 2q + h, q = 0..15.  The list reads
+    // are software-pipelined: the next chunk of entries (and, across slots,
+    // the next slot's first chunk and count) is requested before the current
+    // one is evaluated, so the DRAM latency of the lists overlaps the L2
+    // gathers and the arithmetic.  vcap >= 32, so the first chunk of any row
+    // is in bounds.
+    uint32_t e_pre = 0u;
+    int cnt_pre = 0;
+    if (g0 + half < g1) {
+      e_pre = a.vlist[(g0 + half) * (int64_t)a.vcap + hl];
+      cnt_pre = a.vcnt[g0 + half];
+    }
+    for (int q = 0; g0 + 2 * q < g1; ++q) {            // warp-uniform
+      const int64_t i = g0 + 2 * q + half;            // this half's slot
+      const bool iv = i < g1;                         // half-uniform
+      const int cnt = iv ? cnt_pre : 0;
       uint32_t e_cur = e_pre;
-      if (i + 1 < g1) {
-        e_pre = a.vlist[(i + 1) * (int64_t)a.vcap + lane];
-        cnt_pre = a.vcnt[i + 1];
+      if (i + 2 < g1) {
+        e_pre = a.vlist[(i + 2) * (int64_t)a.vcap + hl];
+        cnt_pre = a.vcnt[i + 2];
       }
+      const int64_t ii = iv ? i : g0;                 // a valid slot for the loads
       int b = 0;
       if (a.n_inst > 1) {
         int lo = 0, hi = a.n_inst;
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
-          if (a.inst_off[mid] <= i) lo = mid; else hi = mid;
+          if (a.inst_off[mid] <= ii) lo = mid; else hi = mid;
         }
         b = lo;
       }
       const GridInfo& g = a.grid[b];
       const T dcs = MIXED ? (T)g.dc_f : T(0);
       const float band = MIXED ? 0x1p-12f * g.dc_f * g.dc_f : 0.f;
-      const V4 Ai = A[i];
-      const V4 Bi = reinterpret_cast<const V4*>(a.B)[i];
-      const V2 Ci = reinterpret_cast<const V2*>(a.C)[i];
+      const V4 Ai = A[ii];
+      const V4 Bi = reinterpret_cast<const V4*>(a.B)[ii];
+      const V2 Ci = reinterpret_cast<const V2*>(a.C)[ii];
       const T khdi = MIXED ? (T)a.kh_f * Ai.w : T(0);
-      const int ui = a.K > 0 ? a.slot_unit[i] : 0;
-      const uint32_t* __restrict__ row = a.vlist + i * (int64_t)a.vcap;
+      const int ui = a.K > 0 ? a.slot_unit[ii] : 0;
+      const uint32_t* __restrict__ row = a.vlist + ii * (int64_t)a.vcap;
       FwdAcc<MIXED, DIM, false, HLL> fw;
-      unsigned nacc = 0;   // accepted pairs of i (warp-uniform)
-      for (int base = 0; base < cnt; base += 32) {
-        const int k = base + lane;
+      unsigned nacc = 0;                              // accepted pairs of i (half-uniform)
+      const int other = __shfl_xor_sync(0xffffffffu, cnt, 16);
+      const int cmax = cnt > other ? cnt : other;     // chunks run by the whole warp
+      for (int base = 0; base < cmax; base += 16) {
+        const int k = base + hl;
         const bool kv = k < cnt;
         const uint32_t e = kv ? e_cur : 0u;
-        if (base + 32 < cnt) e_cur = (k + 32 < cnt) ? row[k + 32] : 0u;   // next chunk, requested now
+        if (base + 16 < cnt) e_cur = (k + 16 < cnt) ? row[k + 16] : 0u;   // next chunk, requested now
         bool acc = false;
         if (kv) {
           T sx = T(0), sy = T(0), sz = T(0);
@@ -944,40 +983,42 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairAr
             sy = (T)U.y * dcs;
             sz = (T)U.z * dcs;
           }
-          acc = fw.pair_listed(a, i, Ai, Bi, Ci, ui, (int64_t)(e >> 5), sx, sy, sz, khdi, band, te);
+          acc = fw.pair_listed(a, ii, Ai, Bi, Ci, ui, (int64_t)(e >> 5), sx, sy, sz, khdi, band, te);
         }
-        nacc += __popc(__ballot_sync(0xffffffffu, acc));
+        nacc += __popc(__ballot_sync(0xffffffffu, acc) & hmask);
       }
-      // combine the lanes' sums (fixed butterfly order); the rates are scaled below, per lane
-      const T srho = warp_sum(fw.s_rho), sfx = warp_sum(fw.s_fx);
-      const T sfy = DIM >= 2 ? warp_sum(fw.s_fy) : T(0), sfz = DIM >= 3 ? warp_sum(fw.s_fz) : T(0);
-      const T sq = warp_sum(fw.s_q);
+      // combine the half's sums (fixed butterfly order); the rates are scaled below, per lane
+      const T srho = half_sum(fw.s_rho), sfx = half_sum(fw.s_fx);
+      const T sfy = DIM >= 2 ? half_sum(fw.s_fy) : T(0), sfz = DIM >= 3 ? half_sum(fw.s_fz) : T(0);
+      const T sq = half_sum(fw.s_q);
       T dm = fw.dmax;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T other = __shfl_xor_sync(0xffffffffu, dm, o);
-        dm = other > dm ? other : dm;
+      for (int o = 8; o > 0; o >>= 1) {
+        const T ot = __shfl_xor_sync(0xffffffffu, dm, o);
+        dm = ot > dm ? ot : dm;
       }
-      if (lane == 0) {
-        const int r = (int)(i - g0);
-        const T vals[6] = {srho, sfx, sfy, sfz, sq, dm};
+      if (iv) {
+        if (hl == 0) {
+          const int r = (int)(i - g0);
+          const T vals[6] = {srho, sfx, sfy, sfz, sq, dm};
 #pragma unroll
-        for (int qv = 0; qv < 6; ++qv) {
-          if constexpr (MIXED) res[warp][qv][r] = (float)vals[qv];
-          else res64[warp][qv][r] = (double)vals[qv];
+          for (int qv = 0; qv < 6; ++qv) {
+            if constexpr (MIXED) res[warp][qv][r] = (float)vals[qv];
+            else res64[warp][qv][r] = (double)vals[qv];
+          }
+          res_n[warp][r] = nacc;
+          tf += nacc;
+          tc += (unsigned)cnt;
         }
-        res_n[warp][r] = nacc;
-      }
-      tf += nacc;
-      tc += (unsigned)cnt;
-      if (a.K > 0) {                                   // loads per unit, flushed when the unit changes
-        if (ui != unit_run && unit_run >= 0 && lane == 0 && unit_load)
-          atomicAdd(&a.load_acc[unit_run], (unsigned long long)unit_load);
-        if (ui != unit_run) { unit_run = ui; unit_load = 0; }
-        unit_load += nacc;
+        if (a.K > 0) {                                 // loads per unit, flushed when the unit changes
+          if (ui != unit_run && unit_run >= 0 && hl == 0 && unit_load)
+            atomicAdd(&a.load_acc[unit_run], (unsigned long long)unit_load);
+          if (ui != unit_run) { unit_run = ui; unit_load = 0; }
+          unit_load += nacc;
+        }
       }
     }
-    if (a.K > 0 && lane == 0 && unit_run >= 0 && unit_load)
+    if (a.K > 0 && hl == 0 && unit_run >= 0 && unit_load)
       atomicAdd(&a.load_acc[unit_run], (unsigned long long)unit_load);
     __syncwarp();
     {
@@ -999,6 +1040,8 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairAr
     }
     __syncwarp();
     te = __reduce_add_sync(0xffffffffu, te);
+    tf = __reduce_add_sync(0xffffffffu, tf);
+    tc = __reduce_add_sync(0xffffffffu, tc);
     if (lane == 0) {
       atomicAdd(&a.counters[0], (unsigned long long)tf);
       atomicAdd(&a.counters[1], (unsigned long long)tc);
