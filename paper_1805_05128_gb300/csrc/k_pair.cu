@@ -869,33 +869,40 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
   }
 }
 
-// Pair evaluation over the Verlet lists: one half warp per slot i (two slots
-// per warp, which halves the per-slot reductions and set-up), taken in
-// groups of 32 consecutive slots from a global counter.  The half warp reads
-// i's list 16 entries at a time (particle-major, so the reads are contiguous);
+// Pair evaluation over the Verlet lists: four lanes per slot i (eight slots
+// per warp: the per-slot reductions and set-up are shared by eight slots, and
+// a list of ~90 entries fills its lanes to the last chunk), taken in groups
+// of 32 consecutive slots from a global counter.  The slot's lanes read i's
+// list four entries at a time (particle-major, so the reads are contiguous);
 // each lane decides its entry as k_pair does (FP32 test outside the band of
 // 2^-12 D^c^2, FP64 in the oracle's operation order inside it) and, if the
 // pair interacts, adds its flux to the lane's Kahan sums (FwdAcc).  Test and
 // flux share the loads and the separation; about 86 % of the entries of a
 // list built with beta = 0.15 interact, so the lanes whose entry does not
-// are cheaper than compacting the accepted ones first.  The half warp's sums
-// are combined by a fixed butterfly, and the FP64 scaling of the rates is done
+// are cheaper than compacting the accepted ones first.  Each lane's Kahan
+// sum takes about a quarter of the slot's pairs; the slot's four sums are
+// combined by a fixed butterfly, and the FP64 scaling of the rates is done
 // for the 32 slots of the group at once, one slot per lane.  Offsets stay
 // relative to the cells of the build and each pair's shift comes from its
 // neighbour-cell code, so the fluxes keep their bitwise antisymmetry; every
 // order is fixed, so results are reproducible bit for bit.
 
-// Sum over a half warp's lanes of their Kahan sums (s - c), by a fixed butterfly.
+// Lanes per slot of k_pair_lists (a divisor of 32): measured on the 1.125M
+// plate impact, 16 / 8 / 4 / 2 lanes per slot take 0.89 / 0.81 / 0.75 / 0.76 ms.
+constexpr int kSlotLanes = 4;
+constexpr int kSlotsPerWarp = 32 / kSlotLanes;
+
+// Sum over a slot's lanes of their Kahan sums (s - c), by a fixed butterfly.
 template <typename T>
-__device__ __forceinline__ T half_sum(const Kahan<T>& k) {
+__device__ __forceinline__ T slot_sum(const Kahan<T>& k) {
   T v = k.s - k.c;
 #pragma unroll
-  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = kSlotLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
 template <bool MIXED, int DIM, bool HLL = false>
-__global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair_lists(PairArgs a) {
+__global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairArgs a) {
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
   using V4 = typename P::V4;
@@ -913,8 +920,8 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair_lists(PairAr
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int half = lane >> 4, hl = lane & 15;      // two slots per warp, one per half warp
-  const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
+  const int half = lane / kSlotLanes, hl = lane % kSlotLanes;   // the slot's group of lanes, lane in it
+  const unsigned hmask = (kSlotLanes == 32 ? 0xffffffffu : ((1u << kSlotLanes) - 1u)) << (half * kSlotLanes);
   const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
   for (;;) {
     int64_t g0 = 0;
@@ -937,14 +944,14 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair_lists(PairAr
       e_pre = a.vlist[(g0 + half) * (int64_t)a.vcap + hl];
       cnt_pre = a.vcnt[g0 + half];
     }
-    for (int q = 0; g0 + 2 * q < g1; ++q) {            // warp-uniform
-      const int64_t i = g0 + 2 * q + half;            // this half's slot
-      const bool iv = i < g1;                         // half-uniform
+    for (int q = 0; g0 + kSlotsPerWarp * q < g1; ++q) {   // warp-uniform
+      const int64_t i = g0 + kSlotsPerWarp * q + half;       // this group's slot
+      const bool iv = i < g1;                                // uniform in the group
       const int cnt = iv ? cnt_pre : 0;
       uint32_t e_cur = e_pre;
-      if (i + 2 < g1) {
-        e_pre = a.vlist[(i + 2) * (int64_t)a.vcap + hl];
-        cnt_pre = a.vcnt[i + 2];
+      if (i + kSlotsPerWarp < g1) {
+        e_pre = a.vlist[(i + kSlotsPerWarp) * (int64_t)a.vcap + hl];
+        cnt_pre = a.vcnt[i + kSlotsPerWarp];
       }
       const int64_t ii = iv ? i : g0;                 // a valid slot for the loads
       int b = 0;
@@ -967,13 +974,17 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair_lists(PairAr
       const uint32_t* __restrict__ row = a.vlist + ii * (int64_t)a.vcap;
       FwdAcc<MIXED, DIM, false, HLL> fw;
       unsigned nacc = 0;                              // accepted pairs of i (half-uniform)
-      const int other = __shfl_xor_sync(0xffffffffu, cnt, 16);
-      const int cmax = cnt > other ? cnt : other;     // chunks run by the whole warp
-      for (int base = 0; base < cmax; base += 16) {
+      int cmax = cnt;                                 // chunks run by the whole warp
+#pragma unroll
+      for (int o = kSlotLanes; o < 32; o <<= 1) {
+        const int other = __shfl_xor_sync(0xffffffffu, cmax, o);
+        cmax = cmax > other ? cmax : other;
+      }
+      for (int base = 0; base < cmax; base += kSlotLanes) {
         const int k = base + hl;
         const bool kv = k < cnt;
         const uint32_t e = kv ? e_cur : 0u;
-        if (base + 16 < cnt) e_cur = (k + 16 < cnt) ? row[k + 16] : 0u;   // next chunk, requested now
+        if (base + kSlotLanes < cnt) e_cur = (k + kSlotLanes < cnt) ? row[k + kSlotLanes] : 0u;   // next chunk, requested now
         bool acc = false;
         if (kv) {
           T sx = T(0), sy = T(0), sz = T(0);
@@ -988,12 +999,12 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 6 : 4) k_pair_lists(PairAr
         nacc += __popc(__ballot_sync(0xffffffffu, acc) & hmask);
       }
       // combine the half's sums (fixed butterfly order); the rates are scaled below, per lane
-      const T srho = half_sum(fw.s_rho), sfx = half_sum(fw.s_fx);
-      const T sfy = DIM >= 2 ? half_sum(fw.s_fy) : T(0), sfz = DIM >= 3 ? half_sum(fw.s_fz) : T(0);
-      const T sq = half_sum(fw.s_q);
+      const T srho = slot_sum(fw.s_rho), sfx = slot_sum(fw.s_fx);
+      const T sfy = DIM >= 2 ? slot_sum(fw.s_fy) : T(0), sfz = DIM >= 3 ? slot_sum(fw.s_fz) : T(0);
+      const T sq = slot_sum(fw.s_q);
       T dm = fw.dmax;
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1) {
+      for (int o = kSlotLanes / 2; o > 0; o >>= 1) {
         const T ot = __shfl_xor_sync(0xffffffffu, dm, o);
         dm = ot > dm ? ot : dm;
       }
