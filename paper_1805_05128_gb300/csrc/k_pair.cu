@@ -459,14 +459,12 @@ __device__ __forceinline__ void warp_counters(const PairArgs& a, bool act, unsig
 }
 
 // One warp per home cell, lane l owning home particle start_c + chunk + l.
-// Candidate test, transposed: for each neighbour row (the 3 x-consecutive
-// cells at (oy, oz), contiguous in slot order) the warp takes 32 candidates
-// at a time, one per lane (position relative to the home cell origin in
-// mixed mode, global in FP64), and loops over the home particles, whose data
-// is broadcast from shared memory.  Each lane tests its candidate against
-// home particle hp; a ballot collects the accepted lanes and each writes its
-// entry at the next free positions of hp's list (prefix popcount), so the
-// 32 lanes are busy in every test and consecutive tests are independent.
+// For each neighbour row (the 3 x-consecutive cells at (oy, oz), contiguous
+// in slot order) the warp stages 32 candidates at a time in shared memory,
+// one loaded per lane (position relative to the home cell origin in mixed
+// mode, global in FP64); every lane then tests its own home particle against
+// each staged candidate, a broadcast read, and appends the accepted ones to
+// its list in candidate order (no ballots or shuffles in the test loop).
 // A list entry is 16 bits: the neighbour-cell code (ox+1) + 3 (oy+1) +
 // 9 (oz+1) and the offset inside that cell.  Lists are rows of padded
 // stride in shared memory; after the scan (or when some list could overflow
@@ -487,6 +485,8 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
   using V2 = typename P::V2;
   __shared__ uint16_t list[kWarps][32][kRow];               // [warp][home particle][entry]
   __shared__ V4 home[kWarps][32];                            // home particles: x, y, z, kh d (mixed) or d (FP64)
+  __shared__ V4 cand[kWarps][32];                            // list build: candidates (shifted in mixed), d
+  __shared__ uint16_t cand_ent[kWarps][32];                  // list build: their list entries
   __shared__ int32_t nb_start[kWarps][27];                   // start slot of each neighbour cell
   __shared__ float4 nb_tab[kWarps][27];                      // per neighbour cell: start (bits), shift x, y, z
 
@@ -545,12 +545,12 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
     const int ii = act ? i : hs;
     const V4 Ai = A[ii];
     const T khdi = MIXED ? (T)a.kh_f * Ai.w : T(0);
-    {
+    if constexpr (!LIST) {
       V4 hv = Ai;
       if (MIXED) hv.w = khdi;
       home[warp][lane] = hv;
+      __syncwarp();
     }
-    __syncwarp();
     int cnt = 0, vc = 0;
     unsigned nfull = 0, ncand = 0, nexact = 0;
     const int ui = a.K > 0 ? a.slot_unit[ii] : 0;
@@ -772,39 +772,70 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
             if (off > 2047) set_status(a.status, SPH_ERR_CAPACITY);   // cell over 2047 particles
             ent = ((uint32_t)(rc + ox + 1) << 11) | (uint32_t)(off & 2047);
           }
+          if constexpr (LIST) {
+            cand[warp][lane] = S;
+            cand_ent[warp][lane] = (uint16_t)ent;
+            __syncwarp();
+            // each lane tests its home particle against the chunk's candidates,
+            // broadcast from shared memory, and appends the accepted ones to its
+            // own list in candidate order
+            const int nc = min(32, r1 - base);
 #pragma unroll 4
-          for (int hp = 0; hp < nh; ++hp) {
-            const V4 H = home[warp][hp];
-            bool acc;
-            if (MIXED) {
-              const T dx = S.x - H.x;
-              const T dy = DIM >= 2 ? S.y - H.y : T(0);
-              const T dz = DIM >= 3 ? S.z - H.z : T(0);
-              const T r2 = P::r2_of(dx, dy, dz);
-              const T R = fmaf((T)a.kh_f, S.w, H.w);
-              const T diff = fmaf(-R, R, r2);          // r^2 - R^2
-              if constexpr (LIST) {
-                acc = diff < band;                      // superset of the (1 + beta) radius
+            for (int c = 0; c < nc; ++c) {
+              const V4 Sc = cand[warp][c];
+              bool acc;
+              if (MIXED) {
+                const T dx = Sc.x - Ai.x;
+                const T dy = DIM >= 2 ? Sc.y - Ai.y : T(0);
+                const T dz = DIM >= 3 ? Sc.z - Ai.z : T(0);
+                const T r2 = P::r2_of(dx, dy, dz);
+                const T R = fmaf((T)a.kh_f, Sc.w, khdi);
+                const T diff = fmaf(-R, R, r2);          // r^2 - R^2
+                acc = diff < band;                        // superset of the (1 + beta) radius
               } else {
+                T dx, dy, dz;
+                P::sep(true, Ai, Sc, T(0), T(0), T(0), dx, dy, dz);   // x_j - x_i, oracle order
+                const T r2 = P::r2_of(dx, dy, dz);
+                const double R = __dmul_rn(a.kh, __dadd_rn(Ai.w, Sc.w));
+                acc = r2 < __dmul_rn(R, R);
+              }
+              if (acc && act) list[warp][lane][cnt++] = cand_ent[warp][c];
+            }
+            __syncwarp();   // the candidate buffer is rewritten by the next chunk
+          } else {
+            // transposed test: each lane tests its candidate against home particle
+            // hp, broadcast from shared memory; a ballot collects the accepted lanes
+            // and each writes its entry at the next free position of hp's list
+#pragma unroll 4
+            for (int hp = 0; hp < nh; ++hp) {
+              const V4 H = home[warp][hp];
+              bool acc;
+              if (MIXED) {
+                const T dx = S.x - H.x;
+                const T dy = DIM >= 2 ? S.y - H.y : T(0);
+                const T dz = DIM >= 3 ? S.z - H.z : T(0);
+                const T r2 = P::r2_of(dx, dy, dz);
+                const T R = fmaf((T)a.kh_f, S.w, H.w);
+                const T diff = fmaf(-R, R, r2);          // r^2 - R^2
                 acc = diff < T(0);
-                if (fabsf(diff) <= band && jv) {        // too close to call in FP32: FP64 decides
+                if (fabsf(diff) <= band && jv) {          // too close to call in FP32: FP64 decides
                   ++nexact;
                   acc = (j == h0 + hp) || exact_accept(a, DIM, a.perm[h0 + hp], a.perm[j]);
                 }
+              } else {
+                T dx, dy, dz;
+                P::sep(true, H, S, T(0), T(0), T(0), dx, dy, dz);   // x_j - x_i, oracle order
+                const T r2 = P::r2_of(dx, dy, dz);
+                const double R = __dmul_rn(a.kh, __dadd_rn(H.w, S.w));
+                acc = r2 < __dmul_rn(R, R);
               }
-            } else {
-              T dx, dy, dz;
-              P::sep(true, H, S, T(0), T(0), T(0), dx, dy, dz);   // x_j - x_i, oracle order
-              const T r2 = P::r2_of(dx, dy, dz);
-              const double R = __dmul_rn(a.kh, __dadd_rn(H.w, S.w));
-              acc = r2 < __dmul_rn(R, R);
-            }
-            acc = acc && jv;
-            const unsigned mask = __ballot_sync(0xffffffffu, acc);
-            if (mask) {
-              const int c = __shfl_sync(0xffffffffu, cnt, hp);
-              if (acc) list[warp][hp][c + __popc(mask & lt)] = (uint16_t)ent;
-              if (lane == hp) cnt += __popc(mask);
+              acc = acc && jv;
+              const unsigned mask = __ballot_sync(0xffffffffu, acc);
+              if (mask) {
+                const int c = __shfl_sync(0xffffffffu, cnt, hp);
+                if (acc) list[warp][hp][c + __popc(mask & lt)] = (uint16_t)ent;
+                if (lane == hp) cnt += __popc(mask);
+              }
             }
           }
         }
