@@ -248,6 +248,28 @@ __global__ void k_derive(DevParams P, sph_state s, const int64_t* __restrict__ b
   if (threadIdx.x == 0) write_part(part, r);
 }
 
+// One block per instance: the step's dt = cfl * (minimum of the instance's
+// block minima).  Only the dtmin fields are read, four independent loads in
+// flight per thread.
+__global__ void k_reduce_dt(const int32_t* __restrict__ inst_blk, const BlockPart* __restrict__ part, double cfl,
+                            double* dt) {
+  const int b = blockIdx.x;
+  const int k0 = inst_blk[b], k1 = inst_blk[b + 1];
+  long long m = LLONG_MAX;
+  for (int k = k0 + threadIdx.x; k < k1; k += 4 * blockDim.x) {
+    long long q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int kk = k + u * blockDim.x;
+      q[u] = kk < k1 ? part[kk].dtmin : LLONG_MAX;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) m = q[u] < m ? q[u] : m;
+  }
+  m = block_min_key(m);
+  if (threadIdx.x == 0) dt[b] = cfl * dunkey(m);
+}
+
 // One block per instance: reduce the block partials of the instance.
 // mode 1: dt = cfl * min; mode 2: bounding box and sizes into the grid record.
 __global__ void k_reduce_inst(const int32_t* __restrict__ inst_blk, const BlockPart* __restrict__ part,
@@ -327,24 +349,27 @@ __device__ __forceinline__ int64_t local_cell(const GridInfo& g, int dim, double
 }
 
 __global__ void k_cell_count(int dim, sph_state s, const int64_t* __restrict__ blk_start,
-                             const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst,
+                             const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst, int nblk,
                              const GridInfo* __restrict__ grid, int32_t* cell_count, int32_t* cell_of,
                              int32_t* rank, int* status, const int* __restrict__ gate) {
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
-  int64_t p = blk_start[blockIdx.x] + threadIdx.x;
-  if (p >= blk_end[blockIdx.x]) return;
-  const GridInfo& g = grid[blk_inst[blockIdx.x]];
-  int32_t c[3];
-  int64_t lc = local_cell(g, dim, s.x[p], dim >= 2 ? s.y[p] : 0.0, dim >= 3 ? s.z[p] : 0.0, c);
-  bool ok = true;
-  for (int a = 0; a < 3; ++a) ok = ok && c[a] >= 0 && c[a] < g.dims[a];
-  if (!ok) {  // only a non-finite position can leave the mesh: latch it, stay in bounds
-    set_status(status, SPH_ERR_NONFINITE);
-    lc = 0;
+  // a capped grid strides over the segmented blocks (cheap to launch when gated)
+  for (int lb = blockIdx.x; lb < nblk; lb += gridDim.x) {
+    const int64_t p = blk_start[lb] + threadIdx.x;
+    if (p >= blk_end[lb]) continue;
+    const GridInfo& g = grid[blk_inst[lb]];
+    int32_t c[3];
+    int64_t lc = local_cell(g, dim, s.x[p], dim >= 2 ? s.y[p] : 0.0, dim >= 3 ? s.z[p] : 0.0, c);
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) ok = ok && c[a] >= 0 && c[a] < g.dims[a];
+    if (!ok) {  // only a non-finite position can leave the mesh: latch it, stay in bounds
+      set_status(status, SPH_ERR_NONFINITE);
+      lc = 0;
+    }
+    const int32_t gc = (int32_t)(g.cell_off + lc);
+    cell_of[p] = gc;
+    rank[p] = atomicAdd(&cell_count[gc], 1);
   }
-  int32_t gc = (int32_t)(g.cell_off + lc);
-  cell_of[p] = gc;
-  rank[p] = atomicAdd(&cell_count[gc], 1);
 }
 
 // Exclusive scan of cell_count[0, total) into cell_start, 1024 cells per tile.
@@ -442,9 +467,8 @@ __global__ void k_scan_down(int32_t* cnt, const int64_t* __restrict__ total, con
 __global__ void k_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of, const int32_t* __restrict__ rank,
                                const int32_t* __restrict__ start, int32_t* perm, const int* __restrict__ gate) {
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  perm[start[cell_of[p]] + rank[p]] = (int32_t)p;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    perm[start[cell_of[p]] + rank[p]] = (int32_t)p;
 }
 
 // Within each cell, order the particles by index (the atomic arrival order is
@@ -766,7 +790,7 @@ cudaError_t launch_derive_dt(sph_handle* h, const sph_state& s, bool with_bbox, 
 }
 
 cudaError_t launch_reduce_dt(sph_handle* h, cudaStream_t st) {
-  k_reduce_inst<<<h->n_inst, kBlock, 0, st>>>(h->inst_blk, h->part, h->dp.cfl, h->dt, h->grid, 1, nullptr);
+  k_reduce_dt<<<h->n_inst, kBlock, 0, st>>>(h->inst_blk, h->part, h->dp.cfl, h->dt);
   h->launches += 1;
   return cudaGetLastError();
 }
@@ -788,14 +812,15 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
   k_reduce_inst<<<h->n_inst, kBlock, 0, st>>>(h->inst_blk, h->part, h->dp.cfl, h->dt, h->grid, 2, gate);
   k_grid_setup<<<1, 32, 0, st>>>(h->dp, h->n_inst, h->inst_off, h->inst_cap, h->grid, h->total_cells,
                                  h->status, gate);
-  k_cell_count<<<h->nblk, kBlock, 0, st>>>(h->dp.dim, s, h->blk_start, h->blk_end, h->blk_inst, h->grid,
+  k_cell_count<<<capped_grid(h->nblk), kBlock, 0, st>>>(h->dp.dim, s, h->blk_start, h->blk_end, h->blk_inst,
+                                                        h->nblk, h->grid,
                                            h->cell_count, h->cell_of, h->rank, h->status, gate);
   int tiles = capped_grid(grid_for(h->cell_cap, kScanTile));
   k_scan_reduce<<<tiles, kBlock, 0, st>>>(h->cell_count, h->total_cells, h->scan_sums, gate);
   k_scan_sums<<<1, 1024, 0, st>>>(h->scan_sums, h->total_cells, gate);
   k_scan_down<<<tiles, kBlock, 0, st>>>(h->cell_count, h->total_cells, h->scan_sums, h->cell_start, h->n, gate);
-  k_cell_scatter<<<grid_for(h->n, kBlock), kBlock, 0, st>>>(h->n, h->cell_of, h->rank, h->cell_start, h->perm,
-                                                            gate);
+  k_cell_scatter<<<capped_grid(grid_for(h->n, kBlock)), kBlock, 0, st>>>(h->n, h->cell_of, h->rank,
+                                                                         h->cell_start, h->perm, gate);
   k_cell_sort<<<capped_grid(grid_for(h->cell_cap, kBlock)), kBlock, 0, st>>>(h->total_cells, h->cell_start,
                                                                              h->perm, gate);
   h->launches += 8;
@@ -809,7 +834,16 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
 __global__ void k_verlet_flag(const BlockPart* __restrict__ part, int nblk, int* vflag) {
   __shared__ long long sh[1024];
   long long m = LLONG_MIN;
-  for (int k = threadIdx.x; k < nblk; k += blockDim.x) m = part[k].viol > m ? part[k].viol : m;
+  for (int k = threadIdx.x; k < nblk; k += 4 * blockDim.x) {   // four independent loads in flight
+    long long q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int kk = k + u * (int)blockDim.x;
+      q[u] = kk < nblk ? part[kk].viol : LLONG_MIN;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) m = q[u] > m ? q[u] : m;
+  }
   sh[threadIdx.x] = m;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
