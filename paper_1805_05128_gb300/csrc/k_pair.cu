@@ -82,8 +82,9 @@ struct PairArgs {
   // mixed precision: the packed volume is V' = V vscale and W' is used as
   // W'' = W' wscale (both powers of two chosen by sph_init), so that the FP32
   // products stay in the normal range at any length scale; fscale =
-  // 1 / (vscale^2 wscale) and rscale = 1 / (vscale wscale) undo them in FP64,
-  // vinv = 1 / vscale.  All 1 in FP64 mode.
+  // 2 / (vscale^2 wscale) undoes them in FP64 and applies the factor 2 of the
+  // momentum and energy fluxes, rscale = 1 / (vscale wscale),
+  // vinv = 1 / vscale.  In FP64 mode the scales are 1 (fscale 2).
   float wscale_f;
   double fscale, rscale, vinv;
 };
@@ -160,17 +161,19 @@ __device__ __forceinline__ bool exact_accept(const PairArgs& a, int dim, int64_t
 }
 
 // dW/dr of the cubic spline (support 2h) or Wendland C2 (support kappa h)
-// with the reciprocals above.
+// with the reciprocals above, times ws, a power of two folded into the
+// normalisation constant (so the result is exactly ws times the unscaled
+// value: the mixed path's W'' = W' wscale at no extra multiply).
 template <typename T, int DIM>
-__device__ __forceinline__ T dw_fast(int kernel, T kappa, T r, T h) {
+__device__ __forceinline__ T dw_fast(int kernel, T kappa, T r, T h, T ws) {
   const T pi = T(3.14159265358979323846);
   if (kernel == SPH_KERNEL_CUBIC) {
     const T ih = rcp_(h);
     const T q = r * ih;
     T norm;
-    if (DIM == 1) norm = T(2.0 / 3.0) * ih * ih;
-    else if (DIM == 2) norm = T(10.0 / (7.0 * 3.14159265358979323846)) * ih * ih * ih;
-    else norm = T(1.0 / 3.14159265358979323846) * (ih * ih) * (ih * ih);
+    if (DIM == 1) norm = (T(2.0 / 3.0) * ws) * ih * ih;
+    else if (DIM == 2) norm = (T(10.0 / (7.0 * 3.14159265358979323846)) * ws) * ih * ih * ih;
+    else norm = (T(1.0 / 3.14159265358979323846) * ws) * (ih * ih) * (ih * ih);
     const T t = T(2) - q;
     const T f_in = q * (T(2.25) * q - T(3));
     const T f_out = T(-0.75) * t * t;
@@ -181,8 +184,8 @@ __device__ __forceinline__ T dw_fast(int kernel, T kappa, T r, T h) {
     const T s = r * iH;
     if (s >= T(1)) return T(0);
     const T t = T(1) - s;
-    if (DIM == 1) return T(1.25) * iH * iH * (T(-12) * s * t * t);
-    const T norm = (DIM == 2) ? T(7) / pi * iH * iH * iH : T(21) / (T(2) * pi) * (iH * iH) * (iH * iH);
+    if (DIM == 1) return (T(1.25) * ws) * iH * iH * (T(-12) * s * t * t);
+    const T norm = (DIM == 2) ? (T(7) / pi * ws) * iH * iH * iH : (T(21) / (T(2) * pi) * ws) * (iH * iH) * (iH * iH);
     return norm * (T(-20) * s * t * t * t);
   }
 }
@@ -404,9 +407,10 @@ struct FwdAcc {
       vs = mul_(T(0.5), add_(wi, wj));
     }
     const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * add_(Ai.w, Aj.w);
-    const T dW = MIXED ? mul_(dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij), (T)a.wscale_f)
+    const T dW = MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij, (T)a.wscale_f)
                        : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij);
-    const T F = mul_(mul_(mul_(T(2), mul_(Bi.w, Bj.w)), Ps), dW);   // momentum flux along e (scaled)
+    // momentum flux along e, without its factor 2 (carried by fscale; exact)
+    const T F = mul_(mul_(mul_(Bi.w, Bj.w), Ps), dW);
     s_rho.add(Bj.w * (vi - vs) * (-dW));
     s_fx.add(mul_(F, ex));
     if (DIM >= 2) s_fy.add(mul_(F, ey));
@@ -602,7 +606,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
       const T r = r2 * ir;
       const T e[3] = {dx * ir, dy * ir, dz * ir};
       const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * (Ai.w + Aj.w);
-      const T w = -(MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij) * (T)a.wscale_f
+      const T w = -(MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij, (T)a.wscale_f)
                           : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij));
       const T f = Bj.w * w;
       const T dP = Cj.x - Ci.x;
@@ -1230,7 +1234,7 @@ PairArgs make_args(sph_handle* h, const sph_state& s) {
   a.gP = h->grad_p;
   a.gV = h->grad_v;
   a.wscale_f = (float)h->wscale;
-  a.fscale = 1.0 / (h->vscale * h->vscale * h->wscale);
+  a.fscale = 2.0 / (h->vscale * h->vscale * h->wscale);   // with the factor 2 of the momentum flux
   a.rscale = 1.0 / (h->vscale * h->wscale);
   a.vinv = 1.0 / h->vscale;
   return a;
