@@ -479,11 +479,20 @@ __device__ __forceinline__ void warp_counters(const PairArgs& a, bool act, unsig
 // stride in shared memory; after the scan (or when some list could overflow
 // during the next chunk) each lane evaluates the fluxes of its own row.
 constexpr int kWarps = kPairBlock / 32;
-constexpr int kRow = kListCap + 2;   // padded row stride (16-bit entries): lane rows fall in distinct banks
+// List staging per home particle in shared memory: kListCap entries for the
+// flux modes, kBuildCap for the list build (whose rows are flushed to the
+// global lists, so a shorter row only means more frequent flushes and frees
+// shared memory for more resident blocks).  Row stride: cap + 2 16-bit
+// entries, an odd number of words, so lane rows fall in distinct banks.
+// Measured on the 1.125M plate: rows of 64 or 96 entries with 7-8 resident
+// blocks made the step 0.3-3 % slower than 128 entries with 6 blocks.
+constexpr int kBuildCap = 128;
+constexpr int kBuildBlocks = 6;      // resident blocks per SM of the mixed list build
 
 template <bool MIXED, int DIM, int MODE, bool HLL = false>
 __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kModeFwd2) ? (MIXED ? 4 : 2)
-                                                 : (MODE == kModeGrad ? (MIXED ? 5 : 3) : (MIXED ? 6 : 4)))
+                                                 : (MODE == kModeGrad ? (MIXED ? 5 : 3)
+                                                 : (MODE == kModeList ? (MIXED ? kBuildBlocks : 4) : (MIXED ? 6 : 4))))
     k_pair(PairArgs a) {
   constexpr bool VJP = MODE == kModeVjp;
   constexpr bool LIST = MODE == kModeList;
@@ -492,8 +501,9 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
   using T = typename P::T;
   using V4 = typename P::V4;
   using V2 = typename P::V2;
-  __shared__ uint16_t list[kWarps][32][kRow];               // [warp][home particle][entry]
-  __shared__ V4 home[kWarps][32];                            // home particles: x, y, z, kh d (mixed) or d (FP64)
+  constexpr int kCap = MODE == kModeList ? kBuildCap : kListCap;
+  __shared__ uint16_t list[kWarps][32][kCap + 2];           // [warp][home particle][entry]
+  __shared__ V4 home[kWarps][LIST ? 1 : 32];                 // home particles: x, y, z, kh d (mixed) or d (FP64)
   __shared__ V4 cand[kWarps][32];                            // list build: candidates (shifted in mixed), d
   __shared__ uint16_t cand_ent[kWarps][32];                  // list build: their list entries
   __shared__ int32_t nb_start[kWarps][27];                   // start slot of each neighbour cell
@@ -766,7 +776,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
         ncand += act ? (unsigned)(r1 - r0) : 0u;
         for (int base = r0; base < r1; base += 32) {
           // a chunk adds at most 32 entries to a list: flush first if one could overflow
-          if (__any_sync(0xffffffffu, cnt > kListCap - 32)) {
+          if (__any_sync(0xffffffffu, cnt > kCap - 32)) {
             if constexpr (LIST) flush_lists();
             else if (act) flush();
           }
