@@ -270,7 +270,9 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     CKI(cudaMemset(h->unit_work, 0, sizeof(int32_t) * (2 * h->unit_work_total + h->unit_work_total / 1024 + 4)));
     CKI(dalloc(&h->unit_total, 1));
     CKI(cudaMemcpy(h->unit_total, &h->unit_work_total, sizeof(int64_t), cudaMemcpyHostToDevice));
-    CKI(dalloc(&h->unit_stats, (size_t)K * 9));   // 5 statistics + 4 balancing scratch per unit
+    // 5 statistics + 4 balancing scratch per unit, then the statistics' partial sums
+    // (up to 16 blocks per unit, 4 values each)
+    CKI(dalloc(&h->unit_stats, (size_t)K * (9 + 16 * 4)));
   }
 
   // order-2 reconstruction: SPH gradients of P and v in slot order

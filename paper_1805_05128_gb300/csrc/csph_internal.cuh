@@ -118,7 +118,8 @@ struct sph_handle {
   int32_t* unit_work = nullptr;            // partition scratch: counts, starts, scan sums
   int64_t* unit_total = nullptr;           // device scalar K * nb
   int64_t unit_work_total = 0;             // K * nb on the host
-  double* unit_stats = nullptr;            // [K x 5] centroid, count, max R^hrz; then [K x 4] balance scratch
+  double* unit_stats = nullptr;            // [K x 5] centroid, count, max R^hrz; [K x 4] balance scratch;
+                                            // [K x 16 x 4] partial sums of the statistics
 
   // optional pair output of the pair kernel (sph_pair_list)
   bool collect_adj = true;                  // record unit adjacency in the next pair evaluation

@@ -22,84 +22,121 @@ constexpr int kUnitBlock = 1024;   // particles per block of the unit partition 
 // re-evaluated in FP64 with the oracle's operation order (dx = x - g,
 // squares summed in axis order), the smallest with strict < winning.
 // ---------------------------------------------------------------------------
-__global__ void k_assign(int64_t n, int dim, const double* __restrict__ x, const double* __restrict__ y,
+// The block's prologue (the generators' mean o, per axis in index order; their
+// FP32 offsets and the largest of them) is shared out over the threads, and a
+// capped grid strides over the particles, so that it runs once per resident
+// block: done serially by one thread in every block of a one-particle-per-
+// thread grid, its FP64 chain dominated the kernel.
+template <int DIM>
+__global__ void k_assign(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
                          const double* __restrict__ z, const double* __restrict__ gen, int K,
                          int32_t* unit, unsigned long long* n_exact) {
   __shared__ double gd[SPH_MAX_UNITS * 3];
   __shared__ float gf[SPH_MAX_UNITS * 3];
   __shared__ double org[3];
-  __shared__ float gmax;
-  for (int k = threadIdx.x; k < K * dim; k += blockDim.x) gd[k] = gen[k];
+  __shared__ float gred[kBlock / 32];
+  for (int k = threadIdx.x; k < K * DIM; k += blockDim.x) gd[k] = gen[k];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int a = 0; a < dim; ++a) {
-      double s = 0.0;
-      for (int k = 0; k < K; ++k) s += gd[k * dim + a];
-      org[a] = s / K;
-    }
-    float gm = 0.f;
-    for (int k = 0; k < K; ++k)
-      for (int a = 0; a < dim; ++a) {
-        float v = (float)(gd[k * dim + a] - org[a]);
-        gf[k * dim + a] = v;
-        gm = fmaxf(gm, fabsf(v));
-      }
-    gmax = gm;
+  if (threadIdx.x < DIM) {
+    const int a = threadIdx.x;
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) s += gd[k * DIM + a];
+    org[a] = s / K;
   }
   __syncthreads();
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
+  float gm = 0.f;
+  for (int k = threadIdx.x; k < K * DIM; k += blockDim.x) {
+    const float v = (float)(gd[k] - org[k % DIM]);
+    gf[k] = v;
+    gm = fmaxf(gm, fabsf(v));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+  if ((threadIdx.x & 31) == 0) gred[threadIdx.x >> 5] = gm;
+  __syncthreads();
+  float gmax = 0.f;
+  for (int w = 0; w < kBlock / 32; ++w) gmax = fmaxf(gmax, gred[w]);
   const double* X[3] = {x, y, z};
-  float xf[3] = {0.f, 0.f, 0.f};
-  float M = gmax;
-  for (int a = 0; a < dim; ++a) {
-    xf[a] = (float)(X[a][p] - org[a]);
-    M = fmaxf(M, fabsf(xf[a]));
-  }
-  // inflate M by a relative 2^-20 for the rounding of M itself
-  M = M * (1.0f + 0x1p-20f);
-  const float B = (float)dim * M * M * 0x1p-19f;
-  float best = FLT_MAX;
-  for (int k = 0; k < K; ++k) {
-    float d2 = 0.f;
-    for (int a = 0; a < dim; ++a) {
-      float t = xf[a] - gf[k * dim + a];
-      d2 = fmaf(t, t, d2);
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    float xf[3] = {0.f, 0.f, 0.f};
+    float M = gmax;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      xf[a] = (float)(X[a][p] - org[a]);
+      M = fmaxf(M, fabsf(xf[a]));
     }
-    best = fminf(best, d2);
-  }
-  const float lim = best + 3.0f * B;
-  int first = -1, ncand = 0;
-  for (int k = 0; k < K; ++k) {
-    float d2 = 0.f;
-    for (int a = 0; a < dim; ++a) {
-      float t = xf[a] - gf[k * dim + a];
-      d2 = fmaf(t, t, d2);
-    }
-    if (d2 <= lim) {
-      if (first < 0) first = k;
-      ++ncand;
-    }
-  }
-  int win = first;
-  if (ncand > 1) {
-    atomicAdd(n_exact, 1ull);
-    double bd = DBL_MAX;
-    for (int k = first; k < K; ++k) {
-      float d2f = 0.f;
-      for (int a = 0; a < dim; ++a) {
-        float t = xf[a] - gf[k * dim + a];
-        d2f = fmaf(t, t, d2f);
+    // inflate M by a relative 2^-20 for the rounding of M itself
+    M = M * (1.0f + 0x1p-20f);
+    const float B = (float)DIM * M * M * 0x1p-19f;
+    float best = FLT_MAX;
+    for (int k = 0; k < K; ++k) {
+      float d2 = 0.f;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        float t = xf[a] - gf[k * DIM + a];
+        d2 = fmaf(t, t, d2);
       }
-      if (d2f > lim) continue;
-      double dx = __dsub_rn(X[0][p], gd[k * dim + 0]);
-      double d2 = __dmul_rn(dx, dx);
-      if (dim >= 2) { double dy = __dsub_rn(X[1][p], gd[k * dim + 1]); d2 = __dadd_rn(d2, __dmul_rn(dy, dy)); }
-      if (dim >= 3) { double dz = __dsub_rn(X[2][p], gd[k * dim + 2]); d2 = __dadd_rn(d2, __dmul_rn(dz, dz)); }
-      if (d2 < bd) { bd = d2; win = k; }
+      best = fminf(best, d2);
     }
+    const float lim = best + 3.0f * B;
+    int first = -1, ncand = 0;
+    for (int k = 0; k < K; ++k) {
+      float d2 = 0.f;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        float t = xf[a] - gf[k * DIM + a];
+        d2 = fmaf(t, t, d2);
+      }
+      if (d2 <= lim) {
+        if (first < 0) first = k;
+        ++ncand;
+      }
+    }
+    int win = first;
+    if (ncand > 1) {
+      atomicAdd(n_exact, 1ull);
+      double bd = DBL_MAX;
+      for (int k = first; k < K; ++k) {
+        float d2f = 0.f;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          float t = xf[a] - gf[k * DIM + a];
+          d2f = fmaf(t, t, d2f);
+        }
+        if (d2f > lim) continue;
+        double dx = __dsub_rn(X[0][p], gd[k * DIM + 0]);
+        double d2 = __dmul_rn(dx, dx);
+        if (DIM >= 2) { double dy = __dsub_rn(X[1][p], gd[k * DIM + 1]); d2 = __dadd_rn(d2, __dmul_rn(dy, dy)); }
+        if (DIM >= 3) { double dz = __dsub_rn(X[2][p], gd[k * DIM + 2]); d2 = __dadd_rn(d2, __dmul_rn(dz, dz)); }
+        if (d2 < bd) { bd = d2; win = k; }
+      }
+    }
+    unit[p] = win < 0 ? 0 : win;   // no candidate only for non-finite input (latched elsewhere)
   }
-  unit[p] = win < 0 ? 0 : win;   // no candidate only for non-finite input (latched elsewhere)
+}
+
+// Grid of the assignment: particles in blocks of kBlock, at most 8 resident
+// blocks' worth per SM (the blocks stride over the rest).
+int assign_grid(int64_t n) {
+  static int cap = 0;
+  if (cap == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cap = 8 * (sms > 0 ? sms : 1);
+  }
+  const int64_t want = (n + kBlock - 1) / kBlock;
+  return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+cudaError_t launch_assign_kernel(int64_t n, int dim, const double* x, const double* y, const double* z,
+                                 const double* gen, int K, int32_t* unit, unsigned long long* n_exact,
+                                 cudaStream_t st) {
+  const int g = assign_grid(n);
+  if (dim == 1) k_assign<1><<<g, kBlock, 0, st>>>(n, x, y, z, gen, K, unit, n_exact);
+  else if (dim == 2) k_assign<2><<<g, kBlock, 0, st>>>(n, x, y, z, gen, K, unit, n_exact);
+  else k_assign<3><<<g, kBlock, 0, st>>>(n, x, y, z, gen, K, unit, n_exact);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -168,17 +205,23 @@ __global__ void k_unit_offsets(const int32_t* __restrict__ start, int K, int nb,
 // centroid (eq. VoronoiGeomCenters over the current positions), count, and
 // max_{i in k} R^hrz_i with R^hrz_i = (1 + beta)(kh (d_i + max_j d_j)).
 // ---------------------------------------------------------------------------
+// S blocks per unit (blockIdx.x = k S + s) each sum a strided share of the
+// unit's particles into part[(k S + s) x 4] (position sums, max R^hrz); a
+// second kernel adds the S partials of each unit in order.  One block per
+// unit left most SMs idle (64 units) on a kernel bound by FP64 adds.
+constexpr int kUnitSplit = 16;
+
 __global__ void k_unit_stats(const int32_t* __restrict__ unit_off, const int32_t* __restrict__ list,
                              const double* __restrict__ x, const double* __restrict__ y,
                              const double* __restrict__ z, const double* __restrict__ d,
-                             const double* __restrict__ dmax_nbr, int gdim, double kh, double beta,
-                             double* out /* K x 5: cx, cy, cz, count, rmax */) {
-  int k = blockIdx.x;
+                             const double* __restrict__ dmax_nbr, int gdim, double kh, double beta, int S,
+                             double* part) {
+  const int k = blockIdx.x / S, sp = blockIdx.x % S;
   int b = unit_off[k], e = unit_off[k + 1];
   double acc[3] = {0, 0, 0};
   double rmax = 0.0;
   const double* X[3] = {x, y, z};
-  for (int q = b + threadIdx.x; q < e; q += blockDim.x) {
+  for (int q = b + sp * (int)blockDim.x + threadIdx.x; q < e; q += S * (int)blockDim.x) {
     int64_t p = list[q];
     for (int a = 0; a < gdim; ++a) acc[a] += X[a][p];
     double dm = dmax_nbr[p] < 0.0 ? d[p] : dmax_nbr[p];
@@ -197,11 +240,26 @@ __global__ void k_unit_stats(const int32_t* __restrict__ unit_off, const int32_t
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    int cnt = e - b;
-    for (int a = 0; a < 3; ++a) out[k * 5 + a] = cnt > 0 ? sh[a][0] / (double)cnt : 0.0;
-    out[k * 5 + 3] = (double)cnt;
-    out[k * 5 + 4] = sh[3][0];
+    double* o = part + (size_t)blockIdx.x * 4;
+    for (int a = 0; a < 4; ++a) o[a] = sh[a][0];
   }
+}
+
+// Per unit: the S partials in order -> out[k x 5] = centroid (3), count, max R^hrz.
+__global__ void k_unit_stats_final(const int32_t* __restrict__ unit_off, int K, int S,
+                                   const double* __restrict__ part, double* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double acc[3] = {0, 0, 0}, rmax = 0.0;
+  for (int sp = 0; sp < S; ++sp) {
+    const double* q = part + ((size_t)k * S + sp) * 4;
+    for (int a = 0; a < 3; ++a) acc[a] += q[a];
+    rmax = fmax(rmax, q[3]);
+  }
+  const int cnt = unit_off[k + 1] - unit_off[k];
+  for (int a = 0; a < 3; ++a) out[k * 5 + a] = cnt > 0 ? acc[a] / (double)cnt : 0.0;
+  out[k * 5 + 3] = (double)cnt;
+  out[k * 5 + 4] = rmax;
 }
 
 __device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
@@ -424,10 +482,8 @@ __global__ void k_balance_apply(int K, int gdim, double* gen, const double* __re
 
 cudaError_t launch_assign(sph_handle* h, const sph_state& s, const double* gen, int K, int dim,
                           int32_t* unit_out, cudaStream_t st) {
-  k_assign<<<grid_for(h->n, kBlock), kBlock, 0, st>>>(h->n, dim, s.x, s.y, s.z, gen, K, unit_out,
-                                                      &h->counters[3]);
   h->launches += 1;
-  return cudaGetLastError();
+  return launch_assign_kernel(h->n, dim, s.x, s.y, s.z, gen, K, unit_out, &h->counters[3], st);
 }
 
 cudaError_t launch_unit_lists(sph_handle* h, const int32_t* unit, int32_t* unit_offsets, cudaStream_t st) {
@@ -453,14 +509,26 @@ cudaError_t launch_balance(sph_handle* h, const sph_state& s, double* gen, int K
   cudaError_t e = launch_unit_lists(h, s.unit, nullptr, st);
   if (e != cudaSuccess) return e;
   double* stats = h->unit_stats;
-  k_unit_stats<<<K, kBlock, 0, st>>>(h->unit_off, h->unit_list, s.x, s.y, s.z, s.d, h->dmax_nbr, dim, h->dp.kh,
-                                     bp.beta_sh, stats);
+  // blocks per unit: about four per SM in total, at most kUnitSplit
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+  }
+  int S = (4 * sms + K - 1) / K;
+  S = S < 1 ? 1 : (S > kUnitSplit ? kUnitSplit : S);
+  double* part = stats + (size_t)9 * K;
+  k_unit_stats<<<K * S, kBlock, 0, st>>>(h->unit_off, h->unit_list, s.x, s.y, s.z, s.d, h->dmax_nbr, dim,
+                                         h->dp.kh, bp.beta_sh, S, part);
+  k_unit_stats_final<<<(K + 63) / 64, 64, 0, st>>>(h->unit_off, K, S, part, stats);
   double* scratch = stats + (size_t)5 * K;
   k_balance_unit<<<K, 32, 0, st>>>(K, dim, gen, load, h->load_acc, h->adj_bits, (K + 31) / 32, stats, bp.theta,
                                    bp.sigma, bp.gamma_b, scratch);
   k_balance_apply<<<1, SPH_MAX_UNITS, 0, st>>>(K, dim, gen, scratch, h->load_acc, h->adj_bits, (K + 31) / 32,
                                                shift_out);
-  h->launches += 3;
+  h->launches += 4;
   return cudaGetLastError();
 }
 
@@ -553,7 +621,7 @@ extern "C" int voronoi_assign_static(int64_t n, const double* x, const double* y
   unsigned long long* exact = reinterpret_cast<unsigned long long*>(scr + kOffTail + 2);
   const size_t smem = sizeof(int) * 32 * K;
   k_static_reset<<<1, 1, 0, st>>>(total, exact, tot);   // the previous call left its values here
-  k_assign<<<grid_for(n, kBlock), kBlock, 0, st>>>(n, dim, x, y, z, gen, K, unit_out, exact);
+  launch_assign_kernel(n, dim, x, y, z, gen, K, unit_out, exact, st);
   k_unit_hist<<<nb, kUnitBlock, smem, st>>>(unit_out, n, K, nb, counts);   // writes every count
   e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_exclusive_scan(counts, total, sums, starts, n, tot, st);
