@@ -1,5 +1,6 @@
 // csph_api.cu -- the C ABI of include/csph.h: argument checks, workspace
 // ownership and the orchestration of the kernels of one CSPH step.
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -44,7 +45,7 @@ void free_all(sph_handle* h) {
                   h->status, h->counters, h->scratch, h->adj_G,
                   h->adj_GR, h->adj_pair, h->adj_par, h->adj_W, h->adj_store, h->mat_dev, h->vlist, h->vcnt,
                   h->vref, h->vflag, h->grad_p, h->grad_v, h->adj64_A, h->adj64_B, h->adj64_C,
-                  h->adj64_rho};
+                  h->adj64_rho, h->dt_key};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -247,6 +248,11 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   }
   CKI(dalloc(&h->rho_slot, n));
   CKI(dalloc(&h->dmax_nbr, n));
+  CKI(dalloc(&h->dt_key, (size_t)n_instances));
+  {
+    std::vector<long long> inf((size_t)n_instances, LLONG_MAX);
+    CKI(cudaMemcpy(h->dt_key, inf.data(), sizeof(long long) * inf.size(), cudaMemcpyHostToDevice));
+  }
   CKI(dalloc(&h->status, 1));
   CKI(cudaMemset(h->status, 0, sizeof(int)));
   CKI(dalloc(&h->counters, 8));
@@ -381,12 +387,13 @@ int sph_step(sph_handle* h, sph_state* s, int n_steps, double* t_dev, void* stre
   }
   const bool vd3 = h->K > 0 && h->p.n_upd > 0;
   sph_balance_params bp{h->p.theta, h->p.sigma, h->p.gamma_b, h->p.beta_sh};
+  bool dt_from_key = false;   // the previous step's fused second kick left the CFL keys
   for (int k = 0; k < n_steps; ++k) {
     // the CFL minima of the step's start state: from the previous step's second
     // kick inside this call (renumbering permutes an instance's particles and
     // leaves its minimum unchanged), else a k_derive pass
     if (k == 0) CK(h, launch_derive_dt(h, *s, false, st));
-    CK(h, launch_reduce_dt(h, st));
+    CK(h, launch_reduce_dt(h, st, dt_from_key));
     CK(h, launch_kick_drift(h, *s, st));
     if (h->verlet) {
       // Verlet lists: the mesh, slot order and lists are rebuilt only when the device flag
@@ -399,14 +406,19 @@ int sph_step(sph_handle* h, sph_state* s, int n_steps, double* t_dev, void* stre
     CK(h, launch_pack(h, *s, true, st));
     // unit adjacency is needed only from the evaluation that precedes a rebalance
     h->collect_adj = !vd3 || h->steps_since_balance + 1 >= h->p.n_upd;
+    const bool next_dt = k + 1 < n_steps;
     if (h->verlet) {
+      // the second half kick, the time and the next CFL bound are fused into the
+      // list kernel's rate write
       CK(h, launch_list_build(h, *s, st));
-      CK(h, launch_pair_lists(h, *s, st));
+      CK(h, launch_pair_lists(h, *s, st, true, t_dev, next_dt));
+      dt_from_key = next_dt;
     } else {
       CK(h, launch_pair(h, *s, st));
+      CK(h, launch_kick2(h, *s, t_dev, st, next_dt));
+      dt_from_key = false;
     }
     h->collect_adj = true;
-    CK(h, launch_kick2(h, *s, t_dev, st, k + 1 < n_steps));
     if (vd3 && ++h->steps_since_balance >= h->p.n_upd) {
       // Alg. 1 outer loop: shift generators, reassign, renumber
       h->steps_since_balance = 0;

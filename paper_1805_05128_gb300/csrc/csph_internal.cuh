@@ -106,6 +106,7 @@ struct sph_handle {
   void* packC = nullptr;
   double* rho_slot = nullptr;        // [n] density of slot s (FP64)
 
+  long long* dt_key = nullptr;             // [n_inst] CFL keys left by the fused second kick
   double* dmax_nbr = nullptr;        // [n] largest neighbour size of particle p (last evaluation)
 
   // Voronoi work units
@@ -258,7 +259,9 @@ void set_global_error(const std::string& msg);
 // Launchers (defined in k_step.cu, k_pair.cu, k_vd3.cu).  They enqueue on
 // `st` and return the launch status.
 cudaError_t launch_derive_dt(sph_handle* h, const sph_state& s, bool with_bbox, cudaStream_t st);
-cudaError_t launch_reduce_dt(sph_handle* h, cudaStream_t st);
+// from_key: the step's dt from the CFL keys that the previous step's fused second
+// kick left in dt_key (else from the block partials); dt_key is reset either way
+cudaError_t launch_reduce_dt(sph_handle* h, cudaStream_t st, bool from_key = false);
 cudaError_t launch_kick_drift(sph_handle* h, const sph_state& s, cudaStream_t st);
 // gate (Verlet mode): device flag, the mesh kernels return at once while gate[0] == 0
 cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st, const int* gate = nullptr);
@@ -289,7 +292,10 @@ cudaError_t launch_pair_vjp(sph_handle* h, const sph_state& s, const void* G, co
 // Verlet lists: build (k_pair over the (1 + beta) radius, returns at once unless vflag[0]) and
 // the pair evaluation over the lists
 cudaError_t launch_list_build(sph_handle* h, const sph_state& s, cudaStream_t st);
-cudaError_t launch_pair_lists(sph_handle* h, const sph_state& s, cudaStream_t st);
+// kick2: also the second half kick of the step (and the instance time, and with
+// next_dt the CFL keys of the new state), fused into the rate write
+cudaError_t launch_pair_lists(sph_handle* h, const sph_state& s, cudaStream_t st, bool kick2 = false,
+                              double* t_dev = nullptr, bool next_dt = false);
 cudaError_t launch_assign(sph_handle* h, const sph_state& s, const double* gen, int K, int dim,
                           int32_t* unit_out, cudaStream_t st);
 cudaError_t launch_unit_lists(sph_handle* h, const int32_t* unit, int32_t* unit_offsets, cudaStream_t st);

@@ -21,6 +21,7 @@
 // order as the oracle, so the pair set is the FP64 one.  Per-particle sums
 // are Kahan-compensated.
 #include "csph_internal.cuh"
+#include "step_math.cuh"
 
 namespace csph {
 
@@ -87,6 +88,17 @@ struct PairArgs {
   // vinv = 1 / vscale.  In FP64 mode the scales are 1 (fscale 2).
   float wscale_f;
   double fscale, rscale, vinv;
+  // second half kick fused into the list kernel's rate write (k_pair_lists):
+  // v, rho, E advanced by dt/2 with the new rates (the arithmetic of k_kick2),
+  // the instance time advanced by dt, and with kick2_cfl the CFL keys of the
+  // new state min-reduced into dt_key[instance] for the next step
+  int kick2, kick2_cfl;
+  double *kx_vx, *kx_vy, *kx_vz, *kx_rho, *kx_E;
+  const int32_t* kx_mat;
+  const double* kx_dt;
+  double* kx_t;
+  long long* dt_key;
+  DevParams dp;
 };
 
 constexpr int kModeFwd = 0;    // rates
@@ -952,7 +964,7 @@ __device__ __forceinline__ T slot_sum(const Kahan<T>& k) {
 }
 
 template <bool MIXED, int DIM, bool HLL = false, bool EXTRA = true>
-__global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairArgs a) {
+__global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pair_lists(PairArgs a) {
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
   using V4 = typename P::V4;
@@ -1086,19 +1098,65 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairAr
     __syncwarp();
     {
       const int64_t i = g0 + lane;                     // one slot of the group per lane
+      long long key = LLONG_MAX;
+      int bi = 0;
       if (i < g1) {
         auto rv = [&](int qv) -> double {
           if constexpr (MIXED) return (double)res[warp][qv][lane];
           else return res64[warp][qv][lane];
         };
         const int64_t p = a.perm[i];
-        a.drho[p] = 2.0 * a.rho_slot[i] * (rv(0) * a.rscale);
+        const double drho = 2.0 * a.rho_slot[i] * (rv(0) * a.rscale);
         const double im = a.fscale / a.m[p];
-        a.ax[p] = rv(1) * im;
-        if (DIM >= 2) a.ay[p] = rv(2) * im;
-        if (DIM >= 3) a.az[p] = rv(3) * im;
-        a.dE[p] = rv(4) * im;
+        const double acc[3] = {rv(1) * im, DIM >= 2 ? rv(2) * im : 0.0, DIM >= 3 ? rv(3) * im : 0.0};
+        const double dE = rv(4) * im;
+        a.drho[p] = drho;
+        a.ax[p] = acc[0];
+        if (DIM >= 2) a.ay[p] = acc[1];
+        if (DIM >= 3) a.az[p] = acc[2];
+        a.dE[p] = dE;
         if (EXTRA) a.dmax_nbr[p] = res_n[warp][lane] ? rv(5) : -1.0;
+        if (a.kick2) {
+          if (a.n_inst > 1) {
+            int lo = 0, hi = a.n_inst;
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (a.inst_off[mid] <= i) lo = mid; else hi = mid;
+            }
+            bi = lo;
+          }
+          const double dt = a.kx_dt[bi];
+          const double hdt = 0.5 * dt;
+          double* V[3] = {a.kx_vx, a.kx_vy, a.kx_vz};
+          double v[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) v[c] = V[c][p];
+          const double rho0 = a.kx_rho[p], E0 = a.kx_E[p];
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) v[c] = axpy<MIXED>(hdt, acc[c], v[c]);
+          const double rho = axpy<MIXED>(hdt, drho, rho0);
+          const double E = axpy<MIXED>(hdt, dE, E0);
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) V[c][p] = v[c];
+          a.kx_rho[p] = rho;
+          a.kx_E[p] = E;
+          if (a.kx_t && i == a.inst_off[bi]) a.kx_t[bi] += dt;    // one slot per instance
+          if (a.kick2_cfl) key = cfl_key(a.dp, v[0], v[1], v[2], E, rho, a.m[p], a.kx_mat ? a.kx_mat[p] : 0);
+        }
+      }
+      if (a.kick2_cfl) {
+        // one atomic per warp when the group lies in one instance (the usual case)
+        const int b0 = __shfl_sync(0xffffffffu, bi, 0);
+        if (__all_sync(0xffffffffu, i >= g1 || bi == b0)) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const long long q = __shfl_xor_sync(0xffffffffu, key, o);
+            key = q < key ? q : key;
+          }
+          if (lane == 0) atomicMin(&a.dt_key[b0], key);
+        } else if (i < g1) {
+          atomicMin(&a.dt_key[bi], key);
+        }
       }
     }
     __syncwarp();
@@ -1297,8 +1355,21 @@ cudaError_t launch_list_build(sph_handle* h, const sph_state& s, cudaStream_t st
 }
 
 // Pair evaluation over the Verlet lists (rates, counters, unit loads).
-cudaError_t launch_pair_lists(sph_handle* h, const sph_state& s, cudaStream_t st) {
+cudaError_t launch_pair_lists(sph_handle* h, const sph_state& s, cudaStream_t st, bool kick2, double* t_dev,
+                              bool next_dt) {
   PairArgs a = make_args(h, s);
+  a.kick2 = kick2 ? 1 : 0;
+  a.kick2_cfl = kick2 && next_dt ? 1 : 0;
+  a.kx_vx = s.vx;
+  a.kx_vy = s.vy;
+  a.kx_vz = s.vz;
+  a.kx_rho = s.rho;
+  a.kx_E = s.E;
+  a.kx_mat = s.mat;
+  a.kx_dt = h->dt;
+  a.kx_t = t_dev;
+  a.dt_key = h->dt_key;
+  a.dp = h->dp;
   cudaError_t e = cudaMemsetAsync(h->counters, 0, 3 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(&h->counters[5], 0, sizeof(unsigned long long), st);

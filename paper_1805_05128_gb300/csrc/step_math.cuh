@@ -1,0 +1,129 @@
+// step_math.cuh -- per-particle arithmetic shared by the step kernels and
+// the pair-list kernel's fused second kick: order keys of doubles, the size
+// d = (m / rho)^(1/D), the half-kick update, the FP32 sound speed and the CFL
+// key of a particle.
+#pragma once
+
+#include "csph_internal.cuh"
+
+namespace csph {
+
+// Reductions run on order-preserving 64-bit integer keys of the doubles
+// (integer ALU instead of the narrow FP64 pipe): key(x) = bits(x) for x >= 0,
+// bits(x) ^ 0x7fff...f for x < 0, so key order is numeric order.
+__device__ __forceinline__ long long dkey(double x) {
+  long long b = __double_as_longlong(x);
+  return b < 0 ? b ^ 0x7fffffffffffffffLL : b;
+}
+__device__ __forceinline__ double dunkey(long long k) {
+  return __longlong_as_double(k < 0 ? k ^ 0x7fffffffffffffffLL : k);
+}
+
+// Cube root in FP64 with little FP64 work: the FP32 cube root as seed, then
+// two Newton steps on y^3 - x = 0 whose derivative reciprocal 1/(3 y^2) is
+// taken in FP32 (a ~1e-7 relative error in the slope only scales each
+// correction, so the error falls ~1e-7-fold per step to rounding level).
+__device__ __forceinline__ double cbrt_fast(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return cbrt(x);   // outside the FP32 seed's comfortable range
+  double y = (double)cbrtf((float)x);
+  const double r = (double)__frcp_rn((float)(3.0 * y * y));
+  y = y - (y * y * y - x) * r;
+  y = y - (y * y * y - x) * r;
+  return y;
+}
+
+__device__ __forceinline__ double size_of(int dim, double m, double rho) {
+  double vol = m / rho;
+  return dim == 1 ? vol : (dim == 2 ? sqrt(vol) : cbrt_fast(vol));
+}
+
+// d = (m / rho)^(1/D) for a mixed-precision step, with a third of the FP64
+// work of size_of: FP32 seeds for 1/rho and the root, each refined by one
+// FP64 Newton step (the error squares: ~1e-7 -> ~1e-14 relative).  The step's
+// pair decisions take this d as given and its FP32 fluxes are far coarser.
+__device__ __forceinline__ double size_of_mixed(int dim, double m, double rho) {
+  const float rf = (float)rho;
+  double r = (double)__frcp_rn(rf);
+  r = r * __fma_rn(-rho, r, 2.0);
+  const double vol = m * r;
+  if (dim == 1) return vol;
+  const float vf = (float)vol;
+  if (dim == 2) {
+    const float y0 = sqrtf(vf);
+    const double y = (double)y0;
+    return __fma_rn(__fma_rn(-y, y, vol), (double)(0.5f / y0), y);
+  }
+  if (!(vf > 1e-30f && vf < 1e30f)) return cbrt(vol);   // outside the FP32 seed's comfortable range
+  const float y0 = cbrtf(vf);
+  const double y = (double)y0;
+  return __fma_rn(-__fma_rn(y * y, y, -vol), (double)__frcp_rn(3.0f * y0 * y0), y);
+}
+
+// Half kick / drift y + a x: the oracle's correctly rounded product and sum
+// for an FP64 handle; one fused multiply-add for a mixed handle (FP64 is the
+// narrow pipe on this GPU and these kernels are bound by it).
+template <bool MIXED>
+__device__ __forceinline__ double axpy(double a, double x, double y) {
+  if constexpr (MIXED) return __fma_rn(a, x, y);
+  else return __dadd_rn(y, __dmul_rn(a, x));
+}
+
+// isfinite on the bits (integer ALU, not the FP64 pipe)
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+
+// Sound speed in FP32 from an FP64 specific internal energy (the closures of
+// eos() written in single precision; the stiffened gas in the form
+// c^2 = gamma (gamma - 1)(rho e - P_inf) / rho, without the P + P_inf
+// cancellation).  For the CFL bound of a mixed-precision step only.
+__device__ __forceinline__ float sound_speed_f32(const Mat& m, float rho, float e) {
+  const float g = (float)m.gamma;
+  float c2;
+  if (m.eos == SPH_EOS_IDEAL) {
+    c2 = g * (g - 1.0f) * e;
+  } else if (m.eos == SPH_EOS_STIFFENED) {
+    c2 = g * (g - 1.0f) * (rho * e - (float)m.p_inf) / rho;
+  } else if (m.eos == SPH_EOS_TAIT) {
+    const float c0 = (float)m.c0;
+    c2 = c0 * c0 * powf(rho / (float)m.rho0, g - 1.0f);
+  } else {
+    const float ca = (float)m.c0, sa = (float)m.s_a, r0 = (float)m.rho0;
+    const float x = r0 / rho, u = 1.0f - x, D = 1.0f - sa * u, iD2 = 1.0f / (D * D);
+    const float Pr = r0 * ca * ca * u * iD2, er = 0.5f * ca * ca * u * u * iD2;
+    const float du = x / rho;
+    const float dPr = r0 * ca * ca * (1.0f + sa * u) * iD2 / D * du;
+    const float der = ca * ca * u * iD2 / D * du;
+    const float P = Pr + g * rho * (e - er);
+    c2 = dPr + g * (e - er) - g * rho * der + g * P / rho;
+  }
+  return c2 > 0.0f ? sqrtf(c2) : 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// The CFL bound dt_i = eta d_i / (c_i + |v_i|).  Inside a mixed-precision step
+// (no bbox, nothing written back) it is evaluated in FP32 from the FP64 state
+// (e = E - v^2/2 in FP64): it is a stability bound, the step then uses that dt
+// exactly in FP64, and the FP64 divisions, roots and cube root of every
+// particle are what bound these kernels on GB300.  FP64 handles keep the FP64
+// expression (bit parity of dt).
+// ---------------------------------------------------------------------------
+// CFL order key of one particle's bound dt_i = eta d_i / (c_i + |v_i|) at the
+// given state: FP32 in a mixed-precision handle (see above), FP64 otherwise.
+__device__ __forceinline__ long long cfl_key(const DevParams& P, double vx, double vy, double vz, double E,
+                                             double rho, double m, int mi) {
+  const double v2 = vx * vx + vy * vy + vz * vz;
+  const double e = E - 0.5 * v2;
+  if (P.precision == SPH_PREC_MIXED) {
+    const float rf = (float)rho;
+    const float c = sound_speed_f32(P.mat[mi], rf, (float)e);
+    const float vol = (float)m / rf;
+    const float d = P.dim == 1 ? vol : (P.dim == 2 ? sqrtf(vol) : cbrtf(vol));
+    return dkey((double)((float)P.eta * d / (c + sqrtf((float)v2))));
+  }
+  double Pp, cp;
+  eos(P.mat[mi], rho, e, Pp, cp);
+  return dkey((P.eta * size_of(P.dim, m, rho)) / (cp + sqrt(v2)));
+}
+
+}  // namespace csph
