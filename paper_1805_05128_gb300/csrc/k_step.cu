@@ -167,10 +167,10 @@ __global__ void k_reduce_dt(const int32_t* __restrict__ inst_blk, const BlockPar
   }
 }
 
-// One block per instance: reduce the block partials of the instance.
-// mode 1: dt = cfl * min; mode 2: bounding box and sizes into the grid record.
+// One block per instance: the bounding box and the two largest sizes of the
+// instance from its block partials, into the grid record.
 __global__ void k_reduce_inst(const int32_t* __restrict__ inst_blk, const BlockPart* __restrict__ part,
-                              double cfl, double* dt, GridInfo* grid, int mode, const int* __restrict__ gate) {
+                              GridInfo* grid, const int* __restrict__ gate) {
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   int b = blockIdx.x;
   Red r;
@@ -183,13 +183,10 @@ __global__ void k_reduce_inst(const int32_t* __restrict__ inst_blk, const BlockP
   }
   block_reduce(r);
   if (threadIdx.x == 0) {
-    if (mode == 1) dt[b] = cfl * dunkey(r.dtmin);
-    if (mode == 2) {
-      GridInfo& g = grid[b];
-      for (int a = 0; a < 3; ++a) { g.x0[a] = dunkey(r.lo[a]); g.hi[a] = dunkey(r.hi[a]); }
-      g.dmax1 = dunkey(r.d1);
-      g.dmax2 = dunkey(r.d2);
-    }
+    GridInfo& g = grid[b];
+    for (int a = 0; a < 3; ++a) { g.x0[a] = dunkey(r.lo[a]); g.hi[a] = dunkey(r.hi[a]); }
+    g.dmax1 = dunkey(r.d1);
+    g.dmax2 = dunkey(r.d2);
   }
 }
 
@@ -706,7 +703,7 @@ cudaError_t launch_kick_drift(sph_handle* h, const sph_state& s, cudaStream_t st
 // Mesh from the block partials left by k_derive(with_bbox) or k_kick_drift,
 // then the counting sort of particles into cells.
 cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st, const int* gate) {
-  k_reduce_inst<<<h->n_inst, kBlock, 0, st>>>(h->inst_blk, h->part, h->dp.cfl, h->dt, h->grid, 2, gate);
+  k_reduce_inst<<<h->n_inst, kBlock, 0, st>>>(h->inst_blk, h->part, h->grid, gate);
   k_grid_setup<<<1, 32, 0, st>>>(h->dp, h->n_inst, h->inst_off, h->inst_cap, h->grid, h->total_cells,
                                  h->status, gate);
   k_cell_count<<<capped_grid(h->nblk), kBlock, 0, st>>>(h->dp.dim, s, h->blk_start, h->blk_end, h->blk_inst,
