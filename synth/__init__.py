@@ -142,6 +142,36 @@ def plate_impact(proj: int = 50, target=(200, 200, 25), a: float = 1e-4, v: floa
                    meta=dict(a=a, v=v, target=target, proj=proj, n_target=len(xt)))
 
 
+def plate_impact_2d(proj: int = 20, target=(80, 12), a: float = 1e-4, v: float = 1000.0,
+                    rho0: float = 2700.0, c0: float = 5300.0, gamma: float = 2.0, units: int = 0,
+                    n_steps: int = 100, seed: int | None = None, jitter: float = 0.0) -> Problem:
+    """The plate impact in a plane (x, y), y the impact axis: square lattices of
+    spacing a, target tx*ty with rows y = k a (k = 0..ty-1), projector square
+    proj^2 centred above it with its lowest row at y = (ty + 1) a, moving at -v
+    along y; both at rho0 and P = 0; mass rho0 a^2 (so d = a)."""
+    tx, ty = target
+    i, k = np.meshgrid(np.arange(tx), np.arange(ty), indexing="ij")
+    xt = ((i - (tx - 1) / 2.0) * a).ravel()
+    yt = (k * a).ravel().astype(np.float64)
+    i, k = np.meshgrid(np.arange(proj), np.arange(proj), indexing="ij")
+    xp = ((i - (proj - 1) / 2.0) * a).ravel()
+    yp = ((k + ty + 1) * a).ravel().astype(np.float64)
+    x = np.concatenate([xt, xp]); y = np.concatenate([yt, yp])
+    n = len(x)
+    if seed is not None and jitter > 0.0:
+        r = uniform(seed, 2 * n)
+        x = x + jitter * a * (2.0 * r[0::2] - 1.0)
+        y = y + jitter * a * (2.0 * r[1::2] - 1.0)
+    vy = np.concatenate([np.zeros(len(xt)), np.full(len(xp), -v)])
+    mat = stiffened(rho0, c0, gamma)
+    e0 = gamma * mat.p_inf / ((gamma - 1.0) * rho0)
+    arrays = dict(x=x, y=y, vx=np.zeros(n), vy=vy, rho=np.full(n, rho0), E=e0 + 0.5 * vy * vy,
+                  m=np.full(n, rho0 * a ** 2))
+    return Problem(f"plate_impact_2d_{n}", 2, arrays, [mat], kernel="cubic", kappa=2.0, eta=1.3,
+                   cfl=0.3, n_steps=n_steps, units=units, unit_dim=2, n_upd=10,
+                   meta=dict(a=a, v=v, target=target, proj=proj, n_target=len(xt)))
+
+
 def plate_impact_full() -> Problem:
     """1.125M particles: 50^3 projector at 1 km/s onto a 200x200x25 slab."""
     return plate_impact(50, (200, 200, 25), units=64, n_steps=500)

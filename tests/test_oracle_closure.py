@@ -31,7 +31,7 @@ def test_kernel_normalised(kernel, kappa, dim):
 
 
 @pytest.mark.parametrize("kernel,kappa", [(O.KERNEL_CUBIC, 2.0), (O.KERNEL_WENDLAND_C2, 1.936)])
-@pytest.mark.parametrize("dim", [1, 3])
+@pytest.mark.parametrize("dim", [1, 2, 3])
 def test_kernel_derivative_matches_fd(kernel, kappa, dim):
     h = 1.3
     for q in np.linspace(0.05, 1.9, 23):

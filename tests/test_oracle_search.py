@@ -67,7 +67,8 @@ def test_brute_force_matches_kdtree(dim):
 def test_lattice_neighbour_counts():
     """Perfect cubic lattice, h = 1.3 a, support 2h: lattice points with
     0 < r^2 < 6.76 a^2 are the shells r^2 = 1, 2, 3, 4, 5, 6 with 6, 12, 8, 6,
-    24, 24 points: 80 neighbours.  1D with h = 1.5 a: 4 neighbours."""
+    24, 24 points: 80 neighbours.  Square lattice, same h: r^2 = 1, 2, 4, 5
+    with 4, 4, 4, 8 points: 20 neighbours.  1D with h = 1.5 a: 4 neighbours."""
     n = 9
     pos, d = _jittered_lattice(3, n, 0.0, 0)
     s = _state(3, pos, d)
@@ -75,6 +76,11 @@ def test_lattice_neighbour_counts():
     cnt = np.bincount(np.concatenate([pi, pj]), minlength=s.n)
     centre = (n // 2) + n * (n // 2) + n * n * (n // 2)
     assert cnt[centre] == 80
+    pos, d = _jittered_lattice(2, n, 0.0, 0)
+    s = _state(2, pos, d)
+    pi, pj = O.pairs(O.Params(dim=2, eta=1.3), s)
+    cnt = np.bincount(np.concatenate([pi, pj]), minlength=s.n)
+    assert cnt[(n // 2) + n * (n // 2)] == 20
     pos, d = _jittered_lattice(1, 50, 0.0, 0)
     s = _state(1, pos, d)
     pi, pj = O.pairs(O.Params(dim=1, eta=1.5), s)

@@ -78,11 +78,14 @@ def test_cfl_first_step():
     assert dts[0] == pytest.approx(0.3 * 1.5 / 320.0 / math.sqrt(1.4), rel=1e-14)
 
 
-@pytest.mark.parametrize("case", ["sod", "plate"])
+@pytest.mark.parametrize("case", ["sod", "plate_2d", "plate"])
 def test_conservation(case):
     if case == "sod":
         prob = synth.sod_1d()
         steps = 200
+    elif case == "plate_2d":
+        prob = synth.plate_impact_2d(8, (24, 6), a=1e-4, v=1000.0, seed=3, jitter=0.05)
+        steps = 30
     else:
         prob = synth.plate_impact(5, (14, 14, 5), a=1e-4, v=1000.0, units=4, seed=3, jitter=0.05)
         steps = 30
