@@ -454,7 +454,7 @@ struct FwdAcc {
     if (DIM >= 2) a.ay[p] = (double)s_fy.s * im;
     if (DIM >= 3) a.az[p] = (double)s_fz.s * im;
     a.dE[p] = (double)s_q.s * im;
-    a.dmax_nbr[p] = nfull ? (double)dmax : -1.0;
+    if (EXTRA) a.dmax_nbr[p] = nfull ? (double)dmax : -1.0;
   }
 };
 
@@ -501,7 +501,7 @@ constexpr int kWarps = kPairBlock / 32;
 constexpr int kBuildCap = 128;
 constexpr int kBuildBlocks = 6;      // resident blocks per SM of the mixed list build
 
-template <bool MIXED, int DIM, int MODE, bool HLL = false>
+template <bool MIXED, int DIM, int MODE, bool HLL = false, bool EXTRA = true>
 __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kModeFwd2) ? (MIXED ? 4 : 2)
                                                  : (MODE == kModeGrad ? (MIXED ? 5 : 3)
                                                  : (MODE == kModeList ? (MIXED ? kBuildBlocks : 4) : (MIXED ? 6 : 4))))
@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
     if constexpr (VJP) { Gi = Gp[ii]; Ri = Rp[ii]; }
     Kahan<T> s_bx[3], s_bv[3], s_bP, s_bZ, s_bV, s_bd, s_brho;
 
-    FwdAcc<MIXED, DIM, MODE == kModeFwd2, HLL> fw;
+    FwdAcc<MIXED, DIM, MODE == kModeFwd2, HLL, EXTRA> fw;
     if constexpr (MODE == kModeFwd2) {
       fw.gPi = reinterpret_cast<const V4*>(a.gP)[ii];
       const V4* GV = reinterpret_cast<const V4*>(a.gV);
@@ -1173,38 +1173,44 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
 
 // Persistent grid: SMs x resident CTAs per SM, capped by the handle's
 // pair_blocks_per_sm (0 = as many as fit).
-template <bool MIXED, int DIM, int MODE, bool HLL>
+template <bool MIXED, int DIM, int MODE, bool HLL, bool EXTRA = true>
 cudaError_t launch_one(const PairArgs& args, int blocks_per_sm, cudaStream_t st) {
   static int sms = 0, per_sm = 0;
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<MIXED, DIM, MODE, HLL>, kPairBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<MIXED, DIM, MODE, HLL, EXTRA>, kPairBlock, 0);
     if (per_sm < 1) per_sm = 1;
   }
   const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
-  k_pair<MIXED, DIM, MODE, HLL><<<sms * b, kPairBlock, 0, st>>>(args);
+  k_pair<MIXED, DIM, MODE, HLL, EXTRA><<<sms * b, kPairBlock, 0, st>>>(args);
   return cudaGetLastError();
 }
 
-// The pair solver is a template parameter of the flux modes (the HLL select
-// costs about 1 % of the pair kernel when left as a run-time branch).
+template <bool MIXED, int MODE, bool HLL, bool EXTRA>
+cudaError_t launch_dim3(sph_handle* h, const PairArgs& args, cudaStream_t st) {
+  const int b = h->p.pair_blocks_per_sm;
+  switch (h->dp.dim) {
+    case 1: return launch_one<MIXED, 1, MODE, HLL, EXTRA>(args, b, st);
+    case 2: return launch_one<MIXED, 2, MODE, HLL, EXTRA>(args, b, st);
+    default: return launch_one<MIXED, 3, MODE, HLL, EXTRA>(args, b, st);
+  }
+}
+
+// The pair solver and the side outputs (neighbour sizes, unit adjacency, pair
+// output) are template parameters of the flux modes: as run-time branches in
+// the pair loop they cost ~1 % and ~10 % of the kernel.
 template <bool MIXED, int MODE>
 cudaError_t launch_dim(sph_handle* h, const PairArgs& args, cudaStream_t st) {
-  const int b = h->p.pair_blocks_per_sm;
   constexpr bool kFlux = MODE == kModeFwd || MODE == kModeFwd2;
-  if (kFlux && h->solver == SPH_SOLVER_HLL) {
-    switch (h->dp.dim) {
-      case 1: return launch_one<MIXED, 1, MODE, kFlux>(args, b, st);
-      case 2: return launch_one<MIXED, 2, MODE, kFlux>(args, b, st);
-      default: return launch_one<MIXED, 3, MODE, kFlux>(args, b, st);
-    }
-  }
-  switch (h->dp.dim) {
-    case 1: return launch_one<MIXED, 1, MODE, false>(args, b, st);
-    case 2: return launch_one<MIXED, 2, MODE, false>(args, b, st);
-    default: return launch_one<MIXED, 3, MODE, false>(args, b, st);
+  if constexpr (!kFlux) {
+    return launch_dim3<MIXED, MODE, false, true>(h, args, st);
+  } else {
+    const bool extra = args.collect_adj || args.pair_i;
+    if (h->solver == SPH_SOLVER_HLL)
+      return extra ? launch_dim3<MIXED, MODE, true, true>(h, args, st) : launch_dim3<MIXED, MODE, true, false>(h, args, st);
+    return extra ? launch_dim3<MIXED, MODE, false, true>(h, args, st) : launch_dim3<MIXED, MODE, false, false>(h, args, st);
   }
 }
 
