@@ -509,10 +509,13 @@ def pair_traffic_bytes(args):
 
 
 def kernel_rev() -> str:
-    """Identifier of the pair-kernel source the stored ncu traffic belongs to."""
+    """Identifier of the pair-kernel sources the stored ncu traffic belongs to
+    (the two pair translation units and the headers they share)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1805_05128_gb300", "csrc", "k_pair.cu")
-    return hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    h = hashlib.sha1()
+    for f in ("k_pair.cu", "k_pair_lists.cu", "pair_common.cuh", "step_math.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1805_05128_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
 
 
 def main():

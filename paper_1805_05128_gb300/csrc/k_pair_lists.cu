@@ -1,0 +1,316 @@
+// k_pair_lists.cu -- the CSPH pair rates over the Verlet lists (Sec. 4.1-4.2
+// with the buffered horizon of eq. (Dcell)): each list entry is tested as the
+// cell search does, the fluxes of the interacting pairs (pair_common.cuh's
+// FwdAcc) are summed per particle, and the step's second half kick is applied
+// with the new rates.
+#include "pair_common.cuh"
+
+namespace csph {
+
+namespace {
+
+// Pair evaluation over the Verlet lists: four lanes per slot i (eight slots
+// per warp: the per-slot reductions and set-up are shared by eight slots, and
+// a list of ~90 entries fills its lanes to the last chunk), taken in groups
+// of 32 consecutive slots from a global counter.  The slot's lanes read i's
+// list four entries at a time (particle-major, so the reads are contiguous);
+// each lane decides its entry as k_pair does (FP32 test outside the band of
+// 2^-12 D^c^2, FP64 in the oracle's operation order inside it) and, if the
+// pair interacts, adds its flux to the lane's Kahan sums (FwdAcc).  Test and
+// flux share the loads and the separation; about 86 % of the entries of a
+// list built with beta = 0.15 interact, so the lanes whose entry does not
+// are cheaper than compacting the accepted ones first.  Each lane's Kahan
+// sum takes about a quarter of the slot's pairs; the slot's four sums are
+// combined by a fixed butterfly, and the FP64 scaling of the rates is done
+// for the 32 slots of the group at once, one slot per lane.  Offsets stay
+// relative to the cells of the build and each pair's shift comes from its
+// neighbour-cell code, so the fluxes keep their bitwise antisymmetry; every
+// order is fixed, so results are reproducible bit for bit.
+
+// Lanes per slot of k_pair_lists (a divisor of 32): measured on the 1.125M
+// plate impact, 16 / 8 / 4 / 2 lanes per slot take 0.89 / 0.81 / 0.75 / 0.76 ms.
+constexpr int kSlotLanes = 4;
+constexpr int kSlotsPerWarp = 32 / kSlotLanes;
+
+// Sum over a slot's lanes of their Kahan sums (s - c), by a fixed butterfly.
+template <typename T>
+__device__ __forceinline__ T slot_sum(const Kahan<T>& k) {
+  T v = k.s - k.c;
+#pragma unroll
+  for (int o = kSlotLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <bool MIXED, int DIM, bool HLL = false, bool EXTRA = true>
+__global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pair_lists(PairArgs a) {
+  using P = Pair<MIXED, DIM>;
+  using T = typename P::T;
+  using V4 = typename P::V4;
+  using V2 = typename P::V2;
+  __shared__ float res[kWarps][6][32];            // per slot of the group: sums of rho, a (3), E, and dmax
+  __shared__ double res64[kWarps][6][MIXED ? 1 : 32];
+  __shared__ unsigned res_n[kWarps][32];
+  // unit shifts (-1, 0, 1) per axis of each neighbour-cell code; a table read
+  // and three multiplies are cheaper than the integer divisions and
+  // conversions of the decode, and give the same FP32 shifts bit for bit
+  __shared__ float4 unit_shift[32];
+  if (threadIdx.x < 32) {
+    const int c = threadIdx.x;
+    unit_shift[c] = make_float4((float)(c % 3 - 1), (float)((c / 3) % 3 - 1), (float)(c / 9 - 1), 0.f);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int half = lane / kSlotLanes, hl = lane % kSlotLanes;   // the slot's group of lanes, lane in it
+  const unsigned hmask = (kSlotLanes == 32 ? 0xffffffffu : ((1u << kSlotLanes) - 1u)) << (half * kSlotLanes);
+  const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
+  for (;;) {
+    int64_t g0 = 0;
+    if (lane == 0) g0 = (int64_t)atomicAdd(a.work_counter, 32ull);
+    g0 = __shfl_sync(0xffffffffu, g0, 0);
+    if (g0 >= a.n) break;
+    const int64_t g1 = g0 + 32 < a.n ? g0 + 32 : a.n;
+    int unit_run = -1;
+    unsigned unit_load = 0;
+    unsigned tf = 0, tc = 0, te = 0;
+    // Half h of the warp takes slots g0 + 2q + h, q = 0..15.  The list reads
+    // are software-pipelined: the next chunk of entries (and, across slots,
+    // the next slot's first chunk and count) is requested before the current
+    // one is evaluated, so the DRAM latency of the lists overlaps the L2
+    // gathers and the arithmetic.  vcap >= 32, so the first chunk of any row
+    // is in bounds.
+    uint32_t e_pre = 0u;
+    int cnt_pre = 0;
+    if (g0 + half < g1) {
+      e_pre = a.vlist[(g0 + half) * (int64_t)a.vcap + hl];
+      cnt_pre = a.vcnt[g0 + half];
+    }
+    for (int q = 0; g0 + kSlotsPerWarp * q < g1; ++q) {   // warp-uniform
+      const int64_t i = g0 + kSlotsPerWarp * q + half;       // this group's slot
+      const bool iv = i < g1;                                // uniform in the group
+      const int cnt = iv ? cnt_pre : 0;
+      uint32_t e_cur = e_pre;
+      if (i + kSlotsPerWarp < g1) {
+        e_pre = a.vlist[(i + kSlotsPerWarp) * (int64_t)a.vcap + hl];
+        cnt_pre = a.vcnt[i + kSlotsPerWarp];
+      }
+      const int64_t ii = iv ? i : g0;                 // a valid slot for the loads
+      int b = 0;
+      if (a.n_inst > 1) {
+        int lo = 0, hi = a.n_inst;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (a.inst_off[mid] <= ii) lo = mid; else hi = mid;
+        }
+        b = lo;
+      }
+      const GridInfo& g = a.grid[b];
+      const T dcs = MIXED ? (T)g.dc_f : T(0);
+      const float band = MIXED ? 0x1p-12f * g.dc_f * g.dc_f : 0.f;
+      const V4 Ai = A[ii];
+      const V4 Bi = reinterpret_cast<const V4*>(a.B)[ii];
+      const V2 Ci = reinterpret_cast<const V2*>(a.C)[ii];
+      const T khdi = MIXED ? (T)a.kh_f * Ai.w : T(0);
+      const int ui = a.K > 0 ? a.slot_unit[ii] : 0;
+      const uint32_t* __restrict__ row = a.vlist + ii * (int64_t)a.vcap;
+      FwdAcc<MIXED, DIM, false, HLL, EXTRA> fw;
+      unsigned nacc = 0;                              // accepted pairs of i (uniform in the group)
+      int cmax = cnt;                                 // chunks run by the whole warp
+#pragma unroll
+      for (int o = kSlotLanes; o < 32; o <<= 1) {
+        const int other = __shfl_xor_sync(0xffffffffu, cmax, o);
+        cmax = cmax > other ? cmax : other;
+      }
+      for (int base = 0; base < cmax; base += kSlotLanes) {
+        const int k = base + hl;
+        const bool kv = k < cnt;
+        const uint32_t e = kv ? e_cur : 0u;
+        if (base + kSlotLanes < cnt) e_cur = (k + kSlotLanes < cnt) ? row[k + kSlotLanes] : 0u;   // next chunk, requested now
+        bool acc = false;
+        if (kv) {
+          T sx = T(0), sy = T(0), sz = T(0);
+          if (MIXED) {
+            const float4 U = unit_shift[e & 31u];
+            sx = (T)U.x * dcs;
+            sy = (T)U.y * dcs;
+            sz = (T)U.z * dcs;
+          }
+          acc = fw.pair_listed(a, ii, Ai, Bi, Ci, ui, (int64_t)(e >> 5), sx, sy, sz, khdi, band, te);
+        }
+        nacc += __popc(__ballot_sync(0xffffffffu, acc) & hmask);
+      }
+      // combine the half's sums (fixed butterfly order); the rates are scaled below, per lane
+      const T srho = slot_sum(fw.s_rho), sfx = slot_sum(fw.s_fx);
+      const T sfy = DIM >= 2 ? slot_sum(fw.s_fy) : T(0), sfz = DIM >= 3 ? slot_sum(fw.s_fz) : T(0);
+      const T sq = slot_sum(fw.s_q);
+      T dm = fw.dmax;
+      if constexpr (EXTRA) {
+#pragma unroll
+        for (int o = kSlotLanes / 2; o > 0; o >>= 1) {
+          const T ot = __shfl_xor_sync(0xffffffffu, dm, o);
+          dm = ot > dm ? ot : dm;
+        }
+      }
+      if (iv) {
+        if (hl == 0) {
+          const int r = (int)(i - g0);
+          const T vals[6] = {srho, sfx, sfy, sfz, sq, dm};
+#pragma unroll
+          for (int qv = 0; qv < 6; ++qv) {
+            if constexpr (MIXED) res[warp][qv][r] = (float)vals[qv];
+            else res64[warp][qv][r] = (double)vals[qv];
+          }
+          res_n[warp][r] = nacc;
+          tf += nacc;
+          tc += (unsigned)cnt;
+        }
+        if (a.K > 0) {                                 // loads per unit, flushed when the unit changes
+          if (ui != unit_run && unit_run >= 0 && hl == 0 && unit_load)
+            atomicAdd(&a.load_acc[unit_run], (unsigned long long)unit_load);
+          if (ui != unit_run) { unit_run = ui; unit_load = 0; }
+          unit_load += nacc;
+        }
+      }
+    }
+    if (a.K > 0 && hl == 0 && unit_run >= 0 && unit_load)
+      atomicAdd(&a.load_acc[unit_run], (unsigned long long)unit_load);
+    __syncwarp();
+    {
+      const int64_t i = g0 + lane;                     // one slot of the group per lane
+      long long key = LLONG_MAX;
+      int bi = 0;
+      if (i < g1) {
+        auto rv = [&](int qv) -> double {
+          if constexpr (MIXED) return (double)res[warp][qv][lane];
+          else return res64[warp][qv][lane];
+        };
+        const int64_t p = a.perm[i];
+        const double drho = 2.0 * a.rho_slot[i] * (rv(0) * a.rscale);
+        const double im = a.fscale / a.m[p];
+        const double acc[3] = {rv(1) * im, DIM >= 2 ? rv(2) * im : 0.0, DIM >= 3 ? rv(3) * im : 0.0};
+        const double dE = rv(4) * im;
+        a.drho[p] = drho;
+        a.ax[p] = acc[0];
+        if (DIM >= 2) a.ay[p] = acc[1];
+        if (DIM >= 3) a.az[p] = acc[2];
+        a.dE[p] = dE;
+        if (EXTRA) a.dmax_nbr[p] = res_n[warp][lane] ? rv(5) : -1.0;
+        if (a.kick2) {
+          if (a.n_inst > 1) {
+            int lo = 0, hi = a.n_inst;
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (a.inst_off[mid] <= i) lo = mid; else hi = mid;
+            }
+            bi = lo;
+          }
+          const double dt = a.kx_dt[bi];
+          const double hdt = 0.5 * dt;
+          double* V[3] = {a.kx_vx, a.kx_vy, a.kx_vz};
+          double v[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) v[c] = V[c][p];
+          const double rho0 = a.kx_rho[p], E0 = a.kx_E[p];
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) v[c] = axpy<MIXED>(hdt, acc[c], v[c]);
+          const double rho = axpy<MIXED>(hdt, drho, rho0);
+          const double E = axpy<MIXED>(hdt, dE, E0);
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) V[c][p] = v[c];
+          a.kx_rho[p] = rho;
+          a.kx_E[p] = E;
+          if (a.kx_t && i == a.inst_off[bi]) a.kx_t[bi] += dt;    // one slot per instance
+          if (a.kick2_cfl) key = cfl_key(a.dp, v[0], v[1], v[2], E, rho, a.m[p], a.kx_mat ? a.kx_mat[p] : 0);
+        }
+      }
+      if (a.kick2_cfl) {
+        // one atomic per warp when the group lies in one instance (the usual case)
+        const int b0 = __shfl_sync(0xffffffffu, bi, 0);
+        if (__all_sync(0xffffffffu, i >= g1 || bi == b0)) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const long long q = __shfl_xor_sync(0xffffffffu, key, o);
+            key = q < key ? q : key;
+          }
+          if (lane == 0) atomicMin(&a.dt_key[b0], key);
+        } else if (i < g1) {
+          atomicMin(&a.dt_key[bi], key);
+        }
+      }
+    }
+    __syncwarp();
+    te = __reduce_add_sync(0xffffffffu, te);
+    tf = __reduce_add_sync(0xffffffffu, tf);
+    tc = __reduce_add_sync(0xffffffffu, tc);
+    if (lane == 0) {
+      atomicAdd(&a.counters[0], (unsigned long long)tf);
+      atomicAdd(&a.counters[1], (unsigned long long)tc);
+      atomicAdd(&a.counters[2], (unsigned long long)te);
+    }
+  }
+}
+
+template <bool MIXED, int DIM, bool HLL, bool EXTRA>
+cudaError_t launch_lists_one(const PairArgs& args, int blocks_per_sm, cudaStream_t st) {
+  static int sms = 0, per_sm = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_lists<MIXED, DIM, HLL, EXTRA>, kPairBlock, 0);
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
+  k_pair_lists<MIXED, DIM, HLL, EXTRA><<<sms * b, kPairBlock, 0, st>>>(args);
+  return cudaGetLastError();
+}
+
+template <bool MIXED, bool HLL, bool EXTRA>
+cudaError_t launch_lists_dim3(sph_handle* h, const PairArgs& args, cudaStream_t st) {
+  const int b = h->p.pair_blocks_per_sm;
+  switch (h->dp.dim) {
+    case 1: return launch_lists_one<MIXED, 1, HLL, EXTRA>(args, b, st);
+    case 2: return launch_lists_one<MIXED, 2, HLL, EXTRA>(args, b, st);
+    default: return launch_lists_one<MIXED, 3, HLL, EXTRA>(args, b, st);
+  }
+}
+
+// The side outputs (neighbour sizes, unit adjacency, pair output) only when
+// this evaluation must produce them.
+template <bool MIXED>
+cudaError_t launch_lists_dim(sph_handle* h, const PairArgs& args, cudaStream_t st) {
+  const bool extra = args.collect_adj || args.pair_i;
+  if (h->solver == SPH_SOLVER_HLL)
+    return extra ? launch_lists_dim3<MIXED, true, true>(h, args, st) : launch_lists_dim3<MIXED, true, false>(h, args, st);
+  return extra ? launch_lists_dim3<MIXED, false, true>(h, args, st) : launch_lists_dim3<MIXED, false, false>(h, args, st);
+}
+
+}  // namespace
+
+// Pair evaluation over the Verlet lists (rates, counters, unit loads).
+cudaError_t launch_pair_lists(sph_handle* h, const sph_state& s, cudaStream_t st, bool kick2, double* t_dev,
+                              bool next_dt) {
+  PairArgs a = make_args(h, s);
+  a.kick2 = kick2 ? 1 : 0;
+  a.kick2_cfl = kick2 && next_dt ? 1 : 0;
+  a.kx_vx = s.vx;
+  a.kx_vy = s.vy;
+  a.kx_vz = s.vz;
+  a.kx_rho = s.rho;
+  a.kx_E = s.E;
+  a.kx_mat = s.mat;
+  a.kx_dt = h->dt;
+  a.kx_t = t_dev;
+  a.dt_key = h->dt_key;
+  a.dp = h->dp;
+  cudaError_t e = cudaMemsetAsync(h->counters, 0, 3 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(&h->counters[5], 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  if ((e = prof_record(h, true, st)) != cudaSuccess) return e;
+  e = h->dp.precision == SPH_PREC_MIXED ? launch_lists_dim<true>(h, a, st) : launch_lists_dim<false>(h, a, st);
+  h->launches += 1;
+  if (e == cudaSuccess) e = prof_record(h, false, st);
+  return e;
+}
+
+}  // namespace csph

@@ -1,0 +1,536 @@
+// pair_common.cuh -- shared by the pair kernels (k_pair.cu: the cell search
+// and its modes; k_pair_lists.cu: the evaluation over the Verlet lists): the
+// launch arguments, the arithmetic helpers, the pair flux accumulator FwdAcc
+// and the host-side argument set-up.  Everything has internal linkage (an
+// unnamed namespace), so each translation unit holds its own copy.
+#pragma once
+
+#include "csph_internal.cuh"
+#include "step_math.cuh"
+
+namespace csph {
+
+namespace {
+
+struct PairArgs {
+  int64_t n;
+  const int64_t* total_cells_dev;
+  int64_t total_cells;   // read from total_cells_dev by the kernel
+  int n_inst;
+  const int64_t* inst_off;
+  const GridInfo* grid;
+  const void* A;
+  const void* B;
+  const void* C;
+  const double* rho_slot;
+  const int32_t* slot_cell;
+  const int32_t* slot_unit;
+  const int32_t* cell_start;
+  const int32_t* perm;
+  // FP64 state for the exact fallback test
+  const double *x, *y, *z, *d;
+  const double* m;
+  // outputs, particle order
+  double *ax, *ay, *az, *drho, *dE;
+  double* dmax_nbr;
+  // work units
+  int K;
+  unsigned long long* load_acc;
+  uint32_t* adj_bits;
+  int adj_words;  // 32-bit words per row
+  unsigned long long* counters;
+  int* status;
+  unsigned long long* work_counter;   // next cell for the persistent warps (zeroed per launch)
+  int collect_adj;   // record unit adjacency in this evaluation
+  int32_t* pair_i;   // optional unordered pair output (particle indices, i < j)
+  int32_t* pair_j;
+  int64_t pair_cap;
+  double kh;
+  float kh_f, eta_half_f, kappa_f;
+  double eta_half, kappa;
+  int kernel;
+  // reverse mode (k_pair<..., VJP = true>): adjoint operands in slot order,
+  // G = ((dL/da)/m, (dL/ddE)/m), GR2 = (dL/ddrho, rho), and the 11 own-side
+  // derivatives per particle (particle order) it writes
+  const void* G;
+  const void* GR2;
+  double* vjp_out;
+  // Verlet lists (k_pair in list mode writes them, k_pair_lists reads them)
+  uint32_t* vlist;   // [n][vcap]: (slot j << 5) | neighbour-cell code, particle-major
+  int32_t* vcnt;
+  double* vref;      // x, y, z, d per particle at the build (4 arrays of n)
+  int* vflag;        // [0] rebuild now, [1] lists invalid, [2] builds done
+  int vcap;
+  // order-2 reconstruction: SPH gradients in slot order, the kernel's precision;
+  // gP: grad P; gV: grad v_x, grad v_y, grad v_z (three arrays of n, consecutive)
+  void* gP;
+  void* gV;
+  // mixed precision: the packed volume is V' = V vscale and W' is used as
+  // W'' = W' wscale (both powers of two chosen by sph_init), so that the FP32
+  // products stay in the normal range at any length scale; fscale =
+  // 2 / (vscale^2 wscale) undoes them in FP64 and applies the factor 2 of the
+  // momentum and energy fluxes, rscale = 1 / (vscale wscale),
+  // vinv = 1 / vscale.  In FP64 mode the scales are 1 (fscale 2).
+  float wscale_f;
+  double fscale, rscale, vinv;
+  // second half kick fused into the list kernel's rate write (k_pair_lists):
+  // v, rho, E advanced by dt/2 with the new rates (the arithmetic of k_kick2),
+  // the instance time advanced by dt, and with kick2_cfl the CFL keys of the
+  // new state min-reduced into dt_key[instance] for the next step
+  int kick2, kick2_cfl;
+  double *kx_vx, *kx_vy, *kx_vz, *kx_rho, *kx_E;
+  const int32_t* kx_mat;
+  const double* kx_dt;
+  double* kx_t;
+  long long* dt_key;
+  DevParams dp;
+};
+
+constexpr int kModeFwd = 0;    // rates
+constexpr int kModeVjp = 1;    // reverse mode of the rates
+constexpr int kModeList = 2;   // Verlet list build over the (1 + beta) radius
+constexpr int kModeGrad = 3;   // SPH gradients of P and v (order-2 reconstruction)
+constexpr int kModeFwd2 = 4;   // rates with states reconstructed to the pair midpoint
+
+template <bool MIXED>
+struct Ops;
+
+template <>
+struct Ops<true> {
+  using T = float;
+  using V4 = float4;
+  using V2 = float2;
+};
+
+template <>
+struct Ops<false> {
+  using T = double;
+  using V4 = D4;
+  using V2 = D2;
+};
+
+template <typename T>
+struct Kahan {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T v) {
+    T y = v - c;
+    T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+template <>
+struct Kahan<double> {  // FP64 sums need no compensation at these sizes
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+};
+
+// Reciprocal and reciprocal square root: FP32 uses the fast hardware
+// approximations (relative error ~1e-7, far inside the 1e-4 tolerance of the
+// mixed path); FP64 keeps correctly rounded operations.
+__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
+
+__device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+// Uncontracted arithmetic for the expressions whose exchange symmetry must
+// hold bit for bit (the compiler may not fuse these into FMAs).
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Exact FP64 interaction test on the global positions, operation order of the oracle.
+__device__ __forceinline__ bool exact_accept(const PairArgs& a, int dim, int64_t pi, int64_t pj) {
+  double dx = __dsub_rn(a.x[pj], a.x[pi]);
+  double r2 = __dmul_rn(dx, dx);
+  if (dim >= 2) { double dy = __dsub_rn(a.y[pj], a.y[pi]); r2 = __dadd_rn(r2, __dmul_rn(dy, dy)); }
+  if (dim >= 3) { double dz = __dsub_rn(a.z[pj], a.z[pi]); r2 = __dadd_rn(r2, __dmul_rn(dz, dz)); }
+  double R = __dmul_rn(a.kh, __dadd_rn(a.d[pi], a.d[pj]));
+  return r2 < __dmul_rn(R, R);
+}
+
+// dW/dr of the cubic spline (support 2h) or Wendland C2 (support kappa h)
+// with the reciprocals above, times ws, a power of two folded into the
+// normalisation constant (so the result is exactly ws times the unscaled
+// value: the mixed path's W'' = W' wscale at no extra multiply).
+template <typename T, int DIM>
+__device__ __forceinline__ T dw_fast(int kernel, T kappa, T r, T h, T ws) {
+  const T pi = T(3.14159265358979323846);
+  if (kernel == SPH_KERNEL_CUBIC) {
+    const T ih = rcp_(h);
+    const T q = r * ih;
+    T norm;
+    if (DIM == 1) norm = (T(2.0 / 3.0) * ws) * ih * ih;
+    else if (DIM == 2) norm = (T(10.0 / (7.0 * 3.14159265358979323846)) * ws) * ih * ih * ih;
+    else norm = (T(1.0 / 3.14159265358979323846) * ws) * (ih * ih) * (ih * ih);
+    const T t = T(2) - q;
+    const T f_in = q * (T(2.25) * q - T(3));
+    const T f_out = T(-0.75) * t * t;
+    const T f = q < T(1) ? f_in : (q < T(2) ? f_out : T(0));   // selects, no divergence
+    return norm * f;
+  } else {
+    const T iH = rcp_(kappa * h);
+    const T s = r * iH;
+    if (s >= T(1)) return T(0);
+    const T t = T(1) - s;
+    if (DIM == 1) return (T(1.25) * ws) * iH * iH * (T(-12) * s * t * t);
+    const T norm = (DIM == 2) ? (T(7) / pi * ws) * iH * iH * iH : (T(21) / (T(2) * pi) * ws) * (iH * iH) * (iH * iH);
+    return norm * (T(-20) * s * t * t * t);
+  }
+}
+
+// Cubic spline W'(r, h) = s h^-(D+1) g(q) and its derivatives
+// dW'/dr = s h^-(D+2) g'(q), dW'/dh = s h^-(D+2) (-(D+1) g - q g'), q = r/h.
+template <typename T, int DIM>
+__device__ __forceinline__ void cubic_dw3(T r, T h, T& w, T& wr, T& wh) {
+  const T ih = rcp_(h);
+  const T q = r * ih;
+  T norm;
+  if (DIM == 1) norm = T(2.0 / 3.0) * ih * ih;
+  else if (DIM == 2) norm = T(10.0 / (7.0 * 3.14159265358979323846)) * ih * ih * ih;
+  else norm = T(1.0 / 3.14159265358979323846) * (ih * ih) * (ih * ih);
+  const T t = T(2) - q;
+  const T g = q < T(1) ? q * (T(2.25) * q - T(3)) : (q < T(2) ? T(-0.75) * t * t : T(0));
+  const T gp = q < T(1) ? T(4.5) * q - T(3) : (q < T(2) ? T(1.5) * t : T(0));
+  w = norm * g;
+  const T nh = norm * ih;
+  wr = nh * gp;
+  wh = nh * (T(-(DIM + 1)) * g - q * gp);
+}
+
+template <bool MIXED, int DIM>
+struct Pair {
+  using T = typename Ops<MIXED>::T;
+  using V4 = typename Ops<MIXED>::V4;
+  using V2 = typename Ops<MIXED>::V2;
+
+  // Canonical separation lo -> hi.  sh: shift from i's cell to j's cell (mixed only).
+  static __device__ __forceinline__ void sep(bool ilo, const V4& Ai, const V4& Aj, T sx, T sy, T sz, T& dx,
+                                             T& dy, T& dz) {
+    const V4& lo = ilo ? Ai : Aj;
+    const V4& hi = ilo ? Aj : Ai;
+    if (MIXED) {
+      T s0 = ilo ? sx : -sx, s1 = ilo ? sy : -sy, s2 = ilo ? sz : -sz;
+      dx = (hi.x + s0) - lo.x;
+      dy = DIM >= 2 ? (hi.y + s1) - lo.y : T(0);
+      dz = DIM >= 3 ? (hi.z + s2) - lo.z : T(0);
+    } else {
+      dx = __dsub_rn(hi.x, lo.x);
+      dy = DIM >= 2 ? __dsub_rn(hi.y, lo.y) : 0.0;
+      dz = DIM >= 3 ? __dsub_rn(hi.z, lo.z) : 0.0;
+    }
+  }
+
+  static __device__ __forceinline__ T r2_of(T dx, T dy, T dz) {
+    if (MIXED) {
+      T r2 = dx * dx;
+      if (DIM >= 2) r2 = fmaf(dy, dy, r2);
+      if (DIM >= 3) r2 = fmaf(dz, dz, r2);
+      return r2;
+    } else {
+      T r2 = __dmul_rn(dx, dx);
+      if (DIM >= 2) r2 = __dadd_rn(r2, __dmul_rn(dy, dy));
+      if (DIM >= 3) r2 = __dadd_rn(r2, __dmul_rn(dz, dz));
+      return r2;
+    }
+  }
+};
+
+// Flux of the interacting pair (i, j) from i's side.  Every quantity
+// that j computes for the same pair is the exact negative (e^R, v^R, v*,
+// momentum and energy fluxes) or the exact same value (r, P*, h_ij, W'):
+// dx = (off_j - off_i) + shift is the rounded negative of j's
+// (off_i - off_j) - shift, IEEE rounding is sign-symmetric, and the sums
+// that mix i and j are written with uncontracted operations in an order
+// that is symmetric under the exchange.  So the applied fluxes are
+// antisymmetric bit for bit and momentum and energy are conserved by the
+// pair sums up to the per-particle summation.
+//
+// Order 2 (ORDER2): P and v^R are extrapolated from each particle to the pair
+// midpoint with the SPH gradients, each increment limited by minmod against
+// the pair jump (q_L = q_i + minmod(r e.grad q_i, q_j - q_i)/2, q_R = q_j -
+// minmod(r e.grad q_j, q_j - q_i)/2, e.grad v^R = e.(grad v).e), and the
+// acoustic solver takes (P_L, v_L; P_R, v_R).  Written with the same
+// uncontracted, sign-symmetric operations, j's side sees exactly (P_R, P_L,
+// -v_R, -v_L), so the antisymmetry is kept.
+template <typename T>
+__device__ __forceinline__ T minmod(T a, T b) {
+  return (a > T(0) && b > T(0)) ? (a < b ? a : b) : ((a < T(0) && b < T(0)) ? (a > b ? a : b) : T(0));
+}
+
+// EXTRA: also the side outputs of an evaluation, i.e. the largest neighbour
+// size, the unit adjacency and the optional pair output.  Only the
+// evaluations that feed a rebalance or a pair query need them, and leaving
+// them out of the pair loop saves ~10 % of the list kernel.
+template <bool MIXED, int DIM, bool ORDER2 = false, bool HLL = false, bool EXTRA = true>
+struct FwdAcc {
+  using P = Pair<MIXED, DIM>;
+  using T = typename P::T;
+  using V4 = typename P::V4;
+  using V2 = typename P::V2;
+  Kahan<T> s_rho, s_fx, s_fy, s_fz, s_q;
+  T dmax = T(0);
+  int last_adj = -1;
+  V4 gPi{}, gVi[3]{};   // order 2: i's gradients (set by the caller)
+
+  // e . g, in a fixed uncontracted order (sign-symmetric in e)
+  static __device__ __forceinline__ T dot_e(const V4& g, T ex, T ey, T ez) {
+    T s = mul_(g.x, ex);
+    if (DIM >= 2) s = fma_(g.y, ey, s);
+    if (DIM >= 3) s = fma_(g.z, ez, s);
+    return s;
+  }
+  // e . (grad v) . e  (even in e)
+  static __device__ __forceinline__ T dvv(const V4* gv, T ex, T ey, T ez) {
+    T s = mul_(ex, dot_e(gv[0], ex, ey, ez));
+    if (DIM >= 2) s = fma_(ey, dot_e(gv[1], ex, ey, ez), s);
+    if (DIM >= 3) s = fma_(ez, dot_e(gv[2], ex, ey, ez), s);
+    return s;
+  }
+
+  __device__ __forceinline__ void pair(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi, const V2& Ci,
+                                       int ui, int64_t j, T sx, T sy, T sz) {
+    const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
+    const V4* __restrict__ B = reinterpret_cast<const V4*>(a.B);
+    const V2* __restrict__ C = reinterpret_cast<const V2*>(a.C);
+    if (j == i) return;       // the scan keeps the self pair (r = 0); it has no flux
+    const V4 Aj = A[j];
+    const V4 Bj = B[j];
+    const V2 Cj = C[j];
+    T dx, dy, dz;
+    separation(Ai, Aj, sx, sy, sz, dx, dy, dz);
+    flux_at(a, i, Ai, Bi, Ci, ui, j, Aj, Bj, Cj, dx, dy, dz, P::r2_of(dx, dy, dz));
+  }
+
+  // x_j - x_i of the flux (mixed: FP32 offsets plus the cell shift, in an
+  // order that j's side negates exactly)
+  static __device__ __forceinline__ void separation(const V4& Ai, const V4& Aj, T sx, T sy, T sz, T& dx, T& dy,
+                                                    T& dz) {
+    if (MIXED) {
+      dx = (Aj.x - Ai.x) + sx;
+      dy = DIM >= 2 ? (Aj.y - Ai.y) + sy : T(0);
+      dz = DIM >= 3 ? (Aj.z - Ai.z) + sz : T(0);
+    } else {
+      dx = __dsub_rn(Aj.x, Ai.x);
+      dy = DIM >= 2 ? __dsub_rn(Aj.y, Ai.y) : 0.0;
+      dz = DIM >= 3 ? __dsub_rn(Aj.z, Ai.z) : 0.0;
+    }
+  }
+
+  // A listed candidate j of slot i (never i itself): the interaction test of
+  // the scan, then the flux of an interacting pair.  Mixed: FP32 test on the
+  // flux's own separation, decided in FP64 (oracle order) within the band
+  // |r^2 - (kappa h_ij)^2| <= band, where FP32 rounding could flip it; FP64:
+  // the oracle's test.  Returns whether the pair interacts.
+  __device__ __forceinline__ bool pair_listed(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi,
+                                              const V2& Ci, int ui, int64_t j, T sx, T sy, T sz, T khdi,
+                                              float band, unsigned& nexact) {
+    const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
+    const V4* __restrict__ B = reinterpret_cast<const V4*>(a.B);
+    const V2* __restrict__ C = reinterpret_cast<const V2*>(a.C);
+    const V4 Aj = A[j];
+    const V4 Bj = B[j];       // requested with A[j]: most candidates interact
+    const V2 Cj = C[j];
+    T dx, dy, dz;
+    separation(Ai, Aj, sx, sy, sz, dx, dy, dz);
+    const T r2 = P::r2_of(dx, dy, dz);
+    bool acc;
+    if (MIXED) {
+      const T R = fmaf((T)a.kh_f, Aj.w, khdi);
+      const T diff = fmaf(-R, R, r2);
+      acc = diff < T(0);
+      if (fabsf(diff) <= band) {
+        ++nexact;
+        acc = exact_accept(a, DIM, a.perm[i], a.perm[j]);
+      }
+    } else {
+      T ex, ey, ez;
+      P::sep(true, Ai, Aj, T(0), T(0), T(0), ex, ey, ez);   // x_j - x_i, oracle order
+      const double R = __dmul_rn(a.kh, __dadd_rn(Ai.w, Aj.w));
+      acc = P::r2_of(ex, ey, ez) < __dmul_rn(R, R);
+    }
+    if (acc) flux_at(a, i, Ai, Bi, Ci, ui, j, Aj, Bj, Cj, dx, dy, dz, r2);
+    return acc;
+  }
+
+  __device__ __forceinline__ void flux_at(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi, const V2& Ci,
+                                          int ui, int64_t j, const V4& Aj, const V4& Bj, const V2& Cj, T dx, T dy,
+                                          T dz, T r2) {
+    if constexpr (EXTRA) dmax = Aj.w > dmax ? Aj.w : dmax;
+    if (!(r2 > T(0))) return;  // coincident particles: no direction, no flux
+    const T ir = rsqrt_(r2);
+    const T r = r2 * ir;
+    const T ex = dx * ir, ey = dy * ir, ez = dz * ir;
+    T vi = Bi.x * ex, vj = Bj.x * ex;
+    if (DIM >= 2) { vi = fma_(Bi.y, ey, vi); vj = fma_(Bj.y, ey, vj); }
+    if (DIM >= 3) { vi = fma_(Bi.z, ez, vi); vj = fma_(Bj.z, ez, vj); }
+    T Zi = Ci.y, Zj = Cj.y;
+    // HLL with Davis speeds -+max(Z_i, Z_j) is the acoustic state with both
+    // impedances set to that maximum (exchange-symmetric, so the flux keeps
+    // its bitwise antisymmetry)
+    if constexpr (HLL) { const T Zm = Zi > Zj ? Zi : Zj; Zi = Zm; Zj = Zm; }
+    T Pi = Ci.x, Pj = Cj.x, wi = vi, wj = vj;   // states fed to the solver
+    if constexpr (ORDER2) {
+      const V4* __restrict__ GP = reinterpret_cast<const V4*>(a.gP);
+      const V4* __restrict__ GV = reinterpret_cast<const V4*>(a.gV);
+      V4 gvj[3];
+      gvj[0] = GV[j];
+      if (DIM >= 2) gvj[1] = GV[a.n + j];
+      if (DIM >= 3) gvj[2] = GV[2 * a.n + j];
+      const T dP = sub_(Pj, Pi), dv = sub_(vj, vi);
+      const T sPi = mul_(r, dot_e(gPi, ex, ey, ez)), sPj = mul_(r, dot_e(GP[j], ex, ey, ez));
+      const T svi = mul_(r, dvv(gVi, ex, ey, ez)), svj = mul_(r, dvv(gvj, ex, ey, ez));
+      Pi = add_(Ci.x, mul_(T(0.5), minmod(sPi, dP)));
+      Pj = sub_(Cj.x, mul_(T(0.5), minmod(sPj, dP)));
+      wi = add_(vi, mul_(T(0.5), minmod(svi, dv)));
+      wj = sub_(vj, mul_(T(0.5), minmod(svj, dv)));
+    }
+    const T zs = add_(Zi, Zj);
+    T Ps, vs;
+    if (zs > T(0)) {
+      const T izs = rcp_(zs);
+      Ps = mul_(add_(add_(mul_(Zj, Pi), mul_(Zi, Pj)), mul_(mul_(Zi, Zj), sub_(wi, wj))), izs);
+      vs = mul_(add_(add_(mul_(Zi, wi), mul_(Zj, wj)), sub_(Pi, Pj)), izs);
+    } else {
+      Ps = mul_(T(0.5), add_(Pi, Pj));
+      vs = mul_(T(0.5), add_(wi, wj));
+    }
+    const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * add_(Ai.w, Aj.w);
+    const T dW = MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij, (T)a.wscale_f)
+                       : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij);
+    // momentum flux along e, without its factor 2 (carried by fscale; exact)
+    const T F = mul_(mul_(mul_(Bi.w, Bj.w), Ps), dW);
+    s_rho.add(Bj.w * (vi - vs) * (-dW));
+    s_fx.add(mul_(F, ex));
+    if (DIM >= 2) s_fy.add(mul_(F, ey));
+    if (DIM >= 3) s_fz.add(mul_(F, ez));
+    s_q.add(mul_(F, vs));
+    if constexpr (!EXTRA) return;
+    if (a.pair_i) {
+      const int32_t pi = a.perm[i], pj = a.perm[j];
+      if (pi < pj) {
+        const unsigned long long q = atomicAdd(&a.counters[4], 1ull);
+        if ((int64_t)q < a.pair_cap) { a.pair_i[q] = pi; a.pair_j[q] = pj; }
+      }
+    }
+    if (a.collect_adj) {
+      const int uj = a.slot_unit[j];
+      if (uj != ui && uj != last_adj) {
+        atomicOr(&a.adj_bits[ui * a.adj_words + (uj >> 5)], 1u << (uj & 31));
+        last_adj = uj;
+      }
+    }
+  }
+
+  // Rates of home slot i (particle perm[i]) from the sums; nfull: its interacting pairs.
+  __device__ __forceinline__ void write(const PairArgs& a, int64_t i, unsigned nfull) const {
+    const int64_t p = a.perm[i];
+    a.drho[p] = 2.0 * a.rho_slot[i] * ((double)s_rho.s * a.rscale);
+    const double im = a.fscale / a.m[p];
+    a.ax[p] = (double)s_fx.s * im;
+    if (DIM >= 2) a.ay[p] = (double)s_fy.s * im;
+    if (DIM >= 3) a.az[p] = (double)s_fz.s * im;
+    a.dE[p] = (double)s_q.s * im;
+    if (EXTRA) a.dmax_nbr[p] = nfull ? (double)dmax : -1.0;
+  }
+};
+
+// Pair counters and work-unit loads (full-list pairs per unit), aggregated per warp.
+__device__ __forceinline__ void warp_counters(const PairArgs& a, bool act, unsigned nfull, unsigned ncand,
+                                              unsigned nexact, int ui, int lane) {
+  const unsigned tf = __reduce_add_sync(0xffffffffu, act ? nfull : 0u);
+  const unsigned tc = __reduce_add_sync(0xffffffffu, ncand);
+  const unsigned te = __reduce_add_sync(0xffffffffu, nexact);
+  if (lane == 0) {
+    atomicAdd(&a.counters[0], (unsigned long long)tf);
+    atomicAdd(&a.counters[1], (unsigned long long)tc);
+    atomicAdd(&a.counters[2], (unsigned long long)te);
+  }
+  if (a.K > 0) {
+    const int u0 = __shfl_sync(0xffffffffu, ui, 0);
+    if (__all_sync(0xffffffffu, !act || ui == u0)) {
+      if (lane == 0) atomicAdd(&a.load_acc[u0], (unsigned long long)tf);
+    } else if (act) {
+      atomicAdd(&a.load_acc[ui], (unsigned long long)nfull);
+    }
+  }
+}
+
+constexpr int kWarps = kPairBlock / 32;
+
+// CUDA events around a pair-kernel launch when profiling (sph_profile).
+cudaError_t prof_record(sph_handle* h, bool start, cudaStream_t st) {
+  if (!h->profiling) return cudaSuccess;
+  if (start && h->prof_used + 2 > h->prof_events.size()) {
+    for (int k = 0; k < 64; ++k) {
+      cudaEvent_t ev;
+      cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return e;
+      h->prof_events.push_back(ev);
+    }
+  }
+  return cudaEventRecord(h->prof_events[h->prof_used++], st);
+}
+
+PairArgs make_args(sph_handle* h, const sph_state& s) {
+  PairArgs a{};
+  a.n = h->n;
+  a.total_cells_dev = h->total_cells;
+  a.total_cells = 0;
+  a.n_inst = h->n_inst;
+  a.inst_off = h->inst_off;
+  a.grid = h->grid;
+  a.A = h->packA;
+  a.B = h->packB;
+  a.C = h->packC;
+  a.rho_slot = h->rho_slot;
+  a.slot_cell = h->slot_cell;
+  a.slot_unit = h->slot_unit;
+  a.cell_start = h->cell_start;
+  a.perm = h->perm;
+  a.x = s.x; a.y = s.y; a.z = s.z; a.d = s.d; a.m = s.m;
+  a.ax = s.ax; a.ay = s.ay; a.az = s.az; a.drho = s.drho; a.dE = s.dE;
+  a.dmax_nbr = h->dmax_nbr;
+  a.K = h->K;
+  a.load_acc = h->load_acc;
+  a.adj_bits = h->adj_bits;
+  a.adj_words = (h->K + 31) / 32;
+  a.counters = h->counters;
+  a.work_counter = &h->counters[5];
+  a.status = h->status;
+  a.collect_adj = (h->K > 0 && h->collect_adj) ? 1 : 0;
+  a.pair_i = h->pair_out_i;
+  a.pair_j = h->pair_out_j;
+  a.pair_cap = h->pair_out_cap;
+  a.kh = h->dp.kh;
+  a.kh_f = (float)h->dp.kh;
+  a.eta_half = h->dp.eta * 0.5;
+  a.eta_half_f = (float)(h->dp.eta * 0.5);
+  a.kappa = h->dp.kappa;
+  a.kappa_f = (float)h->dp.kappa;
+  a.kernel = h->dp.kernel;
+  a.vlist = h->vlist;
+  a.vcnt = h->vcnt;
+  a.vref = h->vref;
+  a.vflag = h->vflag;
+  a.vcap = h->vcap;
+  a.gP = h->grad_p;
+  a.gV = h->grad_v;
+  a.wscale_f = (float)h->wscale;
+  a.fscale = 2.0 / (h->vscale * h->vscale * h->wscale);   // with the factor 2 of the momentum flux
+  a.rscale = 1.0 / (h->vscale * h->wscale);
+  a.vinv = 1.0 / h->vscale;
+  return a;
+}
+
+}  // namespace
+
+}  // namespace csph
