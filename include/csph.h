@@ -53,6 +53,11 @@ extern "C" {
 #define SPH_SOLVER_HLL 1       /* two-wave HLL state of the same linearised problem with Davis speeds
                                   -+max(Z_i, Z_j): the acoustic formula with both Z set to max(Z_i, Z_j) */
 
+#define SPH_LOAD_PAIRS 0       /* work-unit load L_k: the pair interactions of unit k (deterministic) */
+#define SPH_LOAD_TIME 1        /* L_k: the useful time t^u_k of eq. (load), here the SM cycles the pair
+                                  kernel spends on unit k's particles (timing-dependent, so the
+                                  rebalancing is not reproducible bit for bit) */
+
 #define SPH_MAX_MAT 4
 #define SPH_MAX_UNITS 256
 
@@ -95,6 +100,8 @@ typedef struct sph_params {
                          2: P and v^R extrapolated to the pair midpoint with SPH gradients, minmod-
                          limited against the pair jump (an extension; needs cell_beta = 0, no adjoint) */
   int32_t solver;     /* SPH_SOLVER_*: the pair Riemann solver (HLL: no adjoint) */
+  int32_t load_measure; /* SPH_LOAD_*: what the work-unit loads of the balancing count */
+  int32_t pad3_;
 } sph_params;
 
 /* Particle state: structure of arrays in device memory, n elements each.
@@ -228,7 +235,8 @@ int sph_last_dt(sph_handle* h, double* dt_out, void* stream);
 int sph_conservation(sph_handle* h, const sph_state* s, double* out, void* stream);
 
 /* Host-side copy of the balancing accumulators (for inspection and tests):
- * load_out (host, K doubles, pair counts with 1/2 per crossing end) and
+ * load_out (host, K doubles: pair counts with 1/2 per crossing end, or with
+ * SPH_LOAD_TIME half the accumulated SM cycles) and
  * adj_out (host, K*K bytes, 0/1).  Synchronises the stream. */
 int sph_unit_stats(sph_handle* h, double* load_out, uint8_t* adj_out, void* stream);
 

@@ -17,6 +17,7 @@ SPH_KERNEL_CUBIC, SPH_KERNEL_WENDLAND_C2 = 0, 1
 SPH_EOS_IDEAL, SPH_EOS_STIFFENED, SPH_EOS_TAIT, SPH_EOS_MIE_GRUNEISEN = 0, 1, 2, 3
 SPH_PREC_FP64, SPH_PREC_MIXED = 0, 1
 SPH_SOLVER_ACOUSTIC, SPH_SOLVER_HLL = 0, 1
+SPH_LOAD_PAIRS, SPH_LOAD_TIME = 0, 1
 SPH_MAX_MAT, SPH_MAX_UNITS = 4, 256
 
 ERROR_NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID", 2: "SPH_ERR_CAPACITY", 3: "SPH_ERR_NONFINITE",
@@ -41,7 +42,8 @@ class sph_params(C.Structure):
                 ("n_units", C.c_int32), ("unit_dim", C.c_int32), ("n_upd", C.c_int32), ("pair_blocks_per_sm", C.c_int32),
                 ("theta", C.c_double), ("sigma", C.c_double), ("gamma_b", C.c_double), ("beta_sh", C.c_double),
                 ("generators", C.c_void_p), ("materials", C.c_void_p),
-                ("order", C.c_int32), ("solver", C.c_int32)]
+                ("order", C.c_int32), ("solver", C.c_int32),
+                ("load_measure", C.c_int32), ("pad3_", C.c_int32)]
 
 
 STATE_F64 = ("x", "y", "z", "vx", "vy", "vz", "rho", "E", "m")

@@ -123,6 +123,8 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     return fail(nullptr, SPH_ERR_INVALID, "order 2 runs with the per-step neighbour search (cell_beta = 0)");
   if (p->solver != SPH_SOLVER_ACOUSTIC && p->solver != SPH_SOLVER_HLL)
     return fail(nullptr, SPH_ERR_INVALID, "unknown pair solver");
+  if (p->load_measure != SPH_LOAD_PAIRS && p->load_measure != SPH_LOAD_TIME)
+    return fail(nullptr, SPH_ERR_INVALID, "unknown load measure");
   if (p->n_mat < 1 || p->n_mat > kMaxMaterials || (p->n_mat > SPH_MAX_MAT && !p->materials))
     return fail(nullptr, SPH_ERR_INVALID, "n_mat out of range (more than SPH_MAX_MAT need params.materials)");
   const sph_material* mats = p->materials ? p->materials : p->mat;
@@ -284,6 +286,7 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   // order-2 reconstruction: SPH gradients of P and v in slot order
   h->order2 = p->order == 2;
   h->solver = p->solver;
+  h->load_timed = p->load_measure == SPH_LOAD_TIME;
   if (h->order2) {
     if (p->precision == SPH_PREC_MIXED) {
       CKI(dalloc(reinterpret_cast<float4**>(&h->grad_p), n));

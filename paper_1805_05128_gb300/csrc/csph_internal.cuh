@@ -173,6 +173,7 @@ struct sph_handle {
   // the pair kernel's precision: grad P, then grad v_x, grad v_y, grad v_z
   bool order2 = false;
   int solver = SPH_SOLVER_ACOUSTIC;
+  bool load_timed = false;           // SPH_LOAD_TIME: unit loads in SM cycles
 
   // mixed precision: scales (powers of two) of the packed volume and of W', set
   // by sph_init from the largest particle volume (1 in FP64 mode)

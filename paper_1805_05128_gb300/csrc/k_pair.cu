@@ -10,7 +10,11 @@
 // of the candidate test.
 //
 // Antisymmetry: the momentum flux F_ij e^R and energy flux Q_ij that i and
-// j apply are bitwise negatives of each other (see pair_flux).
+// j apply are bitwise negatives of each other (FwdAcc in pair_common.cuh).
+//
+// Modes of the kernel: the rates (optionally with order-2 states), the SPH
+// gradients of order 2, the reverse mode, and the Verlet list build; the
+// evaluation over the lists is k_pair_lists.cu.
 //
 // Mixed precision: the candidate test and the flux run in FP32 on offsets
 // from each particle's own cell origin (FP32 keeps ~7 digits of a cell edge,
@@ -116,6 +120,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
   }
 
   for (int h0 = hs; h0 < he; h0 += 32) {
+    const long long t_start = a.load_timed ? clock64() : 0;   // timed unit loads
     const int i = h0 + lane;
     const bool act = i < he;
     const int nh = min(32, he - h0);
@@ -470,7 +475,8 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
       nfull -= 1;   // the self pair
       fw.write(a, i, nfull);
     }
-    warp_counters(a, act, nfull, ncand, nexact, ui, lane);
+    warp_counters(a, act, nfull, ncand, nexact, ui, lane,
+                  a.load_timed ? (unsigned)(clock64() - t_start) : 0u);
     __syncwarp();   // the home buffer is rewritten by the next chunk of home particles
   }
   __syncwarp();     // the neighbour-start buffer is rewritten by the next cell

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
       cnt_pre = a.vcnt[g0 + half];
     }
     for (int q = 0; g0 + kSlotsPerWarp * q < g1; ++q) {   // warp-uniform
+      const long long t_start = a.load_timed ? clock64() : 0;
       const int64_t i = g0 + kSlotsPerWarp * q + half;       // this group's slot
       const bool iv = i < g1;                                // uniform in the group
       const int cnt = iv ? cnt_pre : 0;
@@ -167,7 +168,8 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
           if (ui != unit_run && unit_run >= 0 && hl == 0 && unit_load)
             atomicAdd(&a.load_acc[unit_run], (unsigned long long)unit_load);
           if (ui != unit_run) { unit_run = ui; unit_load = 0; }
-          unit_load += nacc;
+          // timed loads: the iteration's SM cycles (the eight slots share them)
+          unit_load += a.load_timed ? (unsigned)((clock64() - t_start) / kSlotsPerWarp) : nacc;
         }
       }
     }

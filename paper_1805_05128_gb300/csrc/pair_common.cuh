@@ -42,6 +42,7 @@ struct PairArgs {
   int* status;
   unsigned long long* work_counter;   // next cell for the persistent warps (zeroed per launch)
   int collect_adj;   // record unit adjacency in this evaluation
+  int load_timed;    // unit loads in SM cycles (SPH_LOAD_TIME) instead of pair counts
   int32_t* pair_i;   // optional unordered pair output (particle indices, i < j)
   int32_t* pair_j;
   int64_t pair_cap;
@@ -444,8 +445,10 @@ struct FwdAcc {
 };
 
 // Pair counters and work-unit loads (full-list pairs per unit), aggregated per warp.
+// With timed loads, cyc is the SM cycles the warp spent on its home chunk,
+// shared evenly by the chunk's particles.
 __device__ __forceinline__ void warp_counters(const PairArgs& a, bool act, unsigned nfull, unsigned ncand,
-                                              unsigned nexact, int ui, int lane) {
+                                              unsigned nexact, int ui, int lane, unsigned cyc = 0) {
   const unsigned tf = __reduce_add_sync(0xffffffffu, act ? nfull : 0u);
   const unsigned tc = __reduce_add_sync(0xffffffffu, ncand);
   const unsigned te = __reduce_add_sync(0xffffffffu, nexact);
@@ -456,10 +459,12 @@ __device__ __forceinline__ void warp_counters(const PairArgs& a, bool act, unsig
   }
   if (a.K > 0) {
     const int u0 = __shfl_sync(0xffffffffu, ui, 0);
+    const unsigned nact = __popc(__ballot_sync(0xffffffffu, act));
+    const unsigned mine = a.load_timed ? (nact ? cyc / nact : 0u) : nfull;
     if (__all_sync(0xffffffffu, !act || ui == u0)) {
-      if (lane == 0) atomicAdd(&a.load_acc[u0], (unsigned long long)tf);
+      if (lane == 0) atomicAdd(&a.load_acc[u0], (unsigned long long)(a.load_timed ? mine * nact : tf));
     } else if (act) {
-      atomicAdd(&a.load_acc[ui], (unsigned long long)nfull);
+      atomicAdd(&a.load_acc[ui], (unsigned long long)mine);
     }
   }
 }
@@ -507,6 +512,7 @@ PairArgs make_args(sph_handle* h, const sph_state& s) {
   a.work_counter = &h->counters[5];
   a.status = h->status;
   a.collect_adj = (h->K > 0 && h->collect_adj) ? 1 : 0;
+  a.load_timed = h->load_timed ? 1 : 0;
   a.pair_i = h->pair_out_i;
   a.pair_j = h->pair_out_j;
   a.pair_cap = h->pair_out_cap;
