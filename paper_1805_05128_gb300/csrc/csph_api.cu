@@ -242,7 +242,7 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   if (p->precision == SPH_PREC_MIXED) {
     CKI(dalloc(reinterpret_cast<float4**>(&h->packA), n));
     CKI(dalloc(reinterpret_cast<float4**>(&h->packB), n));
-    CKI(dalloc(reinterpret_cast<float2**>(&h->packC), n));
+    CKI(dalloc(reinterpret_cast<float4**>(&h->packC), n));
   } else {
     CKI(dalloc(reinterpret_cast<D4**>(&h->packA), n));
     CKI(dalloc(reinterpret_cast<D4**>(&h->packB), n));

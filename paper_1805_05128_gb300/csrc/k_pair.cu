@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
   using T = typename P::T;
   using V4 = typename P::V4;
   using V2 = typename P::V2;
+  using VC = typename P::VC;
   constexpr int kCap = MODE == kModeList ? kBuildCap : kListCap;
   __shared__ uint16_t list[kWarps][32][kCap + 2];           // [warp][home particle][entry]
   __shared__ V4 home[kWarps][LIST ? 1 : 32];                 // home particles: x, y, z, kh d (mixed) or d (FP64)
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
   const int64_t total = *a.total_cells_dev;
   const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
   const V4* __restrict__ B = reinterpret_cast<const V4*>(a.B);
-  const V2* __restrict__ C = reinterpret_cast<const V2*>(a.C);
+  const VC* __restrict__ C = reinterpret_cast<const VC*>(a.C);
   if constexpr (LIST) {
     if (a.vflag[0] == 0) return;                 // lists still valid: nothing to build
     if (blockIdx.x == 0 && threadIdx.x == 0) { a.vflag[1] = 0; a.vflag[2] += 1; }
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
     unsigned nfull = 0, ncand = 0, nexact = 0;
     const int ui = a.K > 0 ? a.slot_unit[ii] : 0;
     const V4 Bi = B[ii];
-    const V2 Ci = C[ii];
+    const VC Ci = C[ii];
     // reverse mode: i's adjoint operands and the 11 own-side sums
     const V4* __restrict__ Gp = reinterpret_cast<const V4*>(a.G);
     const V2* __restrict__ Rp = reinterpret_cast<const V2*>(a.GR2);
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
       if (j == i) return;
       const V4 Aj = A[j];
       const V4 Bj = B[j];
-      const V2 Cj = C[j];
+      const VC Cj = C[j];
       T dx, dy, dz;
       if (MIXED) {
         dx = (Aj.x - Ai.x) + sx;
@@ -183,7 +184,16 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
                           : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij));
       const T f = Bj.w * w;
       const T dP = Cj.x - Ci.x;
-      const T dv[3] = {Bj.x - Bi.x, Bj.y - Bi.y, Bj.z - Bi.z};
+      T dv[3];
+      if constexpr (MIXED) {   // relative velocities plus the exact reference difference
+        dv[0] = dvel(Bi.x, Bj.x, Ci, Cj, 0);
+        dv[1] = dvel(Bi.y, Bj.y, Ci, Cj, 1);
+        dv[2] = dvel(Bi.z, Bj.z, Ci, Cj, 2);
+      } else {
+        dv[0] = Bj.x - Bi.x;
+        dv[1] = Bj.y - Bi.y;
+        dv[2] = Bj.z - Bi.z;
+      }
 #pragma unroll
       for (int b = 0; b < DIM; ++b) {
         gP[b] += f * dP * e[b];
@@ -201,7 +211,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
       if (j == i) return;
       const V4 Aj = A[j];
       const V4 Bj = B[j];
-      const V2 Cj = C[j];
+      const VC Cj = C[j];
       const V4 Gj = Gp[j];
       const V2 Rj = Rp[j];
       T dx, dy, dz;
@@ -219,7 +229,14 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
       const T ir = rsqrt_(r2);
       const T r = r2 * ir;
       const T e[3] = {dx * ir, dy * ir, dz * ir};
-      const T vi[3] = {Bi.x, Bi.y, Bi.z}, vj[3] = {Bj.x, Bj.y, Bj.z};
+      T vi[3] = {Bi.x, Bi.y, Bi.z}, vj[3] = {Bj.x, Bj.y, Bj.z};
+      if constexpr (MIXED) {   // lab-frame velocities: relative ones plus the references
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          vi[q] += ref_v(Ci, q);
+          vj[q] += ref_v(Cj, q);
+        }
+      }
       T vRi = T(0), vRj = T(0);
 #pragma unroll
       for (int q = 0; q < DIM; ++q) { vRi += vi[q] * e[q]; vRj += vj[q] * e[q]; }

@@ -46,10 +46,11 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
   using V4 = typename P::V4;
-  using V2 = typename P::V2;
+  using VC = typename P::VC;
   __shared__ float res[kWarps][6][32];            // per slot of the group: sums of rho, a (3), E, and dmax
   __shared__ double res64[kWarps][6][MIXED ? 1 : 32];
   __shared__ unsigned res_n[kWarps][32];
+  __shared__ long long t_start[kWarps];          // timed loads: start of the warp's slot iteration
   // unit shifts (-1, 0, 1) per axis of each neighbour-cell code; a table read
   // and three multiplies are cheaper than the integer divisions and
   // conversions of the decode, and give the same FP32 shifts bit for bit
@@ -64,11 +65,13 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
   const unsigned hmask = (kSlotLanes == 32 ? 0xffffffffu : ((1u << kSlotLanes) - 1u)) << (half * kSlotLanes);
   const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
   for (;;) {
-    int64_t g0 = 0;
-    if (lane == 0) g0 = (int64_t)atomicAdd(a.work_counter, 32ull);
-    g0 = __shfl_sync(0xffffffffu, g0, 0);
-    if (g0 >= a.n) break;
-    const int64_t g1 = g0 + 32 < a.n ? g0 + 32 : a.n;
+    // slots in 32 bits: list entries hold slot indices in 27 bits
+    unsigned long long gw = 0;
+    if (lane == 0) gw = atomicAdd(a.work_counter, 32ull);
+    gw = __shfl_sync(0xffffffffu, gw, 0);
+    if ((int64_t)gw >= a.n) break;
+    const int g0 = (int)gw;
+    const int g1 = (int64_t)g0 + 32 < a.n ? g0 + 32 : (int)a.n;
     int unit_run = -1;
     unsigned unit_load = 0;
     unsigned tf = 0, tc = 0, te = 0;
@@ -85,8 +88,12 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
       cnt_pre = a.vcnt[g0 + half];
     }
     for (int q = 0; g0 + kSlotsPerWarp * q < g1; ++q) {   // warp-uniform
-      const long long t_start = a.load_timed ? clock64() : 0;
-      const int64_t i = g0 + kSlotsPerWarp * q + half;       // this group's slot
+      if (a.load_timed) {                                    // kept in shared memory: frees registers
+        __syncwarp();
+        if (lane == 0) t_start[warp] = clock64();
+        __syncwarp();
+      }
+      const int i = g0 + kSlotsPerWarp * q + half;           // this group's slot
       const bool iv = i < g1;                                // uniform in the group
       const int cnt = iv ? cnt_pre : 0;
       uint32_t e_cur = e_pre;
@@ -94,7 +101,7 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
         e_pre = a.vlist[(i + kSlotsPerWarp) * (int64_t)a.vcap + hl];
         cnt_pre = a.vcnt[i + kSlotsPerWarp];
       }
-      const int64_t ii = iv ? i : g0;                 // a valid slot for the loads
+      const int ii = iv ? i : g0;                     // a valid slot for the loads
       int b = 0;
       if (a.n_inst > 1) {
         int lo = 0, hi = a.n_inst;
@@ -109,10 +116,10 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
       const float band = MIXED ? 0x1p-12f * g.dc_f * g.dc_f : 0.f;
       const V4 Ai = A[ii];
       const V4 Bi = reinterpret_cast<const V4*>(a.B)[ii];
-      const V2 Ci = reinterpret_cast<const V2*>(a.C)[ii];
+      const VC Ci = reinterpret_cast<const VC*>(a.C)[ii];
       const T khdi = MIXED ? (T)a.kh_f * Ai.w : T(0);
       const int ui = a.K > 0 ? a.slot_unit[ii] : 0;
-      const uint32_t* __restrict__ row = a.vlist + ii * (int64_t)a.vcap;
+      const uint32_t* __restrict__ row = a.vlist + (int64_t)ii * a.vcap;
       FwdAcc<MIXED, DIM, false, HLL, EXTRA> fw;
       unsigned nacc = 0;                              // accepted pairs of i (uniform in the group)
       int cmax = cnt;                                 // chunks run by the whole warp
@@ -153,7 +160,7 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
       }
       if (iv) {
         if (hl == 0) {
-          const int r = (int)(i - g0);
+          const int r = i - g0;
           const T vals[6] = {srho, sfx, sfy, sfz, sq, dm};
 #pragma unroll
           for (int qv = 0; qv < 6; ++qv) {
@@ -169,7 +176,7 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
             atomicAdd(&a.load_acc[unit_run], (unsigned long long)unit_load);
           if (ui != unit_run) { unit_run = ui; unit_load = 0; }
           // timed loads: the iteration's SM cycles (the eight slots share them)
-          unit_load += a.load_timed ? (unsigned)((clock64() - t_start) / kSlotsPerWarp) : nacc;
+          unit_load += a.load_timed ? (unsigned)((clock64() - t_start[warp]) / kSlotsPerWarp) : nacc;
         }
       }
     }
@@ -189,7 +196,7 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
         const double drho = 2.0 * a.rho_slot[i] * (rv(0) * a.rscale);
         const double im = a.fscale / a.m[p];
         const double acc[3] = {rv(1) * im, DIM >= 2 ? rv(2) * im : 0.0, DIM >= 3 ? rv(3) * im : 0.0};
-        const double dE = rv(4) * im;
+        const double dE = rv(4) * im + lab_power_of<MIXED>(a, i, acc);
         a.drho[p] = drho;
         a.ax[p] = acc[0];
         if (DIM >= 2) a.ay[p] = acc[1];

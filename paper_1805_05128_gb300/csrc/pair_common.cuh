@@ -96,11 +96,14 @@ constexpr int kModeFwd2 = 4;   // rates with states reconstructed to the pair mi
 template <bool MIXED>
 struct Ops;
 
+// Packed operands per slot: A = (x, y, z, d), B = (v, V = m/rho), C = (P, Z = rho c)
+// and, mixed, the reference velocity of B's relative velocity (k_pack).
 template <>
 struct Ops<true> {
   using T = float;
   using V4 = float4;
   using V2 = float2;
+  using VC = float4;   // P, Z, reference velocity (x and y in one word, z)
 };
 
 template <>
@@ -108,7 +111,26 @@ struct Ops<false> {
   using T = double;
   using V4 = D4;
   using V2 = D2;
+  using VC = D2;       // P, Z
 };
+
+// Reference velocities of the mixed packs: B holds v - k with k the whole-m/s
+// reference of the particle, C.z holds k_x + 32768 and k_y + 32768 in its low
+// and high halves, C.w holds k_z as a float.  ref_x / ref_y give
+// 2^23 + k + 32768 exactly, so the difference of two particles' values is the
+// exact difference of their references.
+__device__ __forceinline__ float ref_x(float w) { return __int_as_float(__byte_perm(__float_as_int(w), 0x4B00, 0x5410)); }
+__device__ __forceinline__ float ref_y(float w) { return __int_as_float(__byte_perm(__float_as_int(w), 0x4B00, 0x5432)); }
+// Component c of a mixed pack's reference velocity (m/s, exact).
+__device__ __forceinline__ float ref_v(const float4& C, int c) {
+  return c == 0 ? ref_x(C.z) - 8421376.0f : (c == 1 ? ref_y(C.z) - 8421376.0f : C.w);
+}
+// Component c of v_j - v_i from mixed packs: the relative velocities' difference
+// plus the exact difference of the references (negated exactly when i and j swap).
+__device__ __forceinline__ float dvel(float bi, float bj, const float4& Ci, const float4& Cj, int c) {
+  const float du = c == 0 ? ref_x(Cj.z) - ref_x(Ci.z) : (c == 1 ? ref_y(Cj.z) - ref_y(Ci.z) : Cj.w - Ci.w);
+  return __fadd_rn(__fsub_rn(bj, bi), du);
+}
 
 template <typename T>
 struct Kahan {
@@ -212,6 +234,7 @@ struct Pair {
   using T = typename Ops<MIXED>::T;
   using V4 = typename Ops<MIXED>::V4;
   using V2 = typename Ops<MIXED>::V2;
+  using VC = typename Ops<MIXED>::VC;
 
   // Canonical separation lo -> hi.  sh: shift from i's cell to j's cell (mixed only).
   static __device__ __forceinline__ void sep(bool ilo, const V4& Ai, const V4& Aj, T sx, T sy, T sz, T& dx,
@@ -267,6 +290,22 @@ __device__ __forceinline__ T minmod(T a, T b) {
   return (a > T(0) && b > T(0)) ? (a < b ? a : b) : ((a < T(0) && b < T(0)) ? (a > b ? a : b) : T(0));
 }
 
+// The energy fluxes of a mixed evaluation are summed as F_ij (v* - v_i^R);
+// the rate adds v_i . a_i, which is sum_j F_ij v_i^R / m_i (v_i . e_ij =
+// v_i^R), with v_i the packed velocity (relative part plus reference) in
+// FP64.  Zero for FP64 packs, whose fluxes carry v* itself.
+template <bool MIXED>
+__device__ __forceinline__ double lab_power_of(const PairArgs& a, int64_t i, const double* acc) {
+  if constexpr (MIXED) {
+    const float4 Bi = reinterpret_cast<const float4*>(a.B)[i];
+    const float4 Ci = reinterpret_cast<const float4*>(a.C)[i];
+    return ((double)Bi.x + (double)ref_v(Ci, 0)) * acc[0] + ((double)Bi.y + (double)ref_v(Ci, 1)) * acc[1] +
+           ((double)Bi.z + (double)Ci.w) * acc[2];
+  } else {
+    return 0.0;
+  }
+}
+
 // EXTRA: also the side outputs of an evaluation, i.e. the largest neighbour
 // size, the unit adjacency and the optional pair output.  Only the
 // evaluations that feed a rebalance or a pair query need them, and leaving
@@ -276,7 +315,7 @@ struct FwdAcc {
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
   using V4 = typename P::V4;
-  using V2 = typename P::V2;
+  using VC = typename P::VC;
   Kahan<T> s_rho, s_fx, s_fy, s_fz, s_q;
   T dmax = T(0);
   int last_adj = -1;
@@ -297,15 +336,15 @@ struct FwdAcc {
     return s;
   }
 
-  __device__ __forceinline__ void pair(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi, const V2& Ci,
+  __device__ __forceinline__ void pair(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi, const VC& Ci,
                                        int ui, int64_t j, T sx, T sy, T sz) {
     const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
     const V4* __restrict__ B = reinterpret_cast<const V4*>(a.B);
-    const V2* __restrict__ C = reinterpret_cast<const V2*>(a.C);
+    const VC* __restrict__ C = reinterpret_cast<const VC*>(a.C);
     if (j == i) return;       // the scan keeps the self pair (r = 0); it has no flux
     const V4 Aj = A[j];
     const V4 Bj = B[j];
-    const V2 Cj = C[j];
+    const VC Cj = C[j];
     T dx, dy, dz;
     separation(Ai, Aj, sx, sy, sz, dx, dy, dz);
     flux_at(a, i, Ai, Bi, Ci, ui, j, Aj, Bj, Cj, dx, dy, dz, P::r2_of(dx, dy, dz));
@@ -332,14 +371,14 @@ struct FwdAcc {
   // |r^2 - (kappa h_ij)^2| <= band, where FP32 rounding could flip it; FP64:
   // the oracle's test.  Returns whether the pair interacts.
   __device__ __forceinline__ bool pair_listed(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi,
-                                              const V2& Ci, int ui, int64_t j, T sx, T sy, T sz, T khdi,
+                                              const VC& Ci, int ui, int64_t j, T sx, T sy, T sz, T khdi,
                                               float band, unsigned& nexact) {
     const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
     const V4* __restrict__ B = reinterpret_cast<const V4*>(a.B);
-    const V2* __restrict__ C = reinterpret_cast<const V2*>(a.C);
+    const VC* __restrict__ C = reinterpret_cast<const VC*>(a.C);
     const V4 Aj = A[j];
     const V4 Bj = B[j];       // requested with A[j]: most candidates interact
-    const V2 Cj = C[j];
+    const VC Cj = C[j];
     T dx, dy, dz;
     separation(Ai, Aj, sx, sy, sz, dx, dy, dz);
     const T r2 = P::r2_of(dx, dy, dz);
@@ -362,58 +401,102 @@ struct FwdAcc {
     return acc;
   }
 
-  __device__ __forceinline__ void flux_at(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi, const V2& Ci,
-                                          int ui, int64_t j, const V4& Aj, const V4& Bj, const V2& Cj, T dx, T dy,
+  __device__ __forceinline__ void flux_at(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi, const VC& Ci,
+                                          int ui, int64_t j, const V4& Aj, const V4& Bj, const VC& Cj, T dx, T dy,
                                           T dz, T r2) {
     if constexpr (EXTRA) dmax = Aj.w > dmax ? Aj.w : dmax;
     if (!(r2 > T(0))) return;  // coincident particles: no direction, no flux
     const T ir = rsqrt_(r2);
     const T r = r2 * ir;
     const T ex = dx * ir, ey = dy * ir, ez = dz * ir;
-    T vi = Bi.x * ex, vj = Bj.x * ex;
-    if (DIM >= 2) { vi = fma_(Bi.y, ey, vi); vj = fma_(Bj.y, ey, vj); }
-    if (DIM >= 3) { vi = fma_(Bi.z, ez, vi); vj = fma_(Bj.z, ez, vj); }
     T Zi = Ci.y, Zj = Cj.y;
     // HLL with Davis speeds -+max(Z_i, Z_j) is the acoustic state with both
     // impedances set to that maximum (exchange-symmetric, so the flux keeps
     // its bitwise antisymmetry)
     if constexpr (HLL) { const T Zm = Zi > Zj ? Zi : Zj; Zi = Zm; Zj = Zm; }
-    T Pi = Ci.x, Pj = Cj.x, wi = vi, wj = vj;   // states fed to the solver
-    if constexpr (ORDER2) {
-      const V4* __restrict__ GP = reinterpret_cast<const V4*>(a.gP);
-      const V4* __restrict__ GV = reinterpret_cast<const V4*>(a.gV);
-      V4 gvj[3];
-      gvj[0] = GV[j];
-      if (DIM >= 2) gvj[1] = GV[a.n + j];
-      if (DIM >= 3) gvj[2] = GV[2 * a.n + j];
-      const T dP = sub_(Pj, Pi), dv = sub_(vj, vi);
-      const T sPi = mul_(r, dot_e(gPi, ex, ey, ez)), sPj = mul_(r, dot_e(GP[j], ex, ey, ez));
-      const T svi = mul_(r, dvv(gVi, ex, ey, ez)), svj = mul_(r, dvv(gvj, ex, ey, ez));
-      Pi = add_(Ci.x, mul_(T(0.5), minmod(sPi, dP)));
-      Pj = sub_(Cj.x, mul_(T(0.5), minmod(sPj, dP)));
-      wi = add_(vi, mul_(T(0.5), minmod(svi, dv)));
-      wj = sub_(vj, mul_(T(0.5), minmod(svj, dv)));
-    }
     const T zs = add_(Zi, Zj);
-    T Ps, vs;
-    if (zs > T(0)) {
-      const T izs = rcp_(zs);
-      Ps = mul_(add_(add_(mul_(Zj, Pi), mul_(Zi, Pj)), mul_(mul_(Zi, Zj), sub_(wi, wj))), izs);
-      vs = mul_(add_(add_(mul_(Zi, wi), mul_(Zj, wj)), sub_(Pi, Pj)), izs);
+    T Ps, cr, qv;   // P*; v_i^R - v* (continuity); the velocity of the energy flux
+    if constexpr (MIXED) {
+      // Velocities only through differences.  g = v_j - v_i from the relative
+      // packs plus the exact reference difference, gR = g . e: j's side
+      // negates g and e exactly, so gR and P* are the same bits there.  The
+      // energy flux is summed as F (v* - v_i^R); the writer adds v_i . a_i,
+      // which is sum_j F v_i^R.
+      T gR = mul_(dvel(Bi.x, Bj.x, Ci, Cj, 0), ex);
+      if (DIM >= 2) gR = fma_(dvel(Bi.y, Bj.y, Ci, Cj, 1), ey, gR);
+      if (DIM >= 3) gR = fma_(dvel(Bi.z, Bj.z, Ci, Cj, 2), ez, gR);
+      T Pl = Ci.x, Pr = Cj.x, jump = -gR;         // jump = w_i - w_j
+      T hi = T(0), hj = T(0);
+      if constexpr (ORDER2) {
+        const V4* __restrict__ GP = reinterpret_cast<const V4*>(a.gP);
+        const V4* __restrict__ GV = reinterpret_cast<const V4*>(a.gV);
+        V4 gvj[3];
+        gvj[0] = GV[j];
+        if (DIM >= 2) gvj[1] = GV[a.n + j];
+        if (DIM >= 3) gvj[2] = GV[2 * a.n + j];
+        const T dP = sub_(Pr, Pl);
+        const T sPi = mul_(r, dot_e(gPi, ex, ey, ez)), sPj = mul_(r, dot_e(GP[j], ex, ey, ez));
+        const T svi = mul_(r, dvv(gVi, ex, ey, ez)), svj = mul_(r, dvv(gvj, ex, ey, ez));
+        Pl = add_(Ci.x, mul_(T(0.5), minmod(sPi, dP)));
+        Pr = sub_(Cj.x, mul_(T(0.5), minmod(sPj, dP)));
+        hi = mul_(T(0.5), minmod(svi, gR));
+        hj = mul_(T(0.5), minmod(svj, gR));
+        jump = add_(jump, add_(hi, hj));           // j adds the same two increments the other way round
+      }
+      T du;                                        // v* - v_i^R
+      if (zs > T(0)) {
+        const T izs = rcp_(zs);
+        Ps = mul_(add_(add_(mul_(Zj, Pl), mul_(Zi, Pr)), mul_(mul_(Zi, Zj), jump)), izs);
+        if constexpr (ORDER2) du = mul_(add_(add_(mul_(Zi, hi), mul_(Zj, sub_(gR, hj))), sub_(Pl, Pr)), izs);
+        else du = mul_(add_(mul_(Zj, gR), sub_(Pl, Pr)), izs);
+      } else {
+        Ps = mul_(T(0.5), add_(Pl, Pr));
+        du = ORDER2 ? mul_(T(0.5), add_(hi, sub_(gR, hj))) : mul_(T(0.5), gR);
+      }
+      cr = -du;
+      qv = du;
     } else {
-      Ps = mul_(T(0.5), add_(Pi, Pj));
-      vs = mul_(T(0.5), add_(wi, wj));
+      T vi = Bi.x * ex, vj = Bj.x * ex;
+      if (DIM >= 2) { vi = fma_(Bi.y, ey, vi); vj = fma_(Bj.y, ey, vj); }
+      if (DIM >= 3) { vi = fma_(Bi.z, ez, vi); vj = fma_(Bj.z, ez, vj); }
+      T Pi = Ci.x, Pj = Cj.x, wi = vi, wj = vj;   // states fed to the solver
+      if constexpr (ORDER2) {
+        const V4* __restrict__ GP = reinterpret_cast<const V4*>(a.gP);
+        const V4* __restrict__ GV = reinterpret_cast<const V4*>(a.gV);
+        V4 gvj[3];
+        gvj[0] = GV[j];
+        if (DIM >= 2) gvj[1] = GV[a.n + j];
+        if (DIM >= 3) gvj[2] = GV[2 * a.n + j];
+        const T dP = sub_(Pj, Pi), dv = sub_(vj, vi);
+        const T sPi = mul_(r, dot_e(gPi, ex, ey, ez)), sPj = mul_(r, dot_e(GP[j], ex, ey, ez));
+        const T svi = mul_(r, dvv(gVi, ex, ey, ez)), svj = mul_(r, dvv(gvj, ex, ey, ez));
+        Pi = add_(Ci.x, mul_(T(0.5), minmod(sPi, dP)));
+        Pj = sub_(Cj.x, mul_(T(0.5), minmod(sPj, dP)));
+        wi = add_(vi, mul_(T(0.5), minmod(svi, dv)));
+        wj = sub_(vj, mul_(T(0.5), minmod(svj, dv)));
+      }
+      T vs;
+      if (zs > T(0)) {
+        const T izs = rcp_(zs);
+        Ps = mul_(add_(add_(mul_(Zj, Pi), mul_(Zi, Pj)), mul_(mul_(Zi, Zj), sub_(wi, wj))), izs);
+        vs = mul_(add_(add_(mul_(Zi, wi), mul_(Zj, wj)), sub_(Pi, Pj)), izs);
+      } else {
+        Ps = mul_(T(0.5), add_(Pi, Pj));
+        vs = mul_(T(0.5), add_(wi, wj));
+      }
+      cr = vi - vs;
+      qv = vs;
     }
     const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * add_(Ai.w, Aj.w);
     const T dW = MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij, (T)a.wscale_f)
                        : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij);
     // momentum flux along e, without its factor 2 (carried by fscale; exact)
     const T F = mul_(mul_(mul_(Bi.w, Bj.w), Ps), dW);
-    s_rho.add(Bj.w * (vi - vs) * (-dW));
+    s_rho.add(Bj.w * cr * (-dW));
     s_fx.add(mul_(F, ex));
     if (DIM >= 2) s_fy.add(mul_(F, ey));
     if (DIM >= 3) s_fz.add(mul_(F, ez));
-    s_q.add(mul_(F, vs));
+    s_q.add(mul_(F, qv));
     if constexpr (!EXTRA) return;
     if (a.pair_i) {
       const int32_t pi = a.perm[i], pj = a.perm[j];
@@ -436,10 +519,12 @@ struct FwdAcc {
     const int64_t p = a.perm[i];
     a.drho[p] = 2.0 * a.rho_slot[i] * ((double)s_rho.s * a.rscale);
     const double im = a.fscale / a.m[p];
-    a.ax[p] = (double)s_fx.s * im;
-    if (DIM >= 2) a.ay[p] = (double)s_fy.s * im;
-    if (DIM >= 3) a.az[p] = (double)s_fz.s * im;
-    a.dE[p] = (double)s_q.s * im;
+    const double acc[3] = {(double)s_fx.s * im, DIM >= 2 ? (double)s_fy.s * im : 0.0,
+                           DIM >= 3 ? (double)s_fz.s * im : 0.0};
+    a.ax[p] = acc[0];
+    if (DIM >= 2) a.ay[p] = acc[1];
+    if (DIM >= 3) a.az[p] = acc[2];
+    a.dE[p] = (double)s_q.s * im + lab_power_of<MIXED>(a, i, acc);
     if (EXTRA) a.dmax_nbr[p] = nfull ? (double)dmax : -1.0;
   }
 };
