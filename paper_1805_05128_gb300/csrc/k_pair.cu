@@ -9,8 +9,10 @@
 // arithmetic runs on converged lanes instead of under the ~17% acceptance
 // of the candidate test.
 //
-// Antisymmetry: the momentum flux F_ij e^R and energy flux Q_ij that i and
-// j apply are bitwise negatives of each other (FwdAcc in pair_common.cuh).
+// Antisymmetry: the momentum flux F_ij e^R that i and j apply are bitwise
+// negatives of each other, and so are the energy fluxes Q_ij of FP64
+// handles; mixed handles sum the energy flux from velocity differences
+// (FwdAcc in pair_common.cuh).
 //
 // Modes of the kernel: the rates (optionally with order-2 states), the SPH
 // gradients of order 2, the reverse mode, and the Verlet list build; the

@@ -269,14 +269,18 @@ struct Pair {
 };
 
 // Flux of the interacting pair (i, j) from i's side.  Every quantity
-// that j computes for the same pair is the exact negative (e^R, v^R, v*,
-// momentum and energy fluxes) or the exact same value (r, P*, h_ij, W'):
-// dx = (off_j - off_i) + shift is the rounded negative of j's
-// (off_i - off_j) - shift, IEEE rounding is sign-symmetric, and the sums
-// that mix i and j are written with uncontracted operations in an order
-// that is symmetric under the exchange.  So the applied fluxes are
-// antisymmetric bit for bit and momentum and energy are conserved by the
-// pair sums up to the per-particle summation.
+// that j computes for the same pair is the exact negative (e^R, the
+// momentum flux; FP64: v^R, v* and the energy flux) or the exact same value
+// (r, P*, h_ij, W'; mixed: the velocity jump (v_j - v_i) . e): dx =
+// (off_j - off_i) + shift is the rounded negative of j's (off_i - off_j) -
+// shift, IEEE rounding is sign-symmetric, and the sums that mix i and j are
+// written with uncontracted operations in an order that is symmetric under
+// the exchange.  So the momentum fluxes are antisymmetric bit for bit and
+// momentum is conserved by the pair sums up to the per-particle summation.
+// Mixed precision takes velocities only through differences (relative packs
+// with exact whole-m/s references) and sums the energy flux as
+// F (v* - v_i^R), the writer adding v_i . a_i: energy is exchanged exactly up
+// to the rounding of those small terms.
 //
 // Order 2 (ORDER2): P and v^R are extrapolated from each particle to the pair
 // midpoint with the SPH gradients, each increment limited by minmod against
