@@ -579,7 +579,7 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
     reinterpret_cast<float4*>(packA)[sl] = make_float4(off[0], off[1], off[2], (float)d);
     const float Vp = fast ? ((float)m / (float)rho) * (float)P.vscale : (float)((m / rho) * P.vscale);
     // FP32 velocities relative to a reference velocity of whole m/s per
-    // particle (k = v rounded, |k| <= 32767): v - k is exact in FP64 and
+    // particle (k = v truncated, |k| <= 32767): v - k is exact in FP64 and
     // small, so FP32 keeps the velocity differences between neighbours to
     // ~1e-8 m/s instead of one ulp of the bulk velocity.  The references are
     // stored exactly: x and y biased by 32768 in the halves of one word,
@@ -588,11 +588,7 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
     float vr[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      if (a < P.dim) {
-        const int q = __float2int_rn((float)v[a]);
-        k[a] = q < -32767 ? -32767 : (q > 32767 ? 32767 : q);
-        vr[a] = (float)(v[a] - (double)k[a]);
-      }
+      if (a < P.dim) vr[a] = (float)(v[a] - trunc_ref(v[a], k[a]));
     const uint32_t kxy = (uint32_t)(k[0] + 32768) | ((uint32_t)(k[1] + 32768) << 16);
     reinterpret_cast<float4*>(packB)[sl] = make_float4(vr[0], vr[1], vr[2], Vp);
     reinterpret_cast<float4*>(packC)[sl] = make_float4((float)Pp, fast ? (float)rho * cf : (float)(rho * cp),

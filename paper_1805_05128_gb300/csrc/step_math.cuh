@@ -19,6 +19,28 @@ __device__ __forceinline__ double dunkey(long long k) {
   return __longlong_as_double(k < 0 ? k ^ 0x7fffffffffffffffLL : k);
 }
 
+// Reference velocity of a mixed pack: t = trunc(v) with |t| <= 32767, built
+// from v's bits by integer operations (no FP64 arithmetic), and k = t as an
+// int.  v - t is then exact in FP64 (|v - t| < 1 unless clamped) and rounds
+// to FP32 with an error ~6e-8 of itself.  NaN and infinity clamp like large
+// values, and their difference stays non-finite.
+__device__ __forceinline__ double trunc_ref(double v, int& k) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;       // unbiased exponent
+  if (e < 0) {                                          // |v| < 1
+    k = 0;
+    return 0.0;
+  }
+  if (e >= 15) {                                        // |v| >= 32768
+    k = b < 0 ? -32767 : 32767;
+    return b < 0 ? -32767.0 : 32767.0;
+  }
+  const int fb = 52 - e;                                // fraction bits below the binary point
+  const int m = (int)(((b & 0xfffffffffffffLL) | (1LL << 52)) >> fb);
+  k = b < 0 ? -m : m;
+  return __longlong_as_double(b & ~((1LL << fb) - 1));
+}
+
 // Cube root in FP64 with little FP64 work: the FP32 cube root as seed, then
 // two Newton steps on y^3 - x = 0 whose derivative reciprocal 1/(3 y^2) is
 // taken in FP32 (a ~1e-7 relative error in the slope only scales each
