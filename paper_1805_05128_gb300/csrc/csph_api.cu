@@ -168,7 +168,7 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   dp.vscale = 1.0;
   for (int k = 0; k < p->n_mat; ++k) {
     const sph_material& m = mats[k];
-    h->mat_h.push_back(Mat{m.eos, m.gamma, m.rho0, m.c0, m.p_inf, m.s_a});
+    h->mat_h.push_back(make_mat(m.eos, m.gamma, m.rho0, m.c0, m.p_inf, m.s_a));
   }
   h->p.materials = nullptr;   // the caller's host array is not kept
   cudaStream_t st = (cudaStream_t)stream;

@@ -45,7 +45,35 @@ struct BlockPart {
 struct Mat {
   int eos;
   double gamma, rho0, c0, p_inf, s_a;
+  // Tait: B = rho0 c0^2 / gamma, and gamma as an int when it is a whole
+  // number in [1, 16] (0 otherwise), so that r^gamma is a few products
+  // instead of pow (FP64 pow costs ~100 operations of GB300's narrow FP64 pipe)
+  double tait_B;
+  int tait_n;
 };
+
+// Host-side table entry of a material.
+inline Mat make_mat(int eos, double gamma, double rho0, double c0, double p_inf, double s_a) {
+  Mat m{eos, gamma, rho0, c0, p_inf, s_a, 0.0, 0};
+  if (eos == SPH_EOS_TAIT) {
+    m.tait_B = rho0 * c0 * c0 / gamma;
+    m.tait_n = (gamma >= 1.0 && gamma <= 16.0 && gamma == (double)(int)gamma) ? (int)gamma : 0;
+  }
+  return m;
+}
+
+// x^n for n >= 1 by binary powering (a few products; the rounding of each
+// product is the only difference from pow).
+template <typename T>
+__device__ __forceinline__ T ipow(T x, int n) {
+  T r = T(1), b = x;
+  while (n > 0) {
+    if (n & 1) r *= b;
+    n >>= 1;
+    if (n) b *= b;
+  }
+  return r;
+}
 
 struct DevParams {
   int dim, kernel, precision, n_mat;
@@ -199,10 +227,15 @@ __device__ __forceinline__ void eos(const Mat& m, double rho, double e, double& 
     P = (m.gamma - 1.0) * rho * e - m.gamma * m.p_inf;
     c2 = m.gamma * (P + m.p_inf) / rho;
   } else if (m.eos == SPH_EOS_TAIT) {
-    double B = m.rho0 * m.c0 * m.c0 / m.gamma;
-    double r = rho / m.rho0;
-    P = B * (pow(r, m.gamma) - 1.0);
-    c2 = m.c0 * m.c0 * pow(r, m.gamma - 1.0);
+    const double r = rho / m.rho0;
+    if (m.tait_n > 0) {                                  // whole exponent: r^(n-1) and r^n by products
+      const double rn1 = m.tait_n > 1 ? ipow(r, m.tait_n - 1) : 1.0;
+      P = m.tait_B * (rn1 * r - 1.0);
+      c2 = m.c0 * m.c0 * rn1;
+    } else {
+      P = m.tait_B * (pow(r, m.gamma) - 1.0);
+      c2 = m.c0 * m.c0 * pow(r, m.gamma - 1.0);
+    }
   } else {  // Mie-Grueneisen with the linear u_s-u_p Hugoniot reference curves
     double G = m.gamma, ca = m.c0, sa = m.s_a;
     double x = m.rho0 / rho;

@@ -550,11 +550,13 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
   double Pp, cp;
   float cf = 0.0f;
   const Mat& mt = P.mat[mi];
-  const bool fast = MIXED && predict && (mt.eos == SPH_EOS_IDEAL || mt.eos == SPH_EOS_STIFFENED);
+  const bool fast = MIXED && predict &&
+                    (mt.eos == SPH_EOS_IDEAL || mt.eos == SPH_EOS_STIFFENED || (mt.eos == SPH_EOS_TAIT && mt.tait_n > 0));
   if (fast) {
-    // a mixed step packs FP32 operands: P in FP64 (the stiffened-gas difference
-    // of two large terms, the expression of eos()), c in FP32
-    Pp = (mt.gamma - 1.0) * rho * e - (mt.eos == SPH_EOS_STIFFENED ? mt.gamma * mt.p_inf : 0.0);
+    // a mixed step packs FP32 operands: P in FP64 (the stiffened-gas and Tait
+    // differences of two large terms, the expressions of eos()), c in FP32
+    if (mt.eos == SPH_EOS_TAIT) Pp = mt.tait_B * (ipow(rho / mt.rho0, mt.tait_n) - 1.0);
+    else Pp = (mt.gamma - 1.0) * rho * e - (mt.eos == SPH_EOS_STIFFENED ? mt.gamma * mt.p_inf : 0.0);
     cf = sound_speed_f32(mt, (float)rho, (float)e);
     cp = (double)cf;
   } else {

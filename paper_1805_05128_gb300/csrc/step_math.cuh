@@ -107,8 +107,8 @@ __device__ __forceinline__ float sound_speed_f32(const Mat& m, float rho, float 
   } else if (m.eos == SPH_EOS_STIFFENED) {
     c2 = g * (g - 1.0f) * (rho * e - (float)m.p_inf) / rho;
   } else if (m.eos == SPH_EOS_TAIT) {
-    const float c0 = (float)m.c0;
-    c2 = c0 * c0 * powf(rho / (float)m.rho0, g - 1.0f);
+    const float c0 = (float)m.c0, r = rho / (float)m.rho0;
+    c2 = c0 * c0 * (m.tait_n > 1 ? ipow(r, m.tait_n - 1) : (m.tait_n == 1 ? 1.0f : powf(r, g - 1.0f)));
   } else {
     const float ca = (float)m.c0, sa = (float)m.s_a, r0 = (float)m.rho0;
     const float x = r0 / rho, u = 1.0f - x, D = 1.0f - sa * u, iD2 = 1.0f / (D * D);
