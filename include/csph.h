@@ -46,7 +46,8 @@ extern "C" {
 #define SPH_EOS_MIE_GRUNEISEN 3  /* eqs. (mie_gruneisen_eos), (mie_gruneisen_reference), Sec. 7 */
 
 #define SPH_PREC_FP64 0   /* every pair flux in FP64 */
-#define SPH_PREC_MIXED 1  /* FP32 pair fluxes on local-origin offsets, Kahan-compensated
+#define SPH_PREC_MIXED 1  /* FP32 pair fluxes on local-origin offsets and on velocities relative
+                             to whole-m/s references (exact differences), Kahan-compensated
                              per-particle sums; FP64 positions, time, integration */
 
 #define SPH_SOLVER_ACOUSTIC 0  /* pair Riemann solver: linearised acoustic, impedance-weighted (Sec. 4.1) */
