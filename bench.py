@@ -528,13 +528,13 @@ def run_extras(args, dev) -> dict:
     return out
 
 
-def pair_traffic_bytes(args):
+def pair_traffic_bytes(args, profiles_dir: str | None = None):
     """DRAM bytes per launch of the dominant kernel of the benchmark workload,
     from the committed ncu summary of that kernel; None unless the summary was
-    taken on the current k_pair.cu source and the mixed path."""
+    taken on the current pair-kernel sources (kernel_rev) and the mixed path."""
     import re
     name = "k_pair_lists" if args.beta > 0 else "k_pair"
-    path = os.path.join(ROOT, "profiles", f"{name}_plate_impact_387k.md")
+    path = os.path.join(profiles_dir or os.path.join(ROOT, "profiles"), f"{name}_plate_impact_387k.md")
     if args.precision != "mixed" or not os.path.exists(path):
         return None
     text = open(path).read()
