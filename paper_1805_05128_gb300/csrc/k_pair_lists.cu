@@ -24,7 +24,7 @@ namespace {
 // combined by a fixed butterfly, and the FP64 scaling of the rates is done
 // for the 32 slots of the group at once, one slot per lane.  Offsets stay
 // relative to the cells of the build and each pair's shift comes from its
-// neighbour-cell code, so the fluxes keep their bitwise antisymmetry; every
+// neighbour-cell code, so the momentum fluxes stay antisymmetric bit for bit; every
 // order is fixed, so results are reproducible bit for bit.
 
 // Lanes per slot of k_pair_lists (a divisor of 32): measured on the 1.125M

@@ -415,8 +415,8 @@ struct FwdAcc {
     const T ex = dx * ir, ey = dy * ir, ez = dz * ir;
     T Zi = Ci.y, Zj = Cj.y;
     // HLL with Davis speeds -+max(Z_i, Z_j) is the acoustic state with both
-    // impedances set to that maximum (exchange-symmetric, so the flux keeps
-    // its bitwise antisymmetry)
+    // impedances set to that maximum (exchange-symmetric, so P* stays the
+    // same bits on both sides)
     if constexpr (HLL) { const T Zm = Zi > Zj ? Zi : Zj; Zi = Zm; Zj = Zm; }
     const T zs = add_(Zi, Zj);
     T Ps, cr, qv;   // P*; v_i^R - v* (continuity); the velocity of the energy flux
