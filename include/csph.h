@@ -11,9 +11,11 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Calls are asynchronous on that stream: they enqueue work and return.
  *    Only sph_read_status() synchronises.  Errors found on the host (bad
- *    arguments) are returned at once; errors found on the device (capacity,
- *    non-finite values, bounded-wait timeouts) are latched in a device status
- *    word and reported by sph_read_status().
+ *    arguments) are returned at once; errors found on the device (list or
+ *    cell capacity exceeded, non-finite values, unit ids out of range) are
+ *    latched in a device status word and reported by sph_read_status().  A
+ *    kernel that latches an error keeps every access in bounds and returns
+ *    normally; the results of that call are then not meaningful.
  *  - A handle owns only workspace (cell lists, packed operands, work-unit
  *    lists, reduction buffers), allocated in sph_init and freed in
  *    sph_destroy.  A handle is used from one host thread at a time.
@@ -34,7 +36,7 @@ extern "C" {
 #define SPH_ERR_CAPACITY 2   /* more particles / cells / pairs than the workspace holds */
 #define SPH_ERR_NONFINITE 3  /* NaN or Inf found in the particle state */
 #define SPH_ERR_CUDA 4       /* a CUDA runtime call failed */
-#define SPH_ERR_TIMEOUT 5    /* a bounded device-side wait gave up */
+#define SPH_ERR_TIMEOUT 5    /* reserved: no kernel of this library waits on another, so nothing sets it */
 
 /* ---- enumerations ---- */
 #define SPH_KERNEL_CUBIC 0        /* cubic spline M4, support 2h */
@@ -44,6 +46,10 @@ extern "C" {
 #define SPH_EOS_STIFFENED 1      /* P = (gamma-1) rho e - gamma P_inf */
 #define SPH_EOS_TAIT 2           /* P = rho0 c0^2/gamma [(rho/rho0)^gamma - 1] */
 #define SPH_EOS_MIE_GRUNEISEN 3  /* eqs. (mie_gruneisen_eos), (mie_gruneisen_reference), Sec. 7 */
+#define SPH_EOS_STIFFENED_C0 4   /* stiffened gas given by (rho0, c0, gamma): sph_init sets
+                                    P_inf = rho0 c0^2 / gamma, so that c = c0 and P = 0 at rho0 with
+                                    e = gamma P_inf / ((gamma - 1) rho0); p_inf is ignored.  The form
+                                    whose dL/d(c0, gamma) sph_step_adjoint returns. */
 
 #define SPH_PREC_FP64 0   /* every pair flux in FP64 */
 #define SPH_PREC_MIXED 1  /* FP32 pair fluxes on local-origin offsets and on velocities relative
@@ -102,7 +108,10 @@ typedef struct sph_params {
                          limited against the pair jump (an extension; needs cell_beta = 0, no adjoint) */
   int32_t solver;     /* SPH_SOLVER_*: the pair Riemann solver (HLL: no adjoint) */
   int32_t load_measure; /* SPH_LOAD_*: what the work-unit loads of the balancing count */
-  int32_t pad3_;
+  int32_t list_cap;   /* Verlet lists: entries held per particle; 0 = the default (twice the
+                         neighbours of a uniform lattice within the buffered radius, plus 32);
+                         otherwise at least 32 (SPH_ERR_INVALID below).  A list that would grow
+                         past it is cut at the capacity and SPH_ERR_CAPACITY is latched. */
 } sph_params;
 
 /* Particle state: structure of arrays in device memory, n elements each.
@@ -220,10 +229,16 @@ int voronoi_balance(sph_handle* h, const sph_state* s, double* gen, int K, int d
  *            the held rates is folded into x, v, rho, E and the rate fields
  *            are returned as zero.
  *   adj_params: device, 2 doubles, ADDED dL/d(c0, gamma) of material 0
- *            (stiffened gas: P_inf = rho0 c0^2 / gamma; ideal gas: gamma).
- * Requires one instance, the cubic spline and ideal or stiffened gas
- * (SPH_ERR_INVALID otherwise).  No counterpart in the paper, which runs
- * forward only; it differentiates the paper's step. */
+ *            (SPH_EOS_STIFFENED_C0, or SPH_EOS_STIFFENED read as
+ *            P_inf = rho0 c0^2 / gamma; ideal gas: dL/dgamma only).
+ * Scope, narrower than the forward step's: one instance, the cubic spline,
+ * ideal or stiffened gas, the acoustic pair solver and order 1
+ * (SPH_ERR_INVALID otherwise); the replay finds the pairs with the per-step
+ * cell search whatever cell_beta is.  With reverse_fp64 = 0 on a mixed
+ * handle the pair derivatives use FP32 packed volumes rescaled back to SI
+ * units, which loses precision for particles far below a micrometre.  No
+ * counterpart in the paper, which runs forward only; it differentiates the
+ * paper's step. */
 int sph_step_adjoint(sph_handle* h, const sph_ckpt* ck, int n_steps, const sph_state* adj_out,
                      sph_state* adj_in, double* adj_params, void* stream);
 
@@ -284,15 +299,17 @@ int sph_cell_index(sph_handle* h, const sph_state* s, int32_t* cell_out, double*
 int sph_pair_list(sph_handle* h, sph_state* s, int64_t cap, int32_t* pi_out, int32_t* pj_out,
                   int64_t* count_out, void* stream);
 
-/* Allocation-free voronoi_assign, for callers that cannot allocate device
- * memory: code running while a stream is captured into a CUDA graph, code
- * whose device memory all belongs to another allocator or a fixed arena, or
- * a host loop that must not call cudaMalloc.  No handle is needed and
- * nothing is allocated: the scratch (per-unit counts and their scan) lives
- * in one file-scope device array of about 8.4 MB that every device which
- * loads the library keeps until the process exits.  No counterpart in the
- * paper; the result is that of voronoi_assign (eq. VoronoiDefinition, ties
- * to the smaller index) on the same inputs.
+/* Allocation-free voronoi_assign.  Some callers cannot call cudaMalloc: a
+ * host loop that must not allocate (allocation synchronises the device and
+ * can fail under memory pressure at a bad time), or code whose device memory
+ * all belongs to another allocator or a fixed arena that it may not step
+ * outside.  Such a caller cannot create a handle, whose workspace sph_init
+ * allocates.  This entry point needs no handle and allocates nothing: its
+ * scratch (per-unit counts, their scan, a counter) lives in one file-scope
+ * device array of about 8.4 MB that every device which loads the library
+ * keeps until the process exits.  The paper has no counterpart; the result
+ * equals that of voronoi_assign on the same inputs, ties going to the
+ * smaller generator index.
  *   x, y, z      device positions, n doubles each (y NULL for dim 1, z NULL
  *                for dim <= 2)
  *   gen          device, K x dim doubles
@@ -302,12 +319,16 @@ int sph_pair_list(sph_handle* h, sph_state* s, int64_t cap, int32_t* pi_out, int
  *                ascending inside each unit
  * Limits: 1 <= n <= 4,194,304 and 1 <= K <= 256 (else SPH_ERR_CAPACITY, or
  * SPH_ERR_INVALID for n < 1, K < 1, a bad dim or a missing pointer; see
- * sph_last_error(NULL)).  The array is shared by all calls on a device:
- * calls whose work overlaps on the GPU (other streams, other host threads)
- * race on it; each call resets what it needs, so consecutive calls on one
- * stream are independent.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture. */
+ * sph_last_error(NULL)).  Unlike the handle path this call has no status
+ * word: a particle with a NaN or infinite coordinate is given unit 0 and
+ * nothing reports it.  The array is shared by all calls on a device: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on
+ * it; each call resets what it needs, so consecutive calls on one stream are
+ * independent.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current and keeps it for
+ * the life of the process; make that first call before any stream capture.
+ * After cudaDeviceReset the kept address is stale: do not call this entry
+ * point on a device that has been reset. */
 int voronoi_assign_static(int64_t n, const double* x, const double* y, const double* z, const double* gen,
                           int K, int dim, int32_t* unit_out, int32_t* unit_offsets, int32_t* unit_list,
                           void* stream);

@@ -14,7 +14,7 @@ SO_PATH = os.path.join(_PKG, "libcsph.so")
 
 SPH_OK, SPH_ERR_INVALID, SPH_ERR_CAPACITY, SPH_ERR_NONFINITE, SPH_ERR_CUDA, SPH_ERR_TIMEOUT = range(6)
 SPH_KERNEL_CUBIC, SPH_KERNEL_WENDLAND_C2 = 0, 1
-SPH_EOS_IDEAL, SPH_EOS_STIFFENED, SPH_EOS_TAIT, SPH_EOS_MIE_GRUNEISEN = 0, 1, 2, 3
+SPH_EOS_IDEAL, SPH_EOS_STIFFENED, SPH_EOS_TAIT, SPH_EOS_MIE_GRUNEISEN, SPH_EOS_STIFFENED_C0 = 0, 1, 2, 3, 4
 SPH_PREC_FP64, SPH_PREC_MIXED = 0, 1
 SPH_SOLVER_ACOUSTIC, SPH_SOLVER_HLL = 0, 1
 SPH_LOAD_PAIRS, SPH_LOAD_TIME = 0, 1
@@ -43,7 +43,7 @@ class sph_params(C.Structure):
                 ("theta", C.c_double), ("sigma", C.c_double), ("gamma_b", C.c_double), ("beta_sh", C.c_double),
                 ("generators", C.c_void_p), ("materials", C.c_void_p),
                 ("order", C.c_int32), ("solver", C.c_int32),
-                ("load_measure", C.c_int32), ("pad3_", C.c_int32)]
+                ("load_measure", C.c_int32), ("list_cap", C.c_int32)]
 
 
 STATE_F64 = ("x", "y", "z", "vx", "vy", "vz", "rho", "E", "m")

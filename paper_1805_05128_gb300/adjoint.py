@@ -47,10 +47,8 @@ def _params(spec: RunSpec, c0: float, gamma: float) -> abi.sph_params:
     p = abi.sph_params()
     p.dim, p.kernel, p.precision, p.n_mat = spec.dim, abi.SPH_KERNEL_CUBIC, _PREC[spec.precision], 1
     p.kappa, p.eta, p.cfl, p.cell_beta, p.cell_cap = spec.kappa, spec.eta, spec.cfl, 0.0, spec.cell_cap
-    if spec.eos == "stiffened":
-        p.mat[0].eos, p.mat[0].p_inf = abi.SPH_EOS_STIFFENED, spec.rho0 * c0 * c0 / gamma
-    else:
-        p.mat[0].eos, p.mat[0].p_inf = abi.SPH_EOS_IDEAL, 0.0
+    # the stiffened gas given by (rho0, c0, gamma): the library derives P_inf
+    p.mat[0].eos = abi.SPH_EOS_STIFFENED_C0 if spec.eos == "stiffened" else abi.SPH_EOS_IDEAL
     p.mat[0].gamma, p.mat[0].rho0, p.mat[0].c0 = gamma, spec.rho0, c0
     return p
 

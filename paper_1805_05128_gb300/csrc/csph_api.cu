@@ -125,12 +125,17 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     return fail(nullptr, SPH_ERR_INVALID, "unknown pair solver");
   if (p->load_measure != SPH_LOAD_PAIRS && p->load_measure != SPH_LOAD_TIME)
     return fail(nullptr, SPH_ERR_INVALID, "unknown load measure");
+  if (p->list_cap != 0 && (p->list_cap < 32 || p->list_cap > 65536))
+    return fail(nullptr, SPH_ERR_INVALID, "list_cap must be 0 (default) or in [32, 65536]");
   if (p->n_mat < 1 || p->n_mat > kMaxMaterials || (p->n_mat > SPH_MAX_MAT && !p->materials))
     return fail(nullptr, SPH_ERR_INVALID, "n_mat out of range (more than SPH_MAX_MAT need params.materials)");
   const sph_material* mats = p->materials ? p->materials : p->mat;
-  for (int k = 0; k < p->n_mat; ++k)
-    if (mats[k].eos < SPH_EOS_IDEAL || mats[k].eos > SPH_EOS_MIE_GRUNEISEN)
+  for (int k = 0; k < p->n_mat; ++k) {
+    if (mats[k].eos < SPH_EOS_IDEAL || mats[k].eos > SPH_EOS_STIFFENED_C0)
       return fail(nullptr, SPH_ERR_INVALID, "unknown EOS");
+    if (mats[k].eos == SPH_EOS_STIFFENED_C0 && !(mats[k].rho0 > 0 && mats[k].c0 > 0 && mats[k].gamma > 0))
+      return fail(nullptr, SPH_ERR_INVALID, "SPH_EOS_STIFFENED_C0 needs rho0, c0, gamma > 0");
+  }
   if (!(p->kappa > 0) || !(p->eta > 0) || !(p->cfl > 0) || !(p->cell_beta >= 0))
     return fail(nullptr, SPH_ERR_INVALID, "kappa, eta, cfl must be > 0 and cell_beta >= 0");
   if (n_instances < 1 || !inst_offsets) return fail(nullptr, SPH_ERR_INVALID, "need n_instances >= 1 and offsets");
@@ -308,7 +313,7 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     const double rr = p->kappa * p->eta * (1.0 + p->cell_beta);
     const double pi = 3.14159265358979323846;
     const double vol = p->dim == 1 ? 2.0 * rr : (p->dim == 2 ? pi * rr * rr : 4.0 / 3.0 * pi * rr * rr * rr);
-    const double cap = std::ceil((p->dim == 3 ? 2.0 : 3.0) * vol + 32.0);
+    const double cap = p->list_cap > 0 ? (double)p->list_cap : std::ceil((p->dim == 3 ? 2.0 : 3.0) * vol + 32.0);
     h->vcap = (int)std::min(65536.0, std::ceil(cap / 32.0) * 32.0);
     CKI(dalloc(&h->vlist, (size_t)h->vcap * n));
     CKI(dalloc(&h->vcnt, n));

@@ -53,7 +53,12 @@ struct Mat {
 };
 
 // Host-side table entry of a material.
+// SPH_EOS_STIFFENED_C0 becomes the stiffened gas with P_inf = rho0 c0^2 / gamma.
 inline Mat make_mat(int eos, double gamma, double rho0, double c0, double p_inf, double s_a) {
+  if (eos == SPH_EOS_STIFFENED_C0) {
+    eos = SPH_EOS_STIFFENED;
+    p_inf = rho0 * c0 * c0 / gamma;
+  }
   Mat m{eos, gamma, rho0, c0, p_inf, s_a, 0.0, 0};
   if (eos == SPH_EOS_TAIT) {
     m.tait_B = rho0 * c0 * c0 / gamma;

@@ -536,12 +536,12 @@ cudaError_t launch_balance(sph_handle* h, const sph_state& s, double* gen, int K
 
 // ---------------------------------------------------------------------------
 // Allocation-free Voronoi assignment for callers that cannot allocate device
-// memory (no counterpart in the paper).  Code that runs while a CUDA stream
-// is being captured into a graph, code whose device memory is all owned by
-// another pool (a framework's caching allocator, a fixed arena), or a host
-// loop that must not call cudaMalloc, cannot create a handle, whose
-// workspace is allocated in sph_init.  This entry point takes only the
-// caller's positions, generators and output arrays and keeps its scratch
+// memory (no counterpart in the paper): a host loop that must not call
+// cudaMalloc (an allocation synchronises the device and may fail under memory
+// pressure), or code whose device memory is all owned by another pool (a
+// framework's caching allocator, a fixed arena).  Such a caller cannot create
+// a handle, whose workspace sph_init allocates.  This entry point takes only
+// the caller's positions, generators and output arrays and keeps its scratch
 // (per-unit counts, their scan and a counter) in one file-scope device array
 // of fixed size, so it allocates nothing.
 // ---------------------------------------------------------------------------
@@ -572,7 +572,8 @@ constexpr int kMaxDevices = 64;
 int32_t* g_static_addr[kMaxDevices] = {};
 
 // Device address of the scratch on the current device, resolved once per
-// device with that device current.
+// device with that device current and kept for the life of the process
+// (stale after cudaDeviceReset, which unloads the module).
 cudaError_t static_scratch(int32_t** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -620,16 +621,25 @@ extern "C" int voronoi_assign_static(int64_t n, const double* x, const double* y
   int64_t* total = reinterpret_cast<int64_t*>(scr + kOffTail);
   unsigned long long* exact = reinterpret_cast<unsigned long long*>(scr + kOffTail + 2);
   const size_t smem = sizeof(int) * 32 * K;
+  // every launch is checked as soon as it is issued, so a failure is reported
+  // by the launch that caused it
   k_static_reset<<<1, 1, 0, st>>>(total, exact, tot);   // the previous call left its values here
-  launch_assign_kernel(n, dim, x, y, z, gen, K, unit_out, exact, st);
-  k_unit_hist<<<nb, kUnitBlock, smem, st>>>(unit_out, n, K, nb, counts);   // writes every count
   e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_assign_kernel(n, dim, x, y, z, gen, K, unit_out, exact, st);
+  if (e == cudaSuccess) {
+    k_unit_hist<<<nb, kUnitBlock, smem, st>>>(unit_out, n, K, nb, counts);   // writes every count
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = launch_exclusive_scan(counts, total, sums, starts, n, tot, st);
-  if (e == cudaSuccess && unit_list) k_unit_scatter<<<nb, kUnitBlock, smem, st>>>(unit_out, n, K, nb, starts, unit_list);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && unit_list) {
+    k_unit_scatter<<<nb, kUnitBlock, smem, st>>>(unit_out, n, K, nb, starts, unit_list);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
     k_unit_offsets<<<grid_for(K + 1, kBlock), kBlock, 0, st>>>(starts, K, nb, n,
                                                              unit_offsets ? unit_offsets : scr + kOffUnitOff, nullptr);
-  if (e == cudaSuccess) e = cudaGetLastError();
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) {
     set_global_error(std::string("voronoi_assign_static: ") + cudaGetErrorString(e));
     return SPH_ERR_CUDA;

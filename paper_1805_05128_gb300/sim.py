@@ -11,7 +11,7 @@ import torch
 from . import abi
 
 _EOS = {"ideal": abi.SPH_EOS_IDEAL, "stiffened": abi.SPH_EOS_STIFFENED, "tait": abi.SPH_EOS_TAIT,
-        "mie_gruneisen": abi.SPH_EOS_MIE_GRUNEISEN}
+        "mie_gruneisen": abi.SPH_EOS_MIE_GRUNEISEN, "stiffened_c0": abi.SPH_EOS_STIFFENED_C0}
 _KERNEL = {"cubic": abi.SPH_KERNEL_CUBIC, "wendland_c2": abi.SPH_KERNEL_WENDLAND_C2}
 _PREC = {"fp64": abi.SPH_PREC_FP64, "mixed": abi.SPH_PREC_MIXED}
 _SOLVER = {"acoustic": abi.SPH_SOLVER_ACOUSTIC, "hll": abi.SPH_SOLVER_HLL}
@@ -33,7 +33,7 @@ class Simulation:
                  generators=None, n_upd: int | None = None, theta: float = 0.25, sigma: float = 0.5,
                  gamma_b: float = 1.0, beta_sh: float = 0.45, cell_cap: int = 1 << 24, cell_beta: float = 0.0,
                  pair_blocks_per_sm: int = 0, order: int = 1, solver: str = "acoustic",
-                 load_measure: str = "pairs",
+                 load_measure: str = "pairs", list_cap: int = 0,
                  device: str | torch.device = "cuda:0"):
         if not isinstance(problems, (list, tuple)):
             problems = [problems]
@@ -98,6 +98,7 @@ class Simulation:
         prm.order = order
         prm.solver = _SOLVER[solver]
         prm.load_measure = _LOAD[load_measure]
+        prm.list_cap = list_cap
         prm.generators = self.gen.data_ptr() if self.gen is not None else None
         self.params = prm
         self.precision = precision

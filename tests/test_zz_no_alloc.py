@@ -1,8 +1,9 @@
 """voronoi_assign_static: the allocation-free Voronoi assignment, for callers
-that cannot allocate device memory (stream capture, a foreign allocator's
-arena, allocation-free host loops).  Its scratch is a fixed device array in
-the library, so these checks call it several times in a row and compare each
-result with the handle-based voronoi_assign on the same inputs.  This file is
+that cannot allocate device memory (a host loop that must not call cudaMalloc,
+code whose device memory belongs to another allocator or a fixed arena).  Its
+scratch is a fixed device array in the library, so these checks call it
+several times in a row and compare each result with the handle-based
+voronoi_assign on the same inputs.  This file is
 collected last on purpose: if it fails, a run that stops at the first
 failure has already run every other test.
 """
