@@ -492,6 +492,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
     }
     if (act) {
       nfull -= 1;   // the self pair
+      fw.fold();
       fw.write(a, i, nfull);
     }
     warp_counters(a, act, nfull, ncand, nexact, ui, lane,

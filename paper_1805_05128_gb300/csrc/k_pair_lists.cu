@@ -136,16 +136,18 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
         bool acc = false;
         if (kv) {
           T sx = T(0), sy = T(0), sz = T(0);
-          if (MIXED) {
+          if constexpr (MIXED) {
             const float4 U = unit_shift[e & 31u];
-            sx = (T)U.x * dcs;
-            sy = (T)U.y * dcs;
-            sz = (T)U.z * dcs;
+            const float2 sxy = mul2(f2(U.x, U.y), f2(dcs, dcs));
+            sx = sxy.x;
+            sy = sxy.y;
+            sz = U.z * dcs;
           }
           acc = fw.pair_listed(a, ii, Ai, Bi, Ci, ui, (int64_t)(e >> 5), sx, sy, sz, khdi, band, te);
         }
         nacc += __popc(__ballot_sync(0xffffffffu, acc) & hmask);
       }
+      fw.fold();
       // combine the half's sums (fixed butterfly order); the rates are scaled below, per lane
       const T srho = slot_sum(fw.s_rho), sfx = slot_sum(fw.s_fx);
       const T sfy = DIM >= 2 ? slot_sum(fw.s_fy) : T(0), sfz = DIM >= 3 ? slot_sum(fw.s_fz) : T(0);

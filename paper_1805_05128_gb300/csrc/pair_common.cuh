@@ -170,6 +170,30 @@ __device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a,
 __device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Paired FP32 arithmetic (Blackwell's FADD2 / FMUL2 / FFMA2: two independent
+// single-precision operations in one instruction, each rounded to nearest
+// exactly as the scalar operation would be).  The mixed pair loop is bound by
+// instruction issue, so pairing the x and y components, the independent rate
+// terms and the Kahan sums cuts its instruction count while every component
+// keeps the scalar code's bits.  a - b is formed as b * (-1) + a, one
+// rounding, as the scalar subtraction.
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// Two independent Kahan sums carried in the halves of paired operations.
+struct Kahan2 {
+  float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+  __device__ __forceinline__ void add(float2 v) {
+    const float2 y = sub2(v, c);
+    const float2 t = add2(s, y);
+    c = sub2(sub2(t, s), y);
+    s = t;
+  }
+};
+
 // Exact FP64 interaction test on the global positions, operation order of the oracle.
 __device__ __forceinline__ bool exact_accept(const PairArgs& a, int dim, int64_t pi, int64_t pj) {
   double dx = __dsub_rn(a.x[pj], a.x[pi]);
@@ -208,6 +232,24 @@ __device__ __forceinline__ T dw_fast(int kernel, T kappa, T r, T h, T ws) {
     const T norm = (DIM == 2) ? (T(7) / pi * ws) * iH * iH * iH : (T(21) / (T(2) * pi) * ws) * (iH * iH) * (iH * iH);
     return norm * (T(-20) * s * t * t * t);
   }
+}
+
+// dw_fast for the cubic spline in FP32 with the two polynomial pieces
+// evaluated side by side in paired operations.
+template <int DIM>
+__device__ __forceinline__ float dw_cubic_x2(float r, float h, float ws) {
+  const float ih = rcp_(h);
+  const float q = r * ih;
+  float norm;
+  if (DIM == 1) norm = (float(2.0 / 3.0) * ws) * ih * ih;
+  else if (DIM == 2) norm = (float(10.0 / (7.0 * 3.14159265358979323846)) * ws) * ih * ih * ih;
+  else norm = (float(1.0 / 3.14159265358979323846) * ws) * (ih * ih) * (ih * ih);
+  const float t = 2.f - q;
+  // (q (2.25 q - 3), -0.75 t t): inside q < 1 and for 1 <= q < 2
+  const float2 lin = fma2(f2(q, t), f2(2.25f, -0.75f), f2(-3.f, 0.f));
+  const float2 f = mul2(lin, f2(q, t));
+  const float v = q < 1.f ? f.x : (q < 2.f ? f.y : 0.f);
+  return norm * v;
 }
 
 // Cubic spline W'(r, h) = s h^-(D+1) g(q) and its derivatives
@@ -320,10 +362,23 @@ struct FwdAcc {
   using T = typename P::T;
   using V4 = typename P::V4;
   using VC = typename P::VC;
+  // mixed precision at order 1: the flux in paired FP32 operations
+  static constexpr bool kX2 = MIXED && !ORDER2;
   Kahan<T> s_rho, s_fx, s_fy, s_fz, s_q;
+  Kahan2 k_fxy, k_fzq;   // kX2: (a_x, a_y) and (a_z, E) sums in paired form, folded by fold()
   T dmax = T(0);
   int last_adj = -1;
   V4 gPi{}, gVi[3]{};   // order 2: i's gradients (set by the caller)
+
+  // Moves the paired sums into s_fx, s_fy, s_fz, s_q (call once, after the last pair).
+  __device__ __forceinline__ void fold() {
+    if constexpr (kX2) {
+      s_fx.s = k_fxy.s.x; s_fx.c = k_fxy.c.x;
+      s_fy.s = k_fxy.s.y; s_fy.c = k_fxy.c.y;
+      s_fz.s = k_fzq.s.x; s_fz.c = k_fzq.c.x;
+      s_q.s = k_fzq.s.y;  s_q.c = k_fzq.c.y;
+    }
+  }
 
   // e . g, in a fixed uncontracted order (sign-symmetric in e)
   static __device__ __forceinline__ T dot_e(const V4& g, T ex, T ey, T ez) {
@@ -358,7 +413,12 @@ struct FwdAcc {
   // order that j's side negates exactly)
   static __device__ __forceinline__ void separation(const V4& Ai, const V4& Aj, T sx, T sy, T sz, T& dx, T& dy,
                                                     T& dz) {
-    if (MIXED) {
+    if constexpr (kX2) {
+      const float2 dxy = add2(sub2(f2(Aj.x, Aj.y), f2(Ai.x, Ai.y)), f2(sx, sy));
+      dx = dxy.x;
+      dy = DIM >= 2 ? dxy.y : T(0);
+      dz = DIM >= 3 ? (Aj.z - Ai.z) + sz : T(0);
+    } else if (MIXED) {
       dx = (Aj.x - Ai.x) + sx;
       dy = DIM >= 2 ? (Aj.y - Ai.y) + sy : T(0);
       dz = DIM >= 3 ? (Aj.z - Ai.z) + sz : T(0);
@@ -383,6 +443,14 @@ struct FwdAcc {
     const V4 Aj = A[j];
     const V4 Bj = B[j];       // requested with A[j]: most candidates interact
     const VC Cj = C[j];
+    return pair_listed_ops(a, i, Ai, Bi, Ci, ui, j, Aj, Bj, Cj, sx, sy, sz, khdi, band, nexact);
+  }
+
+  // pair_listed with j's operands already at hand (staged by the caller).
+  __device__ __forceinline__ bool pair_listed_ops(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi,
+                                                  const VC& Ci, int ui, int64_t j, const V4& Aj, const V4& Bj,
+                                                  const VC& Cj, T sx, T sy, T sz, T khdi, float band,
+                                                  unsigned& nexact) {
     T dx, dy, dz;
     separation(Ai, Aj, sx, sy, sz, dx, dy, dz);
     const T r2 = P::r2_of(dx, dy, dz);
@@ -405,11 +473,60 @@ struct FwdAcc {
     return acc;
   }
 
+  // The mixed order-1 flux of flux_at below, in paired operations: the same
+  // rounded operations per component, so the same bits and the same exchange
+  // symmetry (e, the velocity jump and the momentum flux negate exactly on j's
+  // side, P* and W' are the same bits).
+  __device__ __forceinline__ void flux_x2(const PairArgs& a, const float4& Ai, const float4& Bi,
+                                          const float4& Ci, const float4& Aj, const float4& Bj, const float4& Cj,
+                                          float dx, float dy, float dz, float r2) {
+    const float ir = rsqrtf(r2);
+    const float r = r2 * ir;
+    const float2 exy = mul2(f2(dx, dy), f2(ir, ir));
+    const float ez = dz * ir;
+    float Zi = Ci.y, Zj = Cj.y;
+    if constexpr (HLL) { const float Zm = Zi > Zj ? Zi : Zj; Zi = Zm; Zj = Zm; }
+    const float zs = add_(Zi, Zj);
+    // v_j - v_i: relative packs plus the exact difference of the references
+    const float2 kij = sub2(f2(ref_x(Cj.z), ref_y(Cj.z)), f2(ref_x(Ci.z), ref_y(Ci.z)));
+    const float2 gxy = add2(sub2(f2(Bj.x, Bj.y), f2(Bi.x, Bi.y)), kij);
+    float gR = mul_(gxy.x, exy.x);
+    if (DIM >= 2) gR = fma_(gxy.y, exy.y, gR);
+    if (DIM >= 3) gR = fma_(__fadd_rn(__fsub_rn(Bj.z, Bi.z), Cj.w - Ci.w), ez, gR);
+    const float Pl = Ci.x, Pr = Cj.x;
+    float Ps, du;                                     // P*; v* - v_i^R
+    if (zs > 0.f) {
+      const float izs = rcp_(zs);
+      const float2 zp = mul2(f2(Zj, Zi), f2(Pl, Pr));
+      const float numP = add_(add_(zp.x, zp.y), mul_(mul_(Zi, Zj), -gR));
+      const float numu = add_(mul_(Zj, gR), sub_(Pl, Pr));
+      const float2 pu = mul2(f2(numP, numu), f2(izs, izs));
+      Ps = pu.x;
+      du = pu.y;
+    } else {
+      Ps = mul_(0.5f, add_(Pl, Pr));
+      du = mul_(0.5f, gR);
+    }
+    const float hij = a.eta_half_f * add_(Ai.w, Aj.w);
+    const float dW = a.kernel == SPH_KERNEL_CUBIC ? dw_cubic_x2<DIM>(r, hij, a.wscale_f)
+                                                  : dw_fast<float, DIM>(a.kernel, a.kappa_f, r, hij, a.wscale_f);
+    // momentum flux along e, without its factor 2 (carried by fscale; exact)
+    const float F = mul_(mul_(mul_(Bi.w, Bj.w), Ps), dW);
+    s_rho.add(Bj.w * (-du) * (-dW));
+    k_fxy.add(mul2(f2(F, F), exy));
+    k_fzq.add(mul2(f2(F, F), f2(ez, du)));
+  }
+
   __device__ __forceinline__ void flux_at(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi, const VC& Ci,
                                           int ui, int64_t j, const V4& Aj, const V4& Bj, const VC& Cj, T dx, T dy,
                                           T dz, T r2) {
     if constexpr (EXTRA) dmax = Aj.w > dmax ? Aj.w : dmax;
     if (!(r2 > T(0))) return;  // coincident particles: no direction, no flux
+    if constexpr (kX2) {
+      flux_x2(a, Ai, Bi, Ci, Aj, Bj, Cj, dx, dy, dz, r2);
+      side_outputs(a, i, ui, j);
+      return;
+    }
     const T ir = rsqrt_(r2);
     const T r = r2 * ir;
     const T ex = dx * ir, ey = dy * ir, ez = dz * ir;
@@ -501,6 +618,11 @@ struct FwdAcc {
     if (DIM >= 2) s_fy.add(mul_(F, ey));
     if (DIM >= 3) s_fz.add(mul_(F, ez));
     s_q.add(mul_(F, qv));
+    side_outputs(a, i, ui, j);
+  }
+
+  // EXTRA: the optional pair output and the unit adjacency of an interacting pair.
+  __device__ __forceinline__ void side_outputs(const PairArgs& a, int64_t i, int ui, int64_t j) {
     if constexpr (!EXTRA) return;
     if (a.pair_i) {
       const int32_t pi = a.perm[i], pj = a.perm[j];
