@@ -346,7 +346,9 @@ def run_extras(args, dev) -> dict:
     FP64), batching (256-instance ensemble, 100 steps in one CUDA
     graph, autotuned, vs 256 sequential single-instance runs) and
     differentiation (forward + reverse mode of a 203k-particle plate, 100
-    steps, checkpoints every 10)."""
+    steps, checkpoints every 10); the Voronoi units as the list kernel's work
+    partition (global queue, per-unit queues with and without stealing, VD3
+    against the static decomposition); and the disk test of Sec. 5."""
     import torch
     import synth
     from paper_1805_05128_gb300 import Simulation
@@ -480,7 +482,18 @@ def run_extras(args, dev) -> dict:
         "tuning": {"cell_beta": tune.cell_beta, "pair_blocks_per_sm": tune.pair_blocks,
                    "ms_per_step": {f"{k[0]}/{k[1]}": v for k, v in tune.timings.items()}}}
 
-    # (6) differentiation
+    # (6) the Voronoi units as the work partition of the list kernel: the global
+    # queue against per-unit queues with stealing and without (each unit owned by
+    # the same number of CTAs), each with VD3 balancing (theta 0.25, sigma 0.5)
+    # and with the static decomposition (gamma = theta = 0); 500 timed steps each,
+    # then the tail ratio max_k / mean_k of the units' completion times in the
+    # list kernel, sampled every 10 steps over 100 more steps
+    out["unit_partition"] = run_unit_partition(args, dev)
+
+    # (7) the disk test of Sec. 5 on the GPU
+    out["disk_balancing"] = run_disk(dev)
+
+    # (8) differentiation
     from paper_1805_05128_gb300.adjoint import RunSpec, csph_run
     q = synth.plate_impact(25, (120, 120, 13), a=1e-4, v=1000.0, units=0)
     A = q.arrays
@@ -525,6 +538,93 @@ def run_extras(args, dev) -> dict:
         np.max(np.abs(np.array(adj["mixed_fp32_reverse"]["grad"]) - g64) / np.abs(g64)))
     adj["workload"] = f"plate impact {q.n} particles, 100 steps, checkpoints every 10, d(rear-face v_z)/d(v, c0, gamma)"
     out["adjoint"] = adj
+    return out
+
+
+# (name, list-kernel schedule, theta, gamma of eq. (TotalOffset), load measure)
+UNIT_FORMS = (("global_queue", "global", 0.25, 1.0, "pairs"), ("units_steal_vd3", "units", 0.25, 1.0, "pairs"),
+              ("units_steal_static", "units", 0.0, 0.0, "pairs"),
+              ("units_owned_vd3", "units_owned", 0.25, 1.0, "pairs"),
+              ("units_owned_vd3_timed_loads", "units_owned", 0.25, 1.0, "time"),
+              ("units_owned_static", "units_owned", 0.0, 0.0, "pairs"))
+
+
+def run_unit_partition(args, dev, steps: int = 500) -> dict:
+    """Step time of the benchmark plate for each work partition of the list
+    kernel, and the spread of the units' completion times (Sec. 2: the step
+    waits for the most loaded unit; balancing evens the loads)."""
+    import torch
+    import synth
+    from paper_1805_05128_gb300 import Simulation
+    prob = synth.plate_impact(units=64, n_steps=500, **WORKLOADS[args.workload])
+    gen = synth.problem_generators(prob)
+    res = {"workload": f"{prob.n} particles, 64 units, beta {BETA}, rebalanced every 10 steps, {steps} steps"}
+    for name, sched, theta, gamma_b, load in UNIT_FORMS:
+        sim = Simulation(prob, precision="mixed", generators=gen, n_upd=10, cell_beta=BETA, unit_sched=sched,
+                         theta=theta, gamma_b=gamma_b, sigma=0.5, load_measure=load, device=dev)
+        sim.assign()
+        sim.build_cells()
+        sim.step(10)
+        torch.cuda.synchronize()
+        sim.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sim.step(steps)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        pair_ms, pair_launches, _ = sim.profile_read()
+        sim.profile(False)
+        r = {"ms_per_step": ms / steps, "pair_ms_per_launch": pair_ms / max(pair_launches, 1),
+             "value": prob.n * steps / (ms * 1e-3), "unit": UNIT}
+        if sched != "global":
+            tails = []
+            for _ in range(10):
+                sim.step(10)
+                ends = sim.unit_times()[:, 1]
+                tails.append(float(ends.max() / ends.mean()))
+            r["tail_ratio_mean"] = float(np.mean(tails))
+            r["tail_ratio_max"] = float(np.max(tails))
+        r["status"] = sim.read_status()
+        res[name] = r
+        sim.close()
+    return res
+
+
+def run_disk(dev, iters: int = 45) -> dict:
+    """The three-subdomain disk of Sec. 5 (127,230 particles at rest) balanced
+    on the GPU through voronoi_assign / the rate evaluation / voronoi_balance;
+    iterations until sum_k |g^_k - g_k| < 0.01 (eq. VDConvergence) for the
+    paper's four variants.  The paper's initial generators are not given, so
+    the counts are reported beside its 21 / 21 / 17 / 11, not compared."""
+    import json as _json
+    import synth
+    from paper_1805_05128_gb300 import Simulation
+    gold = _json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))["disk"]
+    D = synth.disk(gold["particles"], gold["radius"], gold["height"])
+    n, a = len(D["x"]), D["a"]
+    prob = synth.Problem("disk", 3, dict(x=D["x"], y=D["y"], z=D["z"], vx=np.zeros(n), vy=np.zeros(n),
+                                         vz=np.zeros(n), rho=np.ones(n), E=np.ones(n), m=np.full(n, a ** 3)),
+                         [synth.MaterialSpec("ideal", 1.4)], eta=1.3, units=3, unit_dim=2)
+    g0 = np.array([[0.0, 0.1], [-0.12, -0.25], [0.12, -0.25]])
+    paper = {"two_body": (0.0, 0.0, 21), "three_body": (1.0, 0.0, 21), "both": (0.5, 0.0, 17),
+             "both_cumulative": (0.5, 0.25, 11)}
+    out = {"workload": f"disk r 0.45, height 0.1, {n} particles, 3 units, initial loads ~0.53/0.24/0.24",
+           "criterion": "sum_k |g^_k - g_k| < 0.01"}
+    for name, (sigma, theta, ref) in paper.items():
+        sim = Simulation(prob, precision="fp64", generators=g0.copy(), n_upd=0, device=dev)
+        first, imb = None, None
+        for it in range(iters):
+            sim.assign()
+            sim.eval_rates()
+            load, _ = sim.unit_stats()
+            imb = float((load.max() - load.min()) / load.mean())
+            shift = float(sim.balance(theta=theta, sigma=sigma, gamma_b=1.0, beta_sh=0.45)[0])
+            if first is None and shift < 0.01:
+                first = it + 1
+        out[name] = {"sigma": sigma, "theta": theta, "iterations": first, "paper_iterations": ref,
+                     "final_load_imbalance": imb}
+        sim.close()
     return out
 
 

@@ -65,6 +65,16 @@ extern "C" {
                                   kernel spends on unit k's particles (timing-dependent, so the
                                   rebalancing is not reproducible bit for bit) */
 
+#define SPH_SCHED_GLOBAL 0       /* list kernel: warps take groups of 32 slots (cell order) from one global
+                                    counter, whatever their units */
+#define SPH_SCHED_UNITS 1        /* the Voronoi units are the work partition (Secs. 3-4 recast on one GPU):
+                                    at each list build the slots are ordered unit-major (cell order
+                                    inside a unit), each unit owning one contiguous range; each CTA
+                                    drains its home unit's queue, then steals from the following units */
+#define SPH_SCHED_UNITS_OWNED 2  /* as SPH_SCHED_UNITS without stealing: a unit is processed by its own
+                                    CTAs only (the paper's one subdomain per processor), so the step waits
+                                    for the most loaded unit */
+
 #define SPH_MAX_MAT 4
 #define SPH_MAX_UNITS 256
 
@@ -112,6 +122,9 @@ typedef struct sph_params {
                          neighbours of a uniform lattice within the buffered radius, plus 32);
                          otherwise at least 32 (SPH_ERR_INVALID below).  A list that would grow
                          past it is cut at the capacity and SPH_ERR_CAPACITY is latched. */
+  int32_t unit_sched; /* SPH_SCHED_*: work partition of the list kernel (needs cell_beta > 0 and
+                         n_units > 0; otherwise the global counter is used) */
+  int32_t pad4_;
 } sph_params;
 
 /* Particle state: structure of arrays in device memory, n elements each.
@@ -255,6 +268,15 @@ int sph_conservation(sph_handle* h, const sph_state* s, double* out, void* strea
  * SPH_LOAD_TIME half the accumulated SM cycles) and
  * adj_out (host, K*K bytes, 0/1).  Synchronises the stream. */
 int sph_unit_stats(sph_handle* h, double* load_out, uint8_t* adj_out, void* stream);
+
+/* Per-unit timing of the last list evaluation run with SPH_SCHED_UNITS or
+ * SPH_SCHED_UNITS_OWNED (the completion times whose spread the balancing of
+ * Sec. 2 minimises): out (host, 2 K doubles) receives, for unit k, the start
+ * of its first slot group and the end of its last, in ns from the earliest
+ * start of any unit (%globaltimer).  An empty unit reports 0, 0.
+ * Synchronises the stream.  Errors: SPH_ERR_INVALID if the handle does not
+ * partition the list kernel by units. */
+int sph_unit_times(sph_handle* h, double* out, void* stream);
 
 /* Synchronise the handle's last stream and report the device status word
  * (SPH_OK or the first SPH_ERR_* latched by a kernel) in *device_status;

@@ -18,6 +18,7 @@ SPH_EOS_IDEAL, SPH_EOS_STIFFENED, SPH_EOS_TAIT, SPH_EOS_MIE_GRUNEISEN, SPH_EOS_S
 SPH_PREC_FP64, SPH_PREC_MIXED = 0, 1
 SPH_SOLVER_ACOUSTIC, SPH_SOLVER_HLL = 0, 1
 SPH_LOAD_PAIRS, SPH_LOAD_TIME = 0, 1
+SPH_SCHED_GLOBAL, SPH_SCHED_UNITS, SPH_SCHED_UNITS_OWNED = 0, 1, 2
 SPH_MAX_MAT, SPH_MAX_UNITS = 4, 256
 
 ERROR_NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID", 2: "SPH_ERR_CAPACITY", 3: "SPH_ERR_NONFINITE",
@@ -27,7 +28,7 @@ ERROR_NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID", 2: "SPH_ERR_CAPACITY", 3: "SPH
 EXPORTS = ("sph_init", "sph_build_cells", "sph_eval_rates", "sph_step", "voronoi_assign", "voronoi_balance",
            "sph_conservation", "sph_unit_stats", "sph_read_status", "sph_last_error", "sph_pair_counts",
            "sph_cell_index", "sph_pair_list", "voronoi_assign_static", "sph_profile", "sph_profile_read",
-           "sph_step_adjoint", "sph_last_dt", "sph_step_dt", "sph_list_builds", "sph_destroy")
+           "sph_step_adjoint", "sph_last_dt", "sph_step_dt", "sph_list_builds", "sph_unit_times", "sph_destroy")
 
 
 class sph_material(C.Structure):
@@ -43,7 +44,8 @@ class sph_params(C.Structure):
                 ("theta", C.c_double), ("sigma", C.c_double), ("gamma_b", C.c_double), ("beta_sh", C.c_double),
                 ("generators", C.c_void_p), ("materials", C.c_void_p),
                 ("order", C.c_int32), ("solver", C.c_int32),
-                ("load_measure", C.c_int32), ("list_cap", C.c_int32)]
+                ("load_measure", C.c_int32), ("list_cap", C.c_int32),
+                ("unit_sched", C.c_int32), ("pad4_", C.c_int32)]
 
 
 STATE_F64 = ("x", "y", "z", "vx", "vy", "vz", "rho", "E", "m")
@@ -99,6 +101,7 @@ def lib() -> C.CDLL:
     L.sph_last_dt.argtypes = [vp, vp, vp]
     L.sph_step_dt.argtypes = [vp, C.POINTER(sph_state), i32, vp, vp, vp]
     L.sph_list_builds.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32), vp]
+    L.sph_unit_times.argtypes = [vp, C.POINTER(C.c_double), vp]
     L.sph_profile.argtypes = [vp, i32]
     L.sph_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.sph_destroy.argtypes = [vp]
@@ -182,6 +185,11 @@ def sph_list_builds(h, stream):
     b, c = C.c_int64(), C.c_int32()
     check(lib().sph_list_builds(h, C.byref(b), C.byref(c), C.c_void_p(stream)), h)
     return b.value, c.value
+
+
+def sph_unit_times(h, out, stream):
+    """out: host float64 array of 2 K (start, end per unit, ns)."""
+    check(lib().sph_unit_times(h, out.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(stream)), h)
 
 
 def sph_cell_index(h, state, cell_out_ptr, grid_out, stream):

@@ -45,7 +45,7 @@ void free_all(sph_handle* h) {
                   h->status, h->counters, h->scratch, h->adj_G,
                   h->adj_GR, h->adj_pair, h->adj_par, h->adj_W, h->adj_store, h->mat_dev, h->vlist, h->vcnt,
                   h->vref, h->vflag, h->grad_p, h->grad_v, h->adj64_A, h->adj64_B, h->adj64_C,
-                  h->adj64_rho, h->dt_key};
+                  h->adj64_rho, h->dt_key, h->e_of_c, h->perm_e, h->unit_eoff, h->packAc, h->unit_q, h->unit_t};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -125,6 +125,8 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     return fail(nullptr, SPH_ERR_INVALID, "unknown pair solver");
   if (p->load_measure != SPH_LOAD_PAIRS && p->load_measure != SPH_LOAD_TIME)
     return fail(nullptr, SPH_ERR_INVALID, "unknown load measure");
+  if (p->unit_sched < SPH_SCHED_GLOBAL || p->unit_sched > SPH_SCHED_UNITS_OWNED)
+    return fail(nullptr, SPH_ERR_INVALID, "unknown unit_sched");
   if (p->list_cap != 0 && (p->list_cap < 32 || p->list_cap > 65536))
     return fail(nullptr, SPH_ERR_INVALID, "list_cap must be 0 (default) or in [32, 65536]");
   if (p->n_mat < 1 || p->n_mat > kMaxMaterials || (p->n_mat > SPH_MAX_MAT && !p->materials))
@@ -323,6 +325,19 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     const int flags[4] = {1, 1, 0, 0};    // lists invalid until the first build
     CKI(cudaMemcpy(h->vflag, flags, sizeof(flags), cudaMemcpyHostToDevice));
     dp.vref = h->vref;
+    // the units as the list kernel's work partition
+    h->unit_sched = h->K > 0 ? p->unit_sched : SPH_SCHED_GLOBAL;
+    if (h->unit_sched != SPH_SCHED_GLOBAL) {
+      CKI(dalloc(&h->e_of_c, n));
+      CKI(dalloc(&h->perm_e, n));
+      CKI(dalloc(&h->unit_eoff, h->K + 1));
+      CKI(cudaMemset(h->unit_eoff, 0, sizeof(int32_t) * (h->K + 1)));
+      if (p->precision == SPH_PREC_MIXED) CKI(dalloc(reinterpret_cast<float4**>(&h->packAc), n));
+      else CKI(dalloc(reinterpret_cast<D4**>(&h->packAc), n));
+      CKI(dalloc(&h->unit_q, h->K));
+      CKI(dalloc(&h->unit_t, (size_t)2 * h->K));
+      CKI(cudaMemset(h->unit_t, 0, sizeof(unsigned long long) * 2 * h->K));
+    }
   }
 
   CKI(launch_check_finite(h, *s, st));
@@ -408,10 +423,12 @@ int sph_step(sph_handle* h, sph_state* s, int n_steps, double* t_dev, void* stre
       // says so (validity criterion failed or lists invalidated); the kernels read the flag
       CK(h, launch_verlet_flag(h, st));
       CK(h, launch_build_grid(h, *s, st, h->vflag));
+      // unit-major evaluation order of the slots (at builds only)
+      if (h->unit_sched != SPH_SCHED_GLOBAL) CK(h, launch_eorder(h, *s, st));
     } else {
       CK(h, launch_build_grid(h, *s, st));
     }
-    CK(h, launch_pack(h, *s, true, st));
+    CK(h, launch_pack(h, *s, true, st, h->verlet && h->unit_sched != SPH_SCHED_GLOBAL));
     // unit adjacency is needed only from the evaluation that precedes a rebalance
     h->collect_adj = !vd3 || h->steps_since_balance + 1 >= h->p.n_upd;
     const bool next_dt = k + 1 < n_steps;
@@ -434,7 +451,14 @@ int sph_step(sph_handle* h, sph_state* s, int n_steps, double* t_dev, void* stre
       if (rc) return rc;
       rc = assign_impl(h, s, h->p.generators, h->K, h->gdim, s->unit, nullptr, st);
       if (rc) return rc;
-      CK(h, launch_renumber(h, *s, st));
+      if (h->verlet && h->unit_sched != SPH_SCHED_GLOBAL) {
+        // renumber unit-major (cell order inside a unit), the evaluation order
+        // of the new units, so that the list kernel walks the state in order
+        CK(h, launch_eorder(h, *s, st, true));
+        CK(h, launch_renumber(h, *s, st, h->perm_e));
+      } else {
+        CK(h, launch_renumber(h, *s, st));
+      }
     }
   }
   return SPH_OK;
@@ -510,6 +534,27 @@ int sph_unit_stats(sph_handle* h, double* load_out, uint8_t* adj_out, void* stre
     if (load_out) load_out[k] = 0.5 * (double)acc[k];
     if (adj_out)
       for (int l = 0; l < K; ++l) adj_out[k * K + l] = (bits[(size_t)k * words + (l >> 5)] >> (l & 31)) & 1u;
+  }
+  return SPH_OK;
+}
+
+int sph_unit_times(sph_handle* h, double* out, void* stream) {
+  if (!h) return SPH_ERR_INVALID;
+  if (h->unit_sched == SPH_SCHED_GLOBAL || !h->unit_t)
+    return fail(h, SPH_ERR_INVALID, "the list kernel is not partitioned by units (unit_sched, cell_beta, n_units)");
+  if (!out) return fail(h, SPH_ERR_INVALID, "out is NULL");
+  std::vector<unsigned long long> t((size_t)2 * h->K);
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(h, cudaMemcpyAsync(t.data(), h->unit_t, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  const int K = h->K;                    // starts in t[0, K), ends in t[K, 2K)
+  unsigned long long t0 = ~0ull;
+  for (int k = 0; k < K; ++k)
+    if (t[K + k] > 0 && t[k] < t0) t0 = t[k];
+  for (int k = 0; k < K; ++k) {
+    const bool used = t[K + k] > 0;
+    out[2 * k] = used ? (double)(t[k] - t0) : 0.0;
+    out[2 * k + 1] = used ? (double)(t[K + k] - t0) : 0.0;
   }
   return SPH_OK;
 }

@@ -202,6 +202,19 @@ struct sph_handle {
   double* vref = nullptr;             // [4 n] x, y, z, d of each particle at the last build
   int* vflag = nullptr;               // [0]: rebuild in this step; [1]: lists invalid; [2]: builds done
 
+  // Work units as the partition of the list kernel's work (Verlet lists with
+  // n_units > 0 and unit_sched > 0): at every list build the cell-order slots
+  // are stably partitioned by unit into an evaluation order in which every
+  // unit owns one contiguous range of slots; the packed operands and the lists
+  // are laid out in that order and the list kernel drains per-unit queues.
+  int unit_sched = 0;                 // SPH_SCHED_*
+  int32_t* e_of_c = nullptr;          // [n] evaluation slot of each cell-order slot
+  int32_t* perm_e = nullptr;          // [n] particle of each evaluation slot
+  int32_t* unit_eoff = nullptr;       // [K + 1] start of each unit's evaluation range
+  void* packAc = nullptr;             // [n] cell-order copy of the position / size operand (list build)
+  unsigned long long* unit_q = nullptr;   // [K] per-unit work counters of the list kernel
+  unsigned long long* unit_t = nullptr;   // [2K] first group start and last group end per unit (ns)
+
   // order-2 reconstruction (sph_params.order = 2): SPH gradients in slot order,
   // the pair kernel's precision: grad P, then grad v_x, grad v_y, grad v_z
   bool order2 = false;
@@ -305,11 +318,14 @@ cudaError_t launch_kick_drift(sph_handle* h, const sph_state& s, cudaStream_t st
 // gate (Verlet mode): device flag, the mesh kernels return at once while gate[0] == 0
 cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st, const int* gate = nullptr);
 cudaError_t launch_verlet_flag(sph_handle* h, cudaStream_t st);
-cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st);
+// eorder: write the packs in the unit-major evaluation order of the last build (e_of_c), the
+// particle of each evaluation slot (perm_e) and, at builds, the cell-order copy packAc
+cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st, bool eorder = false);
 // next_dt: also leave the CFL block minima of the new state in h->part (the next
 // step's dt without a k_derive pass)
 cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st, bool next_dt = false);
-cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st);
+// order: the particle to place at each position (NULL: h->perm, the cell order of the last mesh)
+cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st, const int32_t* order = nullptr);
 // rates VJP at the state packed by launch_pack (k_adjoint.cu); fp64_pairs: the
 // operands were packed in FP64 by launch_pack_fp64 into adj64_* (mixed handle)
 cudaError_t launch_rates_vjp(sph_handle* h, const sph_state& W, sph_state& adj, const double* dt, int predicted,
@@ -318,8 +334,9 @@ cudaError_t launch_pack_fp64(sph_handle* h, const sph_state& s, bool predict, vo
                              double* rho_out, cudaStream_t st);
 // Exclusive scan of cnt[0, *total) into start[0, *total], start[*total] = n_total;
 // cnt is zeroed; launched for up to `cap` elements.
+// gate (may be NULL): the kernels return at once while gate[0] == 0
 cudaError_t launch_exclusive_scan(int32_t* cnt, const int64_t* total, int32_t* sums, int32_t* start,
-                                  int64_t n_total, int64_t cap, cudaStream_t st);
+                                  int64_t n_total, int64_t cap, cudaStream_t st, const int* gate = nullptr);
 cudaError_t launch_conservation(sph_handle* h, const sph_state& s, double* out, cudaStream_t st);
 cudaError_t launch_check_finite(sph_handle* h, const sph_state& s, cudaStream_t st);
 cudaError_t launch_max_volume(sph_handle* h, const sph_state& s, unsigned long long* out, cudaStream_t st);
@@ -341,5 +358,8 @@ cudaError_t launch_unit_lists(sph_handle* h, const int32_t* unit, int32_t* unit_
 cudaError_t launch_balance(sph_handle* h, const sph_state& s, double* gen, int K, int dim,
                            const double* load, const sph_balance_params& bp, double* shift_out,
                            cudaStream_t st);
+// Evaluation order of the unit-partitioned list kernel (gated on vflag[0], at list builds only,
+// unless forced): e_of_c, perm_e, unit_eoff from the cell-order slots and the units of their particles.
+cudaError_t launch_eorder(sph_handle* h, const sph_state& s, cudaStream_t st, bool force = false);
 
 }  // namespace csph

@@ -77,7 +77,9 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t total = *a.total_cells_dev;
-  const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
+  // the list build reads the cell-order copy of the positions when the lists
+  // are laid out in the unit-major evaluation order
+  const V4* __restrict__ A = reinterpret_cast<const V4*>(LIST && a.Ac ? a.Ac : a.A);
   const V4* __restrict__ B = reinterpret_cast<const V4*>(a.B);
   const VC* __restrict__ C = reinterpret_cast<const VC*>(a.C);
   if constexpr (LIST) {
@@ -306,7 +308,8 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
       for (int hp = 0; hp < nh; ++hp) {
         const int n = __shfl_sync(0xffffffffu, cnt, hp);
         int v0 = __shfl_sync(0xffffffffu, vc, hp);
-        const int64_t ih = h0 + hp;
+        const int64_t ih = a.e_of_c ? (int64_t)a.e_of_c[h0 + hp] : (int64_t)(h0 + hp);   // the row's slot
+        const int64_t ihc = h0 + hp;                                                          // cell order
         for (int k0 = 0; k0 < n; k0 += 32) {
           const int k = k0 + lane;
           uint32_t word = 0;
@@ -314,8 +317,9 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
           if (k < n) {
             const unsigned ent = list[warp][hp][k];
             const int64_t j = (int64_t)__float_as_int(nb_tab[warp][ent >> 11].x) + (ent & 2047u);
-            w = j != ih;
-            word = ((uint32_t)j << 5) | (ent >> 11);
+            w = j != ihc;
+            const int64_t je = a.e_of_c ? (int64_t)a.e_of_c[j] : j;
+            word = ((uint32_t)je << 5) | (ent >> 11);
           }
           const unsigned m = __ballot_sync(0xffffffffu, w);
           const int pos = v0 + __popc(m & lt);
@@ -466,7 +470,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
     if constexpr (LIST) {
       if (act) {
         if (vc > a.vcap) set_status(a.status, SPH_ERR_CAPACITY);
-        a.vcnt[i] = vc < a.vcap ? vc : a.vcap;
+        a.vcnt[a.e_of_c ? a.e_of_c[i] : i] = vc < a.vcap ? vc : a.vcap;
         const int64_t p = a.perm[i];
         a.vref[p] = a.x[p];
         if (DIM >= 2) a.vref[a.n + p] = a.y[p];
@@ -584,6 +588,10 @@ cudaError_t launch_list_build(sph_handle* h, const sph_state& s, cudaStream_t st
   const double khl = h->dp.kh * (1.0 + h->dp.cell_beta);
   a.kh = khl;
   a.kh_f = (float)khl;
+  if (h->unit_sched != SPH_SCHED_GLOBAL) {   // rows and entries in the unit-major evaluation order
+    a.e_of_c = h->e_of_c;
+    a.Ac = h->packAc;
+  }
   cudaError_t e = cudaMemsetAsync(&h->counters[5], 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, kModeList>(h, a, st)

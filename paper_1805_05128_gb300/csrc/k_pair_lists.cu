@@ -64,14 +64,76 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
   const int half = lane / kSlotLanes, hl = lane % kSlotLanes;   // the slot's group of lanes, lane in it
   const unsigned hmask = (kSlotLanes == 32 ? 0xffffffffu : ((1u << kSlotLanes) - 1u)) << (half * kSlotLanes);
   const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
+  // Work partition.  SPH_SCHED_GLOBAL: groups of 32 consecutive slots from one
+  // global counter.  Units: each unit owns a contiguous range of evaluation
+  // slots and a counter; CTA b starts on unit b K / gridDim.x (the CTAs are
+  // spread evenly over the units), takes groups of 32 slots of that unit and,
+  // with SPH_SCHED_UNITS, moves on to the following units once it is drained
+  // (each unit tried once; a drained unit is recognised by a plain read).  With
+  // SPH_SCHED_UNITS_OWNED a warp stops when its home unit is drained.  Every
+  // loop is bounded: no warp waits on another.
+  // The scheduling state lives in shared memory (lane 0 of each warp), which
+  // keeps the registers of the pair loop free.
+  __shared__ int u_cur[kWarps], u_left[kWarps];
+  __shared__ unsigned long long t_grp[kWarps];
+  if (lane == 0) {
+    // Home unit.  With stealing: from the SM the CTA runs on (the CTAs of one
+    // SM share its L1, so they work on one unit's neighbourhood).  Owned: the
+    // grid is K times the CTAs per unit and CTA b serves unit b / (gridDim.x / K),
+    // so that every unit has the same resources and the step waits only for
+    // the most loaded unit.
+    int u = 0;
+    if (a.unit_sched == SPH_SCHED_UNITS) {
+      unsigned smid, nsm;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+      asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+      u = (int)(((long long)smid * a.K) / (nsm > 0 ? nsm : 1));
+    } else if (a.unit_sched == SPH_SCHED_UNITS_OWNED) {
+      const int per = (int)gridDim.x / a.K;
+      u = (int)blockIdx.x / (per > 0 ? per : 1);
+    }
+    u_cur[warp] = u < a.K ? u : a.K - 1;
+    u_left[warp] = a.K;
+  }
   for (;;) {
     // slots in 32 bits: list entries hold slot indices in 27 bits
-    unsigned long long gw = 0;
-    if (lane == 0) gw = atomicAdd(a.work_counter, 32ull);
-    gw = __shfl_sync(0xffffffffu, gw, 0);
-    if ((int64_t)gw >= a.n) break;
-    const int g0 = (int)gw;
-    const int g1 = (int64_t)g0 + 32 < a.n ? g0 + 32 : (int)a.n;
+    int g0 = 0, g1 = 0;
+    if (a.unit_sched == SPH_SCHED_GLOBAL) {
+      unsigned long long gw = 0;
+      if (lane == 0) gw = atomicAdd(a.work_counter, 32ull);
+      gw = __shfl_sync(0xffffffffu, gw, 0);
+      if ((int64_t)gw >= a.n) break;
+      g0 = (int)gw;
+      g1 = (int64_t)g0 + 32 < a.n ? g0 + 32 : (int)a.n;
+    } else {
+      int ok = 0;
+      if (lane == 0) {
+        int u = u_cur[warp];
+        for (;;) {
+          const int ub = a.unit_eoff[u], ue = a.unit_eoff[u + 1];
+          const unsigned long long size = (unsigned long long)(ue - ub);
+          if (*reinterpret_cast<volatile unsigned long long*>(&a.unit_q[u]) < size) {
+            const unsigned long long old = atomicAdd(&a.unit_q[u], 32ull);
+            if (old < size) {
+              g0 = ub + (int)old;
+              g1 = g0 + 32 < ue ? g0 + 32 : ue;
+              ok = 1;
+              break;
+            }
+          }
+          if (a.unit_sched == SPH_SCHED_UNITS_OWNED || --u_left[warp] <= 0) break;
+          u = u + 1 == a.K ? 0 : u + 1;
+        }
+        u_cur[warp] = u;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        t_grp[warp] = t;
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      g0 = __shfl_sync(0xffffffffu, g0, 0);
+      g1 = __shfl_sync(0xffffffffu, g1, 0);
+    }
     int unit_run = -1;
     unsigned unit_load = 0;
     unsigned tf = 0, tc = 0, te = 0;
@@ -256,6 +318,12 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
       atomicAdd(&a.counters[0], (unsigned long long)tf);
       atomicAdd(&a.counters[1], (unsigned long long)tc);
       atomicAdd(&a.counters[2], (unsigned long long)te);
+      if (a.unit_sched != SPH_SCHED_GLOBAL) {         // the unit's first start and last end
+        unsigned long long t_end;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+        atomicMin(&a.unit_t[u_cur[warp]], t_grp[warp]);
+        atomicMax(&a.unit_t[a.K + u_cur[warp]], t_end);
+      }
     }
   }
 }
@@ -271,7 +339,10 @@ cudaError_t launch_lists_one(const PairArgs& args, int blocks_per_sm, cudaStream
     if (per_sm < 1) per_sm = 1;
   }
   const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
-  k_pair_lists<MIXED, DIM, HLL, EXTRA><<<sms * b, kPairBlock, 0, st>>>(args);
+  int grid = sms * b;
+  if (args.unit_sched == SPH_SCHED_UNITS_OWNED && args.K > 0)   // the same number of CTAs for every unit
+    grid = args.K * (grid / args.K > 0 ? grid / args.K : 1);
+  k_pair_lists<MIXED, DIM, HLL, EXTRA><<<grid, kPairBlock, 0, st>>>(args);
   return cudaGetLastError();
 }
 
@@ -315,6 +386,19 @@ cudaError_t launch_pair_lists(sph_handle* h, const sph_state& s, cudaStream_t st
   a.dp = h->dp;
   cudaError_t e = cudaMemsetAsync(h->counters, 0, 3 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  if (h->unit_sched != SPH_SCHED_GLOBAL) {
+    // operands, lists and rows in the unit-major evaluation order; per-unit
+    // queues and times reset for this launch (starts to the maximum, ends to 0)
+    a.perm = h->perm_e;
+    a.e_of_c = h->e_of_c;
+    a.unit_eoff = h->unit_eoff;
+    a.unit_q = h->unit_q;
+    a.unit_t = h->unit_t;
+    a.unit_sched = h->unit_sched;
+    if ((e = cudaMemsetAsync(h->unit_q, 0, sizeof(unsigned long long) * h->K, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(h->unit_t, 0xff, sizeof(unsigned long long) * h->K, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(h->unit_t + h->K, 0, sizeof(unsigned long long) * h->K, st)) != cudaSuccess) return e;
+  }
   e = cudaMemsetAsync(&h->counters[5], 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   if ((e = prof_record(h, true, st)) != cudaSuccess) return e;

@@ -515,11 +515,17 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
                        const GridInfo* __restrict__ grid, const double* __restrict__ dt, int predict,
                        const int32_t* __restrict__ perm, const int32_t* __restrict__ cell_of,
                        void* packA, void* packB, void* packC, double* rho_slot, int32_t* slot_cell,
-                       int32_t* slot_unit, int n_units, int* status) {
-  int64_t sl = blk_start[blockIdx.x] + threadIdx.x;
-  if (sl >= blk_end[blockIdx.x]) return;
+                       int32_t* slot_unit, int n_units, int* status, const int32_t* __restrict__ e_of_c,
+                       int32_t* perm_e, void* packAc, const int* __restrict__ gate) {
+  const int64_t sc = blk_start[blockIdx.x] + threadIdx.x;     // cell-order slot
+  if (sc >= blk_end[blockIdx.x]) return;
+  // the operands go to the slot's evaluation position (unit-major order of the
+  // last list build), or to the cell-order slot itself
+  const int64_t sl = e_of_c ? (int64_t)e_of_c[sc] : sc;
+  const bool build = packAc && gate && gate[0] != 0;          // a list build follows: cell-order copy of A
   int b = blk_inst[blockIdx.x];
-  int64_t p = perm[sl];
+  int64_t p = perm[sc];
+  if (perm_e) perm_e[sl] = (int32_t)p;
   // every load of the gathered particle first (the stores to P and c below
   // would otherwise hold back the loads placed after them)
   const bool pr = predict != 0;
@@ -578,7 +584,9 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
     int64_t cc[3] = {c0, c1, c2};
     float off[3] = {0.f, 0.f, 0.f};
     for (int a = 0; a < P.dim; ++a) off[a] = (float)(X[a] - (g.x0[a] + (double)cc[a] * g.dc));
-    reinterpret_cast<float4*>(packA)[sl] = make_float4(off[0], off[1], off[2], (float)d);
+    const float4 Arec = make_float4(off[0], off[1], off[2], (float)d);
+    reinterpret_cast<float4*>(packA)[sl] = Arec;
+    if (build) reinterpret_cast<float4*>(packAc)[sc] = Arec;
     const float Vp = fast ? ((float)m / (float)rho) * (float)P.vscale : (float)((m / rho) * P.vscale);
     // FP32 velocities relative to a reference velocity of whole m/s per
     // particle (k = v truncated, |k| <= 32767): v - k is exact in FP64 and
@@ -597,6 +605,7 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
                                                        __uint_as_float(kxy), (float)k[2]);
   } else {
     reinterpret_cast<D4*>(packA)[sl] = D4{X[0], X[1], X[2], d};
+    if (build) reinterpret_cast<D4*>(packAc)[sc] = D4{X[0], X[1], X[2], d};
     reinterpret_cast<D4*>(packB)[sl] = D4{v[0], v[1], v[2], m / rho};
     reinterpret_cast<D2*>(packC)[sl] = D2{Pp, rho * cp};
   }
@@ -768,15 +777,20 @@ cudaError_t launch_verlet_flag(sph_handle* h, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st) {
+cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st, bool eorder) {
+  const int32_t* eoc = eorder ? h->e_of_c : nullptr;
+  int32_t* pe = eorder ? h->perm_e : nullptr;
+  void* Ac = eorder ? h->packAc : nullptr;
   if (h->dp.precision == SPH_PREC_MIXED)
     k_pack<true><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->grid, h->dt,
                                              predict ? 1 : 0, h->perm, h->cell_of, h->packA, h->packB, h->packC,
-                                             h->rho_slot, h->slot_cell, h->slot_unit, h->K, h->status);
+                                             h->rho_slot, h->slot_cell, h->slot_unit, h->K, h->status, eoc, pe, Ac,
+                                             h->vflag);
   else
     k_pack<false><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->grid, h->dt,
                                               predict ? 1 : 0, h->perm, h->cell_of, h->packA, h->packB, h->packC,
-                                              h->rho_slot, h->slot_cell, h->slot_unit, h->K, h->status);
+                                              h->rho_slot, h->slot_cell, h->slot_unit, h->K, h->status, eoc, pe, Ac,
+                                              h->vflag);
   h->launches += 1;
   return cudaGetLastError();
 }
@@ -788,7 +802,7 @@ cudaError_t launch_pack_fp64(sph_handle* h, const sph_state& s, bool predict, vo
                              double* rho_out, cudaStream_t st) {
   k_pack<false><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->grid, h->dt,
                                             predict ? 1 : 0, h->perm, h->cell_of, A, B, C, rho_out, h->slot_cell,
-                                            h->slot_unit, h->K, h->status);
+                                            h->slot_unit, h->K, h->status, nullptr, nullptr, nullptr, nullptr);
   h->launches += 1;
   return cudaGetLastError();
 }
@@ -805,7 +819,7 @@ cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st) {
+cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st, const int32_t* order) {
   PermArrays a;
   a.count = 0;
   auto add = [&](void* ptr, int bytes) {
@@ -819,7 +833,7 @@ cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st) {
   add(s.id, 8);
   add(s.mat, 4); add(s.unit, 4);
   int g = grid_for(h->n, kBlock);
-  k_gather<<<g, kBlock, 0, st>>>(h->n, h->perm, a, reinterpret_cast<char*>(h->scratch));
+  k_gather<<<g, kBlock, 0, st>>>(h->n, order ? order : h->perm, a, reinterpret_cast<char*>(h->scratch));
   k_scatter_back<<<g, kBlock, 0, st>>>(h->n, a, reinterpret_cast<const char*>(h->scratch));
   h->launches += 2;
   // particle indices changed under the slot order of the Verlet lists
@@ -828,11 +842,11 @@ cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st) {
 }
 
 cudaError_t launch_exclusive_scan(int32_t* cnt, const int64_t* total, int32_t* sums, int32_t* start,
-                                  int64_t n_total, int64_t cap, cudaStream_t st) {
+                                  int64_t n_total, int64_t cap, cudaStream_t st, const int* gate) {
   int tiles = capped_grid(grid_for(cap, kScanTile));
-  k_scan_reduce<<<tiles, kBlock, 0, st>>>(cnt, total, sums, nullptr);
-  k_scan_sums<<<1, 1024, 0, st>>>(sums, total, nullptr);
-  k_scan_down<<<tiles, kBlock, 0, st>>>(cnt, total, sums, start, n_total, nullptr);
+  k_scan_reduce<<<tiles, kBlock, 0, st>>>(cnt, total, sums, gate);
+  k_scan_sums<<<1, 1024, 0, st>>>(sums, total, gate);
+  k_scan_down<<<tiles, kBlock, 0, st>>>(cnt, total, sums, start, n_total, gate);
   return cudaGetLastError();
 }
 // (launch_exclusive_scan's three kernels are counted by its callers)

@@ -157,7 +157,9 @@ __device__ __forceinline__ void warp_unit_counts(const int32_t* unit, int64_t n,
   if (my_unit >= 0 && rank_in_warp == 0) wcnt[w * K + my_unit] = __popc(same);
 }
 
-__global__ void k_unit_hist(const int32_t* __restrict__ unit, int64_t n, int K, int nb, int32_t* counts) {
+__global__ void k_unit_hist(const int32_t* __restrict__ unit, int64_t n, int K, int nb, int32_t* counts,
+                            const int* __restrict__ gate = nullptr) {
+  if (gate && gate[0] == 0) return;   // evaluation order: only at list builds
   extern __shared__ int wcnt[];
   for (int k = threadIdx.x; k < 32 * K; k += blockDim.x) wcnt[k] = 0;
   __syncthreads();
@@ -172,7 +174,8 @@ __global__ void k_unit_hist(const int32_t* __restrict__ unit, int64_t n, int K, 
 }
 
 __global__ void k_unit_scatter(const int32_t* __restrict__ unit, int64_t n, int K, int nb,
-                               const int32_t* __restrict__ start, int32_t* list) {
+                               const int32_t* __restrict__ start, int32_t* list, const int* __restrict__ gate = nullptr) {
+  if (gate && gate[0] == 0) return;
   extern __shared__ int wcnt[];
   for (int k = threadIdx.x; k < 32 * K; k += blockDim.x) wcnt[k] = 0;
   __syncthreads();
@@ -192,7 +195,8 @@ __global__ void k_unit_scatter(const int32_t* __restrict__ unit, int64_t n, int 
 }
 
 __global__ void k_unit_offsets(const int32_t* __restrict__ start, int K, int nb, int64_t n, int32_t* unit_off,
-                               int32_t* out_copy) {
+                               int32_t* out_copy, const int* __restrict__ gate = nullptr) {
+  if (gate && gate[0] == 0) return;
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k > K) return;
   int32_t v = (k < K) ? start[(int64_t)k * nb] : (int32_t)n;
@@ -501,6 +505,59 @@ cudaError_t launch_unit_lists(sph_handle* h, const int32_t* unit, int32_t* unit_
   k_unit_scatter<<<nb, kUnitBlock, smem, st>>>(unit, h->n, K, nb, starts, h->unit_list);
   k_unit_offsets<<<grid_for(K + 1, kBlock), kBlock, 0, st>>>(starts, K, nb, h->n, h->unit_off, unit_offsets);
   h->launches += 6;
+  return cudaGetLastError();
+}
+
+namespace {
+
+// Unit of each cell-order slot (clamped into range, as k_pack does).
+__global__ void k_slot_units(int64_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ unit, int K,
+                             int32_t* slot_u, const int* __restrict__ gate) {
+  if (gate && gate[0] == 0) return;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    int u = unit[perm[c]];
+    slot_u[c] = (u < 0 || u >= K) ? 0 : u;
+  }
+}
+
+// Inverse of the partition (the evaluation slot of each cell-order slot) and
+// the particle of each evaluation slot.
+__global__ void k_eorder_inverse(int64_t n, const int32_t* __restrict__ c_of_e, const int32_t* __restrict__ perm,
+                                 int32_t* e_of_c, int32_t* perm_e, const int* __restrict__ gate) {
+  if (gate && gate[0] == 0) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = c_of_e[e];
+    e_of_c[c] = (int32_t)e;
+    perm_e[e] = perm[c];
+  }
+}
+
+}  // namespace
+
+// The unit-major evaluation order: a stable partition of the cell-order slots
+// by the unit of their particle (so cell order, and with it locality, is kept
+// inside each unit), the same block-histogram / scan / scatter as the unit
+// lists.  Gated on vflag[0] (it runs only when the lists are rebuilt) unless
+// forced (at a rebalance, where the state is then renumbered in this order).
+cudaError_t launch_eorder(sph_handle* h, const sph_state& s, cudaStream_t st, bool force) {
+  const int K = h->K;
+  const int nb = grid_for(h->n, kUnitBlock);
+  const size_t smem = sizeof(int) * 32 * K;
+  int32_t* counts = h->unit_work;                 // [K * nb]
+  int32_t* starts = counts + (size_t)K * nb;       // [K * nb + 1]
+  int32_t* sums = starts + (size_t)K * nb + 1;
+  int32_t* slot_u = h->rank;                        // free between a cell sort and the next one
+  int32_t* c_of_e = reinterpret_cast<int32_t*>(h->scratch);   // free outside the renumbering
+  const int* gate = force ? nullptr : h->vflag;
+  const int g = assign_grid(h->n);
+  k_slot_units<<<g, kBlock, 0, st>>>(h->n, h->perm, s.unit, K, slot_u, gate);
+  k_unit_hist<<<nb, kUnitBlock, smem, st>>>(slot_u, h->n, K, nb, counts, gate);
+  cudaError_t e = launch_exclusive_scan(counts, h->unit_total, sums, starts, h->n, h->unit_work_total, st, gate);
+  if (e != cudaSuccess) return e;
+  k_unit_scatter<<<nb, kUnitBlock, smem, st>>>(slot_u, h->n, K, nb, starts, c_of_e, gate);
+  k_unit_offsets<<<grid_for(K + 1, kBlock), kBlock, 0, st>>>(starts, K, nb, h->n, h->unit_eoff, nullptr, gate);
+  k_eorder_inverse<<<g, kBlock, 0, st>>>(h->n, c_of_e, h->perm, h->e_of_c, h->perm_e, gate);
+  h->launches += 8;
   return cudaGetLastError();
 }
 

@@ -85,6 +85,18 @@ struct PairArgs {
   double* kx_t;
   long long* dt_key;
   DevParams dp;
+  // unit-partitioned list evaluation (evaluation order): e_of_c maps a
+  // cell-order slot to its evaluation slot (NULL: the two orders coincide),
+  // Ac holds the position / size operand in cell order for the list build;
+  // unit_sched > 0: warps drain per-unit queues (unit_q) over the units'
+  // evaluation ranges (unit_eoff), with stealing when unit_sched == 1;
+  // unit_t receives each unit's first group start and last group end
+  const int32_t* e_of_c;
+  const void* Ac;
+  const int32_t* unit_eoff;
+  unsigned long long* unit_q;
+  unsigned long long* unit_t;
+  int unit_sched;
 };
 
 constexpr int kModeFwd = 0;    // rates
@@ -745,6 +757,12 @@ PairArgs make_args(sph_handle* h, const sph_state& s) {
   a.fscale = 2.0 / (h->vscale * h->vscale * h->wscale);   // with the factor 2 of the momentum flux
   a.rscale = 1.0 / (h->vscale * h->wscale);
   a.vinv = 1.0 / h->vscale;
+  a.e_of_c = nullptr;       // set by the Verlet-list launchers when the units partition the work
+  a.Ac = nullptr;
+  a.unit_eoff = nullptr;
+  a.unit_q = nullptr;
+  a.unit_t = nullptr;
+  a.unit_sched = SPH_SCHED_GLOBAL;
   return a;
 }
 

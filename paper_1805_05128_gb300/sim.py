@@ -16,6 +16,7 @@ _KERNEL = {"cubic": abi.SPH_KERNEL_CUBIC, "wendland_c2": abi.SPH_KERNEL_WENDLAND
 _PREC = {"fp64": abi.SPH_PREC_FP64, "mixed": abi.SPH_PREC_MIXED}
 _SOLVER = {"acoustic": abi.SPH_SOLVER_ACOUSTIC, "hll": abi.SPH_SOLVER_HLL}
 _LOAD = {"pairs": abi.SPH_LOAD_PAIRS, "time": abi.SPH_LOAD_TIME}
+_SCHED = {"global": abi.SPH_SCHED_GLOBAL, "units": abi.SPH_SCHED_UNITS, "units_owned": abi.SPH_SCHED_UNITS_OWNED}
 
 
 def _stream_ptr() -> int:
@@ -33,7 +34,7 @@ class Simulation:
                  generators=None, n_upd: int | None = None, theta: float = 0.25, sigma: float = 0.5,
                  gamma_b: float = 1.0, beta_sh: float = 0.45, cell_cap: int = 1 << 24, cell_beta: float = 0.0,
                  pair_blocks_per_sm: int = 0, order: int = 1, solver: str = "acoustic",
-                 load_measure: str = "pairs", list_cap: int = 0,
+                 load_measure: str = "pairs", list_cap: int = 0, unit_sched: str = "global",
                  device: str | torch.device = "cuda:0"):
         if not isinstance(problems, (list, tuple)):
             problems = [problems]
@@ -99,6 +100,7 @@ class Simulation:
         prm.solver = _SOLVER[solver]
         prm.load_measure = _LOAD[load_measure]
         prm.list_cap = list_cap
+        prm.unit_sched = _SCHED[unit_sched]
         prm.generators = self.gen.data_ptr() if self.gen is not None else None
         self.params = prm
         self.precision = precision
@@ -191,6 +193,12 @@ class Simulation:
     def list_builds(self):
         """(Verlet-list builds so far, list capacity per particle); needs cell_beta > 0."""
         return abi.sph_list_builds(self.handle, _stream_ptr())
+
+    def unit_times(self):
+        """(start, end) in ns of each unit's work in the last list evaluation (K x 2)."""
+        out = np.zeros(2 * self.K)
+        abi.sph_unit_times(self.handle, out, _stream_ptr())
+        return out.reshape(self.K, 2)
 
     def read_status(self) -> int:
         return abi.sph_read_status(self.handle)

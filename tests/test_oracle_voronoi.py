@@ -174,7 +174,8 @@ def test_disk_convergence(disk):
     combination with the cumulative movement (theta = 0.25) reaches the best
     decomposition, three equal sectors meeting at the disk centre, fastest.
     The paper's iteration counts (21/21/17/11) depend on its unstated initial
-    generators and are reported by the benchmark, not asserted."""
+    generators: parity unpinned.  The benchmark reports the GPU's counts for
+    the same start (extras.disk_balancing); they are not asserted."""
     g0 = np.array([[0.0, 0.1], [-0.12, -0.25], [0.12, -0.25]])
     two = _iterate(disk, g0, 0.0, 0.0)
     three = _iterate(disk, g0, 1.0, 0.0)
