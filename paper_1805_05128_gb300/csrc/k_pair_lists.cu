@@ -62,7 +62,6 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int half = lane / kSlotLanes, hl = lane % kSlotLanes;   // the slot's group of lanes, lane in it
-  const unsigned hmask = (kSlotLanes == 32 ? 0xffffffffu : ((1u << kSlotLanes) - 1u)) << (half * kSlotLanes);
   const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
   // Work partition.  SPH_SCHED_GLOBAL: groups of 32 consecutive slots from one
   // global counter.  Units: each unit owns a contiguous range of evaluation
@@ -183,7 +182,7 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
       const int ui = a.K > 0 ? a.slot_unit[ii] : 0;
       const uint32_t* __restrict__ row = a.vlist + (int64_t)ii * a.vcap;
       FwdAcc<MIXED, DIM, false, HLL, EXTRA> fw;
-      unsigned nacc = 0;                              // accepted pairs of i (uniform in the group)
+      unsigned nacc = 0;                              // accepted pairs of i (the slot's total after the loop)
       int cmax = cnt;                                 // chunks run by the whole warp
 #pragma unroll
       for (int o = kSlotLanes; o < 32; o <<= 1) {
@@ -207,9 +206,11 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
           }
           acc = fw.pair_listed(a, ii, Ai, Bi, Ci, ui, (int64_t)(e >> 5), sx, sy, sz, khdi, band, te);
         }
-        nacc += __popc(__ballot_sync(0xffffffffu, acc) & hmask);
+        nacc += acc ? 1u : 0u;                        // this lane's accepted entries
       }
       fw.fold();
+#pragma unroll
+      for (int o = kSlotLanes / 2; o > 0; o >>= 1) nacc += __shfl_xor_sync(0xffffffffu, nacc, o);   // slot total
       // combine the half's sums (fixed butterfly order); the rates are scaled below, per lane
       const T srho = slot_sum(fw.s_rho), sfx = slot_sum(fw.s_fx);
       const T sfy = DIM >= 2 ? slot_sum(fw.s_fy) : T(0), sfz = DIM >= 3 ? slot_sum(fw.s_fz) : T(0);

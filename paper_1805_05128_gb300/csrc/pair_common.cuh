@@ -481,7 +481,17 @@ struct FwdAcc {
       const double R = __dmul_rn(a.kh, __dadd_rn(Ai.w, Aj.w));
       acc = P::r2_of(ex, ey, ez) < __dmul_rn(R, R);
     }
-    if (acc) flux_at(a, i, Ai, Bi, Ci, ui, j, Aj, Bj, Cj, dx, dy, dz, r2);
+    if constexpr (kX2 && !EXTRA) {
+      // Branch-free: every listed entry runs the flux arithmetic, and the
+      // kernel derivative is set to zero where the pair does not interact
+      // (such entries lie at q >= kappa, where W' vanishes anyway; the select
+      // keeps the exact pair set).  With ~86 % of the entries interacting the
+      // lanes would run the flux almost always; the branches and their
+      // reconvergence cost more than the idle arithmetic.
+      flux_x2(a, Ai, Bi, Ci, Aj, Bj, Cj, dx, dy, dz, r2, acc && r2 > T(0));
+    } else {
+      if (acc) flux_at(a, i, Ai, Bi, Ci, ui, j, Aj, Bj, Cj, dx, dy, dz, r2);
+    }
     return acc;
   }
 
@@ -489,9 +499,12 @@ struct FwdAcc {
   // rounded operations per component, so the same bits and the same exchange
   // symmetry (e, the velocity jump and the momentum flux negate exactly on j's
   // side, P* and W' are the same bits).
+  // live = false: the terms are computed with W' = 0 (and a positive stand-in
+  // for r^2 = 0), so they add zeros; the caller then needs no branch.
   __device__ __forceinline__ void flux_x2(const PairArgs& a, const float4& Ai, const float4& Bi,
                                           const float4& Ci, const float4& Aj, const float4& Bj, const float4& Cj,
-                                          float dx, float dy, float dz, float r2) {
+                                          float dx, float dy, float dz, float r2, bool live = true) {
+    if (!(r2 > 0.f)) r2 = 1.f;                       // coincident particles: no direction (live is false)
     const float ir = rsqrtf(r2);
     const float r = r2 * ir;
     const float2 exy = mul2(f2(dx, dy), f2(ir, ir));
@@ -507,21 +520,23 @@ struct FwdAcc {
     if (DIM >= 3) gR = fma_(__fadd_rn(__fsub_rn(Bj.z, Bi.z), Cj.w - Ci.w), ez, gR);
     const float Pl = Ci.x, Pr = Cj.x;
     float Ps, du;                                     // P*; v* - v_i^R
-    if (zs > 0.f) {
-      const float izs = rcp_(zs);
+    {
+      // the impedance-weighted state, and the plain averages when Z_i + Z_j = 0
+      // (selected, both evaluated: no branch)
+      const bool zp0 = zs > 0.f;
+      const float izs = rcp_(zp0 ? zs : 1.f);
       const float2 zp = mul2(f2(Zj, Zi), f2(Pl, Pr));
       const float numP = add_(add_(zp.x, zp.y), mul_(mul_(Zi, Zj), -gR));
       const float numu = add_(mul_(Zj, gR), sub_(Pl, Pr));
       const float2 pu = mul2(f2(numP, numu), f2(izs, izs));
-      Ps = pu.x;
-      du = pu.y;
-    } else {
-      Ps = mul_(0.5f, add_(Pl, Pr));
-      du = mul_(0.5f, gR);
+      const float2 avg = mul2(f2(0.5f, 0.5f), f2(add_(Pl, Pr), gR));
+      Ps = zp0 ? pu.x : avg.x;
+      du = zp0 ? pu.y : avg.y;
     }
     const float hij = a.eta_half_f * add_(Ai.w, Aj.w);
-    const float dW = a.kernel == SPH_KERNEL_CUBIC ? dw_cubic_x2<DIM>(r, hij, a.wscale_f)
-                                                  : dw_fast<float, DIM>(a.kernel, a.kappa_f, r, hij, a.wscale_f);
+    float dW = a.kernel == SPH_KERNEL_CUBIC ? dw_cubic_x2<DIM>(r, hij, a.wscale_f)
+                                            : dw_fast<float, DIM>(a.kernel, a.kappa_f, r, hij, a.wscale_f);
+    dW = live ? dW : 0.f;
     // momentum flux along e, without its factor 2 (carried by fscale; exact)
     const float F = mul_(mul_(mul_(Bi.w, Bj.w), Ps), dW);
     s_rho.add(Bj.w * (-du) * (-dW));
