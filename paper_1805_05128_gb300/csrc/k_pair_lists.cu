@@ -193,9 +193,13 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
         const int k = base + hl;
         const bool kv = k < cnt;
         const uint32_t e = kv ? e_cur : 0u;
-        if (base + kSlotLanes < cnt) e_cur = (k + kSlotLanes < cnt) ? row[k + kSlotLanes] : 0u;   // next chunk, requested now
-        bool acc = false;
-        if (kv) {
+        // next chunk's entry, requested now (always inside the row: vcap >= 32;
+        // past the slot's count it is read but not used)
+        e_cur = row[k + kSlotLanes < a.vcap ? k + kSlotLanes : k];
+        bool acc;
+        {
+          // lanes past their slot's last entry (e = 0) evaluate a stand-in and
+          // accept nothing: no branch around the pair
           T sx = T(0), sy = T(0), sz = T(0);
           if constexpr (MIXED) {
             const float4 U = unit_shift[e & 31u];
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
             sy = sxy.y;
             sz = U.z * dcs;
           }
-          acc = fw.pair_listed(a, ii, Ai, Bi, Ci, ui, (int64_t)(e >> 5), sx, sy, sz, khdi, band, te);
+          acc = fw.pair_listed(a, ii, Ai, Bi, Ci, ui, (int64_t)(e >> 5), sx, sy, sz, khdi, band, te, kv);
         }
         nacc += acc ? 1u : 0u;                        // this lane's accepted entries
       }

@@ -448,21 +448,23 @@ struct FwdAcc {
   // the oracle's test.  Returns whether the pair interacts.
   __device__ __forceinline__ bool pair_listed(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi,
                                               const VC& Ci, int ui, int64_t j, T sx, T sy, T sz, T khdi,
-                                              float band, unsigned& nexact) {
+                                              float band, unsigned& nexact, bool valid = true) {
     const V4* __restrict__ A = reinterpret_cast<const V4*>(a.A);
     const V4* __restrict__ B = reinterpret_cast<const V4*>(a.B);
     const VC* __restrict__ C = reinterpret_cast<const VC*>(a.C);
     const V4 Aj = A[j];
     const V4 Bj = B[j];       // requested with A[j]: most candidates interact
     const VC Cj = C[j];
-    return pair_listed_ops(a, i, Ai, Bi, Ci, ui, j, Aj, Bj, Cj, sx, sy, sz, khdi, band, nexact);
+    return pair_listed_ops(a, i, Ai, Bi, Ci, ui, j, Aj, Bj, Cj, sx, sy, sz, khdi, band, nexact, valid);
   }
 
   // pair_listed with j's operands already at hand (staged by the caller).
+  // valid = false: a lane without an entry in this chunk (its operands are a
+  // stand-in); it runs the same instructions and accepts nothing.
   __device__ __forceinline__ bool pair_listed_ops(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi,
                                                   const VC& Ci, int ui, int64_t j, const V4& Aj, const V4& Bj,
                                                   const VC& Cj, T sx, T sy, T sz, T khdi, float band,
-                                                  unsigned& nexact) {
+                                                  unsigned& nexact, bool valid = true) {
     T dx, dy, dz;
     separation(Ai, Aj, sx, sy, sz, dx, dy, dz);
     const T r2 = P::r2_of(dx, dy, dz);
@@ -470,8 +472,8 @@ struct FwdAcc {
     if (MIXED) {
       const T R = fmaf((T)a.kh_f, Aj.w, khdi);
       const T diff = fmaf(-R, R, r2);
-      acc = diff < T(0);
-      if (fabsf(diff) <= band) {
+      acc = valid && diff < T(0);
+      if (valid && fabsf(diff) <= band) {
         ++nexact;
         acc = exact_accept(a, DIM, a.perm[i], a.perm[j]);
       }
@@ -479,7 +481,7 @@ struct FwdAcc {
       T ex, ey, ez;
       P::sep(true, Ai, Aj, T(0), T(0), T(0), ex, ey, ez);   // x_j - x_i, oracle order
       const double R = __dmul_rn(a.kh, __dadd_rn(Ai.w, Aj.w));
-      acc = P::r2_of(ex, ey, ez) < __dmul_rn(R, R);
+      acc = valid && P::r2_of(ex, ey, ez) < __dmul_rn(R, R);
     }
     if constexpr (kX2 && !EXTRA) {
       // Branch-free: every listed entry runs the flux arithmetic, and the
