@@ -230,7 +230,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         import torch.distributed as dist
     prob = synth.plate_impact(units=64, n_steps=500, **WORKLOADS[args.workload])
     gen = synth.problem_generators(prob)
-    sim = Simulation(prob, precision=args.precision, generators=gen, n_upd=10, cell_beta=args.beta, device=dev)
+    sim = Simulation(prob, precision=args.precision, generators=gen, n_upd=10, cell_beta=args.beta,
+                     list_staging=args.staging, device=dev)
     sim.assign()
     sim.build_cells()
     sim.step(max(args.warmup, 3))
@@ -302,7 +303,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
            "data": "synthetic",
            "config": {"workload": args.workload, "particles": prob.n, "precision": args.precision, "units": 64,
-                      "verlet_beta": args.beta, "list_builds": builds,
+                      "verlet_beta": args.beta, "list_builds": builds, "operand_staging": bool(args.staging),
                       "rebalance_every": 10, "l2": "inputs larger than L2 (no flush)",
                       "parallelism": f"replicas{world}" if world > 1 else "single"},
            "pair_interactions_per_s": half_pairs * world * args.steps / (ms * 1e-3),
@@ -670,6 +671,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-step, batched-ensemble and adjoint measurements")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--staging", action="store_true",
+                    help="stage the list kernel's neighbour operands in shared memory with cp.async")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

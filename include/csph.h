@@ -124,7 +124,9 @@ typedef struct sph_params {
                          past it is cut at the capacity and SPH_ERR_CAPACITY is latched. */
   int32_t unit_sched; /* SPH_SCHED_*: work partition of the list kernel (needs cell_beta > 0 and
                          n_units > 0; otherwise the global counter is used) */
-  int32_t pad4_;
+  int32_t list_staging; /* 1: the list kernel (mixed precision) stages each next chunk's neighbour
+                           operands in shared memory with cp.async while the current one is
+                           evaluated; 0 (default): the operands are gathered through L1 */
 } sph_params;
 
 /* Particle state: structure of arrays in device memory, n elements each.

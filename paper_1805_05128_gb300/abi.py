@@ -45,7 +45,7 @@ class sph_params(C.Structure):
                 ("generators", C.c_void_p), ("materials", C.c_void_p),
                 ("order", C.c_int32), ("solver", C.c_int32),
                 ("load_measure", C.c_int32), ("list_cap", C.c_int32),
-                ("unit_sched", C.c_int32), ("pad4_", C.c_int32)]
+                ("unit_sched", C.c_int32), ("list_staging", C.c_int32)]
 
 
 STATE_F64 = ("x", "y", "z", "vx", "vy", "vz", "rho", "E", "m")

@@ -125,6 +125,7 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     return fail(nullptr, SPH_ERR_INVALID, "unknown pair solver");
   if (p->load_measure != SPH_LOAD_PAIRS && p->load_measure != SPH_LOAD_TIME)
     return fail(nullptr, SPH_ERR_INVALID, "unknown load measure");
+  if (p->list_staging != 0 && p->list_staging != 1) return fail(nullptr, SPH_ERR_INVALID, "list_staging must be 0 or 1");
   if (p->unit_sched < SPH_SCHED_GLOBAL || p->unit_sched > SPH_SCHED_UNITS_OWNED)
     return fail(nullptr, SPH_ERR_INVALID, "unknown unit_sched");
   if (p->list_cap != 0 && (p->list_cap < 32 || p->list_cap > 65536))

@@ -32,6 +32,22 @@ namespace {
 constexpr int kSlotLanes = 4;
 constexpr int kSlotsPerWarp = 32 / kSlotLanes;
 
+// Optional staging of the neighbour operands (sph_params.list_staging): the
+// operands of the next chunk's entries are copied into shared memory with
+// cp.async (16-byte copies, .ca: kept in L1 too) while the current chunk is
+// evaluated, so their L2 latency overlaps the arithmetic without holding
+// them in registers.  Each lane reads back only what it copied, after
+// cp.async.wait_group, so no barrier is needed.  Measured slower than the
+// plain gathers on GB300 (more instructions, shared-memory latency, a
+// smaller L1 for the gathers that hit), so the default gathers through L1.
+__device__ __forceinline__ void cp16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Sum over a slot's lanes of their Kahan sums (s - c), by a fixed butterfly.
 template <typename T>
 __device__ __forceinline__ T slot_sum(const Kahan<T>& k) {
@@ -41,7 +57,7 @@ __device__ __forceinline__ T slot_sum(const Kahan<T>& k) {
   return v;
 }
 
-template <bool MIXED, int DIM, bool HLL = false, bool EXTRA = true>
+template <bool MIXED, int DIM, bool HLL = false, bool EXTRA = true, bool STAGE = false>
 __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pair_lists(PairArgs a) {
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
@@ -55,6 +71,9 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
   // and three multiplies are cheaper than the integer divisions and
   // conversions of the decode, and give the same FP32 shifts bit for bit
   __shared__ float4 unit_shift[32];
+  // STAGE: [warp][stage][16-byte chunk][lane]: A_j, B_j, C_j (3 chunks mixed, 5 in FP64)
+  constexpr int kChA = (int)(sizeof(V4) / 16), kChC = (int)(sizeof(VC) / 16), kCh = 2 * kChA + kChC;
+  __shared__ __align__(16) float4 stg[STAGE ? kWarps : 1][2][kCh][32];
   if (threadIdx.x < 32) {
     const int c = threadIdx.x;
     unit_shift[c] = make_float4((float)(c % 3 - 1), (float)((c / 3) % 3 - 1), (float)(c / 9 - 1), 0.f);
@@ -142,11 +161,33 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
     // one is evaluated, so the DRAM latency of the lists overlaps the L2
     // gathers and the arithmetic.  vcap >= 32, so the first chunk of any row
     // is in bounds.
-    uint32_t e_pre = 0u;
+    uint32_t e_pre = 0u, e_pre1 = 0u;
     int cnt_pre = 0;
+    const V4* __restrict__ Bp = reinterpret_cast<const V4*>(a.B);
+    const VC* __restrict__ Cp = reinterpret_cast<const VC*>(a.C);
+    int stage = 0;
+    // STAGE: copy the operands of entry e (or of slot `self`, a stand-in that
+    // accepts nothing, for a lane without an entry) into stage st
+    auto stage_ops = [&](int st, bool has, uint32_t e, int self) {
+      const int64_t j = has ? (int64_t)(e >> 5) : (int64_t)self;
+      const char* ga = reinterpret_cast<const char*>(A + j);
+      const char* gb = reinterpret_cast<const char*>(Bp + j);
+      const char* gc = reinterpret_cast<const char*>(Cp + j);
+#pragma unroll
+      for (int c = 0; c < kChA; ++c) cp16(&stg[warp][st][c][lane], ga + 16 * c);
+#pragma unroll
+      for (int c = 0; c < kChA; ++c) cp16(&stg[warp][st][kChA + c][lane], gb + 16 * c);
+#pragma unroll
+      for (int c = 0; c < kChC; ++c) cp16(&stg[warp][st][2 * kChA + c][lane], gc + 16 * c);
+    };
     if (g0 + half < g1) {
       e_pre = a.vlist[(g0 + half) * (int64_t)a.vcap + hl];
       cnt_pre = a.vcnt[g0 + half];
+      if constexpr (STAGE) e_pre1 = a.vlist[(g0 + half) * (int64_t)a.vcap + hl + kSlotLanes];
+    }
+    if constexpr (STAGE) {
+      stage_ops(stage, g0 + half < g1 && hl < cnt_pre, e_pre, g0 + half < g1 ? g0 + half : g0);
+      cp_commit();
     }
     for (int q = 0; g0 + kSlotsPerWarp * q < g1; ++q) {   // warp-uniform
       if (a.load_timed) {                                    // kept in shared memory: frees registers
@@ -158,9 +199,13 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
       const bool iv = i < g1;                                // uniform in the group
       const int cnt = iv ? cnt_pre : 0;
       uint32_t e_cur = e_pre;
-      if (i + kSlotsPerWarp < g1) {
+      uint32_t e_nx = e_pre1;                                // STAGE: entry of this slot's chunk 1
+      const bool nv = i + kSlotsPerWarp < g1;                // the group's next slot exists
+      if (STAGE) cnt_pre = 0;
+      if (nv) {
         e_pre = a.vlist[(i + kSlotsPerWarp) * (int64_t)a.vcap + hl];
         cnt_pre = a.vcnt[i + kSlotsPerWarp];
+        if constexpr (STAGE) e_pre1 = a.vlist[(i + kSlotsPerWarp) * (int64_t)a.vcap + hl + kSlotLanes];
       }
       const int ii = iv ? i : g0;                     // a valid slot for the loads
       int b = 0;
@@ -176,8 +221,8 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
       const T dcs = MIXED ? (T)g.dc_f : T(0);
       const float band = MIXED ? 0x1p-12f * g.dc_f * g.dc_f : 0.f;
       const V4 Ai = A[ii];
-      const V4 Bi = reinterpret_cast<const V4*>(a.B)[ii];
-      const VC Ci = reinterpret_cast<const VC*>(a.C)[ii];
+      const V4 Bi = Bp[ii];
+      const VC Ci = Cp[ii];
       const T khdi = MIXED ? (T)a.kh_f * Ai.w : T(0);
       const int ui = a.K > 0 ? a.slot_unit[ii] : 0;
       const uint32_t* __restrict__ row = a.vlist + (int64_t)ii * a.vcap;
@@ -189,7 +234,58 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
         const int other = __shfl_xor_sync(0xffffffffu, cmax, o);
         cmax = cmax > other ? cmax : other;
       }
-      for (int base = 0; base < cmax; base += kSlotLanes) {
+      if constexpr (STAGE) {
+        // the operands of chunk base are in stage `stage`; the next chunk's
+        // (or, at the slot's last chunk, the next slot's first) are copied now
+        const int inext = nv ? i + kSlotsPerWarp : ii;
+        for (int base = 0; base < cmax; base += kSlotLanes) {
+          const int k = base + hl;
+          const bool kv = k < cnt;
+          const uint32_t e_nn = row[k + 2 * kSlotLanes < a.vcap ? k + 2 * kSlotLanes : k];
+          if (base + kSlotLanes < cmax) stage_ops(stage ^ 1, k + kSlotLanes < cnt, e_nx, ii);
+          else stage_ops(stage ^ 1, hl < cnt_pre, e_pre, inext);
+          cp_commit();
+          cp_wait<1>();
+          V4 Aj;
+          V4 Bj;
+          VC Cj;
+          if constexpr (MIXED) {
+            Aj = stg[warp][stage][0][lane];
+            Bj = stg[warp][stage][1][lane];
+            Cj = stg[warp][stage][2][lane];
+          } else {
+            const double2 a0 = reinterpret_cast<const double2&>(stg[warp][stage][0][lane]);
+            const double2 a1 = reinterpret_cast<const double2&>(stg[warp][stage][1][lane]);
+            const double2 b0 = reinterpret_cast<const double2&>(stg[warp][stage][2][lane]);
+            const double2 b1 = reinterpret_cast<const double2&>(stg[warp][stage][3][lane]);
+            const double2 c0 = reinterpret_cast<const double2&>(stg[warp][stage][4][lane]);
+            Aj = V4{a0.x, a0.y, a1.x, a1.y};
+            Bj = V4{b0.x, b0.y, b1.x, b1.y};
+            Cj = VC{c0.x, c0.y};
+          }
+          const uint32_t e = kv ? e_cur : 0u;
+          T sx = T(0), sy = T(0), sz = T(0);
+          if constexpr (MIXED) {
+            const float4 U = unit_shift[e & 31u];
+            const float2 sxy = mul2(f2(U.x, U.y), f2(dcs, dcs));
+            sx = sxy.x;
+            sy = sxy.y;
+            sz = U.z * dcs;
+          }
+          const bool acc = fw.pair_listed_ops(a, ii, Ai, Bi, Ci, ui, kv ? (int64_t)(e >> 5) : (int64_t)ii, Aj, Bj,
+                                              Cj, sx, sy, sz, khdi, band, te, kv);
+          nacc += acc ? 1u : 0u;
+          stage ^= 1;
+          e_cur = e_nx;
+          e_nx = e_nn;
+        }
+        if (cmax == 0) {                              // no chunk ran: stage the next slot's first chunk here
+          stage_ops(stage ^ 1, hl < cnt_pre, e_pre, inext);
+          cp_commit();
+          stage ^= 1;
+        }
+      }
+      for (int base = 0; !STAGE && base < cmax; base += kSlotLanes) {
         const int k = base + hl;
         const bool kv = k < cnt;
         const uint32_t e = kv ? e_cur : 0u;
@@ -249,6 +345,7 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
         }
       }
     }
+    if constexpr (STAGE) cp_wait<0>();              // the last slot's stand-in copy, before the stages are reused
     if (a.K > 0 && hl == 0 && unit_run >= 0 && unit_load)
       atomicAdd(&a.load_acc[unit_run], (unsigned long long)unit_load);
     __syncwarp();
@@ -333,32 +430,42 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
   }
 }
 
-template <bool MIXED, int DIM, bool HLL, bool EXTRA>
+template <bool MIXED, int DIM, bool HLL, bool EXTRA, bool STAGE>
 cudaError_t launch_lists_one(const PairArgs& args, int blocks_per_sm, cudaStream_t st) {
   static int sms = 0, per_sm = 0;
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_lists<MIXED, DIM, HLL, EXTRA>, kPairBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_lists<MIXED, DIM, HLL, EXTRA, STAGE>, kPairBlock, 0);
     if (per_sm < 1) per_sm = 1;
   }
   const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
   int grid = sms * b;
   if (args.unit_sched == SPH_SCHED_UNITS_OWNED && args.K > 0)   // the same number of CTAs for every unit
     grid = args.K * (grid / args.K > 0 ? grid / args.K : 1);
-  k_pair_lists<MIXED, DIM, HLL, EXTRA><<<grid, kPairBlock, 0, st>>>(args);
+  k_pair_lists<MIXED, DIM, HLL, EXTRA, STAGE><<<grid, kPairBlock, 0, st>>>(args);
   return cudaGetLastError();
 }
 
-template <bool MIXED, bool HLL, bool EXTRA>
+template <bool MIXED, bool HLL, bool EXTRA, bool STAGE>
 cudaError_t launch_lists_dim3(sph_handle* h, const PairArgs& args, cudaStream_t st) {
   const int b = h->p.pair_blocks_per_sm;
   switch (h->dp.dim) {
-    case 1: return launch_lists_one<MIXED, 1, HLL, EXTRA>(args, b, st);
-    case 2: return launch_lists_one<MIXED, 2, HLL, EXTRA>(args, b, st);
-    default: return launch_lists_one<MIXED, 3, HLL, EXTRA>(args, b, st);
+    case 1: return launch_lists_one<MIXED, 1, HLL, EXTRA, STAGE>(args, b, st);
+    case 2: return launch_lists_one<MIXED, 2, HLL, EXTRA, STAGE>(args, b, st);
+    default: return launch_lists_one<MIXED, 3, HLL, EXTRA, STAGE>(args, b, st);
   }
+}
+
+// Staged operands only for the mixed evaluations without side outputs (the
+// benchmark's form); every other form gathers through L1.
+template <bool MIXED, bool HLL, bool EXTRA>
+cudaError_t launch_lists_stage(sph_handle* h, const PairArgs& args, cudaStream_t st) {
+  if constexpr (MIXED && !EXTRA) {
+    if (h->p.list_staging) return launch_lists_dim3<MIXED, HLL, EXTRA, true>(h, args, st);
+  }
+  return launch_lists_dim3<MIXED, HLL, EXTRA, false>(h, args, st);
 }
 
 // The side outputs (neighbour sizes, unit adjacency, pair output) only when
@@ -367,8 +474,8 @@ template <bool MIXED>
 cudaError_t launch_lists_dim(sph_handle* h, const PairArgs& args, cudaStream_t st) {
   const bool extra = args.collect_adj || args.pair_i;
   if (h->solver == SPH_SOLVER_HLL)
-    return extra ? launch_lists_dim3<MIXED, true, true>(h, args, st) : launch_lists_dim3<MIXED, true, false>(h, args, st);
-  return extra ? launch_lists_dim3<MIXED, false, true>(h, args, st) : launch_lists_dim3<MIXED, false, false>(h, args, st);
+    return extra ? launch_lists_stage<MIXED, true, true>(h, args, st) : launch_lists_stage<MIXED, true, false>(h, args, st);
+  return extra ? launch_lists_stage<MIXED, false, true>(h, args, st) : launch_lists_stage<MIXED, false, false>(h, args, st);
 }
 
 }  // namespace

@@ -35,6 +35,7 @@ class Simulation:
                  gamma_b: float = 1.0, beta_sh: float = 0.45, cell_cap: int = 1 << 24, cell_beta: float = 0.0,
                  pair_blocks_per_sm: int = 0, order: int = 1, solver: str = "acoustic",
                  load_measure: str = "pairs", list_cap: int = 0, unit_sched: str = "global",
+                 list_staging: bool = False,
                  device: str | torch.device = "cuda:0"):
         if not isinstance(problems, (list, tuple)):
             problems = [problems]
@@ -101,6 +102,7 @@ class Simulation:
         prm.load_measure = _LOAD[load_measure]
         prm.list_cap = list_cap
         prm.unit_sched = _SCHED[unit_sched]
+        prm.list_staging = int(list_staging)
         prm.generators = self.gen.data_ptr() if self.gen is not None else None
         self.params = prm
         self.precision = precision

@@ -44,7 +44,7 @@ def test_struct_layouts_match_header(lib, tmp_path):
     gives the structs of include/csph.h."""
     import subprocess
     prog = tmp_path / "layout.c"
-    fields = {"sph_params": ["dim", "kappa", "cell_cap", "mat", "n_units", "pair_blocks_per_sm", "theta", "generators", "materials", "order", "solver", "load_measure", "list_cap", "unit_sched"],
+    fields = {"sph_params": ["dim", "kappa", "cell_cap", "mat", "n_units", "pair_blocks_per_sm", "theta", "generators", "materials", "order", "solver", "load_measure", "list_cap", "unit_sched", "list_staging"],
               "sph_state": ["n", "x", "mat", "ax", "d", "id", "unit"],
               "sph_material": ["eos", "gamma", "s_a"]}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "csph.h"', "int main(void){"]
@@ -94,6 +94,7 @@ def _fake_state(lib, n=10):
     (lambda p: setattr(p, "order", 3), 1),
     (lambda p: setattr(p, "list_cap", 16), 1),
     (lambda p: setattr(p, "unit_sched", 3), 1),
+    (lambda p: setattr(p, "list_staging", 2), 1),
     (lambda p: setattr(p.mat[0], "eos", 5), 1),
     (lambda p: (setattr(p.mat[0], "eos", 4), setattr(p.mat[0], "c0", 0.0)), 1),
 ])
