@@ -59,26 +59,16 @@ __device__ __forceinline__ double size_of(int dim, double m, double rho) {
   return dim == 1 ? vol : (dim == 2 ? sqrt(vol) : cbrt_fast(vol));
 }
 
-// d = (m / rho)^(1/D) for a mixed-precision step, with a third of the FP64
-// work of size_of: FP32 seeds for 1/rho and the root, each refined by one
-// FP64 Newton step (the error squares: ~1e-7 -> ~1e-14 relative).  The step's
-// pair decisions take this d as given and its FP32 fluxes are far coarser.
+// d = (m / rho)^(1/D) for a mixed-precision step, in FP32 (relative error
+// ~2e-7) from the FP64 mass and density: the step's pair decisions take this
+// d as given (the FP32 packs and the FP64 exact test read the same stored
+// value) and its FP32 fluxes are far coarser, while FP64 divisions, roots and
+// conversions are what bound the per-particle kernels on GB300.  Volumes
+// outside FP32's normal range take the FP64 path.
 __device__ __forceinline__ double size_of_mixed(int dim, double m, double rho) {
-  const float rf = (float)rho;
-  double r = (double)__frcp_rn(rf);
-  r = r * __fma_rn(-rho, r, 2.0);
-  const double vol = m * r;
-  if (dim == 1) return vol;
-  const float vf = (float)vol;
-  if (dim == 2) {
-    const float y0 = sqrtf(vf);
-    const double y = (double)y0;
-    return __fma_rn(__fma_rn(-y, y, vol), (double)(0.5f / y0), y);
-  }
-  if (!(vf > 1e-30f && vf < 1e30f)) return cbrt(vol);   // outside the FP32 seed's comfortable range
-  const float y0 = cbrtf(vf);
-  const double y = (double)y0;
-  return __fma_rn(-__fma_rn(y * y, y, -vol), (double)__frcp_rn(3.0f * y0 * y0), y);
+  const float vf = __fdiv_rn((float)m, (float)rho);
+  if (!(vf > 1e-36f && vf < 1e36f)) return size_of(dim, m, rho);
+  return (double)(dim == 1 ? vf : (dim == 2 ? sqrtf(vf) : cbrtf(vf)));
 }
 
 // Half kick / drift y + a x: the oracle's correctly rounded product and sum
