@@ -214,6 +214,20 @@ int sph_step_dt(sph_handle* h, sph_state* s, int n_steps, const double* dt_dev, 
 int voronoi_assign(sph_handle* h, const sph_state* s, const double* gen, int K, int dim,
                    int32_t* unit_out, int32_t* unit_offsets, void* stream);
 
+/* voronoi_balance from unit statistics given by the caller (host arrays), for
+ * a decomposition spread over several processes whose statistics are reduced
+ * across them first: load (K), adj (K x K bytes, 0/1, symmetric), rmax (K:
+ * max over the unit's particles of R^hrz_i, so that D^sh_kl = max(rmax_k,
+ * rmax_l), eq. Horizon), centroid (K x dim: the mean position of the unit's
+ * particles), count (K).  The same update as voronoi_balance (eqs.
+ * BalancingOffset ... TotalOffset) on gen (device, K x dim, updated in place);
+ * shift_sum_out (device double, may be NULL) receives sum_k |g^_k - g_k|.
+ * Requires K = the handle's n_units and dim = its unit_dim; the handle's
+ * accumulators are reset. */
+int voronoi_balance_stats(sph_handle* h, double* gen, int K, int dim, const double* load, const uint8_t* adj,
+                          const double* rmax, const double* centroid, const int64_t* count,
+                          const sph_balance_params* bp, double* shift_sum_out, void* stream);
+
 /* One balancing update of the generators (Secs. 3.2-3.4): loads L_k (device
  * `load`, K doubles, or NULL for the accumulated pair counts, a pair that
  * crosses units counting 1/2 to each), adjacency from the accumulated
@@ -256,6 +270,21 @@ int voronoi_balance(sph_handle* h, const sph_state* s, double* gen, int K, int d
  * paper's step. */
 int sph_step_adjoint(sph_handle* h, const sph_ckpt* ck, int n_steps, const sph_state* adj_out,
                      sph_state* adj_in, double* adj_params, void* stream);
+
+/* Declare that the rate arrays of the state (ax, ay, az, drho, dE) are the
+ * held rates of the scheme for the next step (the rates of the previous
+ * step's evaluation at its predicted state, e.g. received from the process
+ * that evaluated them), so that sph_step and sph_step_dt use them instead of
+ * evaluating rates at the current state first.  A decomposed run moves
+ * particles between handles with their held rates. */
+int sph_hold_rates(sph_handle* h);
+
+/* The CFL time step of the current state without stepping (Alg. 1: each
+ * process's bound before the global synchronisation of the SPH time step):
+ * dt_out (device, n_instances doubles) receives cfl min_i eta d_i / (c_i + |v_i|)
+ * per instance, the dt sph_step would take.  A rank of a decomposed run
+ * reduces it with the other ranks' (minimum) and steps with sph_step_dt. */
+int sph_cfl_dt(sph_handle* h, const sph_state* s, double* dt_out, void* stream);
 
 /* Copy the dt of the last step (device, n_instances doubles) to dt_out (device),
  * asynchronously; used to record the schedule for sph_step_adjoint. */

@@ -28,7 +28,8 @@ ERROR_NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID", 2: "SPH_ERR_CAPACITY", 3: "SPH
 EXPORTS = ("sph_init", "sph_build_cells", "sph_eval_rates", "sph_step", "voronoi_assign", "voronoi_balance",
            "sph_conservation", "sph_unit_stats", "sph_read_status", "sph_last_error", "sph_pair_counts",
            "sph_cell_index", "sph_pair_list", "voronoi_assign_static", "sph_profile", "sph_profile_read",
-           "sph_step_adjoint", "sph_last_dt", "sph_step_dt", "sph_list_builds", "sph_unit_times", "sph_destroy")
+           "sph_step_adjoint", "sph_last_dt", "sph_step_dt", "sph_list_builds", "sph_unit_times", "sph_cfl_dt", "sph_hold_rates",
+           "voronoi_balance_stats", "sph_destroy")
 
 
 class sph_material(C.Structure):
@@ -102,6 +103,11 @@ def lib() -> C.CDLL:
     L.sph_step_dt.argtypes = [vp, C.POINTER(sph_state), i32, vp, vp, vp]
     L.sph_list_builds.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32), vp]
     L.sph_unit_times.argtypes = [vp, C.POINTER(C.c_double), vp]
+    L.sph_cfl_dt.argtypes = [vp, C.POINTER(sph_state), vp, vp]
+    L.sph_hold_rates.argtypes = [vp]
+    dp = C.POINTER(C.c_double)
+    L.voronoi_balance_stats.argtypes = [vp, vp, i32, i32, dp, C.POINTER(C.c_uint8), dp, dp, C.POINTER(C.c_int64),
+                                        C.POINTER(sph_balance_params), vp, vp]
     L.sph_profile.argtypes = [vp, i32]
     L.sph_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.sph_destroy.argtypes = [vp]
@@ -190,6 +196,24 @@ def sph_list_builds(h, stream):
 def sph_unit_times(h, out, stream):
     """out: host float64 array of 2 K (start, end per unit, ns)."""
     check(lib().sph_unit_times(h, out.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(stream)), h)
+
+
+def sph_hold_rates(h):
+    check(lib().sph_hold_rates(h), h)
+
+
+def sph_cfl_dt(h, state, dt_out_ptr, stream):
+    check(lib().sph_cfl_dt(h, C.byref(state), C.c_void_p(dt_out_ptr), C.c_void_p(stream)), h)
+
+
+def voronoi_balance_stats(h, gen_ptr, K, dim, load, adj, rmax, centroid, count, bp: sph_balance_params,
+                          shift_ptr, stream):
+    """load, rmax (K), centroid (K x dim) float64, adj (K x K) uint8, count (K) int64: host numpy arrays."""
+    dp = C.POINTER(C.c_double)
+    check(lib().voronoi_balance_stats(h, C.c_void_p(gen_ptr), K, dim, load.ctypes.data_as(dp),
+                                      adj.ctypes.data_as(C.POINTER(C.c_uint8)), rmax.ctypes.data_as(dp),
+                                      centroid.ctypes.data_as(dp), count.ctypes.data_as(C.POINTER(C.c_int64)),
+                                      C.byref(bp), C.c_void_p(shift_ptr), C.c_void_p(stream)), h)
 
 
 def sph_cell_index(h, state, cell_out_ptr, grid_out, stream):

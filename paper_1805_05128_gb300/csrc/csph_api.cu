@@ -511,6 +511,56 @@ int voronoi_balance(sph_handle* h, const sph_state* s, double* gen, int K, int d
   return balance_impl(h, const_cast<sph_state*>(s), gen, K, dim, load, *bp, shift_sum_out, st);
 }
 
+int voronoi_balance_stats(sph_handle* h, double* gen, int K, int dim, const double* load, const uint8_t* adj,
+                          const double* rmax, const double* centroid, const int64_t* count,
+                          const sph_balance_params* bp, double* shift_sum_out, void* stream) {
+  if (!h) return SPH_ERR_INVALID;
+  if (h->K == 0 || K != h->K) return fail(h, SPH_ERR_INVALID, "K must equal the handle's n_units (> 0)");
+  if (dim != h->gdim) return fail(h, SPH_ERR_INVALID, "dim must equal the handle's unit_dim");
+  if (!gen || !load || !adj || !rmax || !centroid || !count || !bp)
+    return fail(h, SPH_ERR_INVALID, "gen, load, adj, rmax, centroid, count and bp are required");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  // statistics in the layout of the handle's own: [K x 5] centroid (3), count, rmax; then the loads
+  std::vector<double> stats((size_t)6 * K, 0.0);
+  for (int k = 0; k < K; ++k) {
+    for (int a = 0; a < dim; ++a) stats[(size_t)k * 5 + a] = centroid[(size_t)k * dim + a];
+    stats[(size_t)k * 5 + 3] = (double)count[k];
+    stats[(size_t)k * 5 + 4] = rmax[k];
+    stats[(size_t)5 * K + k] = load[k];
+  }
+  const int words = (K + 31) / 32;
+  std::vector<uint32_t> bits((size_t)K * words, 0u);
+  for (int k = 0; k < K; ++k)
+    for (int l = 0; l < K; ++l)
+      if (adj[(size_t)k * K + l]) bits[(size_t)k * words + (l >> 5)] |= 1u << (l & 31);
+  // the statistics' partial-sum area of unit_stats (free outside voronoi_balance) holds the copies
+  double* dst = h->unit_stats + (size_t)9 * K;
+  CK(h, cudaMemcpyAsync(dst, stats.data(), sizeof(double) * stats.size(), cudaMemcpyHostToDevice, st));
+  CK(h, cudaMemcpyAsync(h->adj_bits, bits.data(), sizeof(uint32_t) * bits.size(), cudaMemcpyHostToDevice, st));
+  CK(h, launch_balance_given(h, gen, K, dim, dst, dst + (size_t)5 * K, *bp, shift_sum_out, st));
+  CK(h, cudaStreamSynchronize(st));     // the host copies above are stack-owned
+  return SPH_OK;
+}
+
+int sph_hold_rates(sph_handle* h) {
+  if (!h) return SPH_ERR_INVALID;
+  h->rates_valid = true;
+  return SPH_OK;
+}
+
+int sph_cfl_dt(sph_handle* h, const sph_state* s, double* dt_out, void* stream) {
+  int rc = check_handle_state(h, s);
+  if (rc) return rc;
+  if (!dt_out) return fail(h, SPH_ERR_INVALID, "dt_out is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  CK(h, launch_derive_dt(h, *s, false, st));
+  CK(h, launch_reduce_dt(h, st, false));
+  CK(h, cudaMemcpyAsync(dt_out, h->dt, sizeof(double) * h->n_inst, cudaMemcpyDeviceToDevice, st));
+  return SPH_OK;
+}
+
 int sph_conservation(sph_handle* h, const sph_state* s, double* out, void* stream) {
   int rc = check_handle_state(h, s);
   if (rc) return rc;

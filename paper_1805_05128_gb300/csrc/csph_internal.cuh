@@ -358,6 +358,11 @@ cudaError_t launch_unit_lists(sph_handle* h, const int32_t* unit, int32_t* unit_
 cudaError_t launch_balance(sph_handle* h, const sph_state& s, double* gen, int K, int dim,
                            const double* load, const sph_balance_params& bp, double* shift_out,
                            cudaStream_t st);
+// The balancing update from statistics already on the device: stats [K x 5] (centroid, count,
+// rmax), load [K] (device), the adjacency already in h->adj_bits.
+cudaError_t launch_balance_given(sph_handle* h, double* gen, int K, int dim, const double* stats,
+                                 const double* load, const sph_balance_params& bp, double* shift_out,
+                                 cudaStream_t st);
 // Evaluation order of the unit-partitioned list kernel (gated on vflag[0], at list builds only,
 // unless forced): e_of_c, perm_e, unit_eoff from the cell-order slots and the units of their particles.
 cudaError_t launch_eorder(sph_handle* h, const sph_state& s, cudaStream_t st, bool force = false);

@@ -561,6 +561,18 @@ cudaError_t launch_eorder(sph_handle* h, const sph_state& s, cudaStream_t st, bo
   return cudaGetLastError();
 }
 
+cudaError_t launch_balance_given(sph_handle* h, double* gen, int K, int dim, const double* stats,
+                                 const double* load, const sph_balance_params& bp, double* shift_out,
+                                 cudaStream_t st) {
+  double* scratch = h->unit_stats + (size_t)5 * K;
+  k_balance_unit<<<K, 32, 0, st>>>(K, dim, gen, load, h->load_acc, h->adj_bits, (K + 31) / 32, stats, bp.theta,
+                                   bp.sigma, bp.gamma_b, scratch);
+  k_balance_apply<<<1, SPH_MAX_UNITS, 0, st>>>(K, dim, gen, scratch, h->load_acc, h->adj_bits, (K + 31) / 32,
+                                               shift_out);
+  h->launches += 2;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_balance(sph_handle* h, const sph_state& s, double* gen, int K, int dim, const double* load,
                            const sph_balance_params& bp, double* shift_out, cudaStream_t st) {
   cudaError_t e = launch_unit_lists(h, s.unit, nullptr, st);
