@@ -360,7 +360,15 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pai
         };
         const int64_t p = a.perm[i];
         const double drho = 2.0 * a.rho_slot[i] * (rv(0) * a.rscale);
-        const double im = a.fscale / a.m[p];
+        double im;
+        if constexpr (MIXED) {   // 1/m from the FP32 reciprocal and one FP64 Newton step (~1e-14 relative)
+          const double mm = a.m[p];
+          double r = (double)__frcp_rn((float)mm);
+          r = r * __fma_rn(-mm, r, 2.0);
+          im = a.fscale * r;
+        } else {
+          im = a.fscale / a.m[p];
+        }
         const double acc[3] = {rv(1) * im, DIM >= 2 ? rv(2) * im : 0.0, DIM >= 3 ? rv(3) * im : 0.0};
         const double dE = rv(4) * im + lab_power_of<MIXED>(a, i, acc);
         a.drho[p] = drho;

@@ -188,7 +188,10 @@ __device__ __forceinline__ double fma_(double a, double b, double c) { return __
 // instruction issue, so pairing the x and y components, the independent rate
 // terms and the Kahan sums cuts its instruction count while every component
 // keeps the scalar code's bits.  a - b is formed as b * (-1) + a, one
-// rounding, as the scalar subtraction.
+// rounding, as the scalar subtraction.  Pairs are formed where both halves
+// already sit in adjacent registers (the x, y of a loaded float4, a pair of
+// running sums): joining two unrelated scalars costs register moves that
+// measured as much as the operation saved.
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -244,24 +247,6 @@ __device__ __forceinline__ T dw_fast(int kernel, T kappa, T r, T h, T ws) {
     const T norm = (DIM == 2) ? (T(7) / pi * ws) * iH * iH * iH : (T(21) / (T(2) * pi) * ws) * (iH * iH) * (iH * iH);
     return norm * (T(-20) * s * t * t * t);
   }
-}
-
-// dw_fast for the cubic spline in FP32 with the two polynomial pieces
-// evaluated side by side in paired operations.
-template <int DIM>
-__device__ __forceinline__ float dw_cubic_x2(float r, float h, float ws) {
-  const float ih = rcp_(h);
-  const float q = r * ih;
-  float norm;
-  if (DIM == 1) norm = (float(2.0 / 3.0) * ws) * ih * ih;
-  else if (DIM == 2) norm = (float(10.0 / (7.0 * 3.14159265358979323846)) * ws) * ih * ih * ih;
-  else norm = (float(1.0 / 3.14159265358979323846) * ws) * (ih * ih) * (ih * ih);
-  const float t = 2.f - q;
-  // (q (2.25 q - 3), -0.75 t t): inside q < 1 and for 1 <= q < 2
-  const float2 lin = fma2(f2(q, t), f2(2.25f, -0.75f), f2(-3.f, 0.f));
-  const float2 f = mul2(lin, f2(q, t));
-  const float v = q < 1.f ? f.x : (q < 2.f ? f.y : 0.f);
-  return norm * v;
 }
 
 // Cubic spline W'(r, h) = s h^-(D+1) g(q) and its derivatives
@@ -527,23 +512,19 @@ struct FwdAcc {
       // (selected, both evaluated: no branch)
       const bool zp0 = zs > 0.f;
       const float izs = rcp_(zp0 ? zs : 1.f);
-      const float2 zp = mul2(f2(Zj, Zi), f2(Pl, Pr));
-      const float numP = add_(add_(zp.x, zp.y), mul_(mul_(Zi, Zj), -gR));
+      const float numP = add_(add_(mul_(Zj, Pl), mul_(Zi, Pr)), mul_(mul_(Zi, Zj), -gR));
       const float numu = add_(mul_(Zj, gR), sub_(Pl, Pr));
-      const float2 pu = mul2(f2(numP, numu), f2(izs, izs));
-      const float2 avg = mul2(f2(0.5f, 0.5f), f2(add_(Pl, Pr), gR));
-      Ps = zp0 ? pu.x : avg.x;
-      du = zp0 ? pu.y : avg.y;
+      Ps = zp0 ? mul_(numP, izs) : mul_(0.5f, add_(Pl, Pr));
+      du = zp0 ? mul_(numu, izs) : mul_(0.5f, gR);
     }
     const float hij = a.eta_half_f * add_(Ai.w, Aj.w);
-    float dW = a.kernel == SPH_KERNEL_CUBIC ? dw_cubic_x2<DIM>(r, hij, a.wscale_f)
-                                            : dw_fast<float, DIM>(a.kernel, a.kappa_f, r, hij, a.wscale_f);
+    float dW = dw_fast<float, DIM>(a.kernel, a.kappa_f, r, hij, a.wscale_f);
     dW = live ? dW : 0.f;
     // momentum flux along e, without its factor 2 (carried by fscale; exact)
     const float F = mul_(mul_(mul_(Bi.w, Bj.w), Ps), dW);
     s_rho.add(Bj.w * (-du) * (-dW));
     k_fxy.add(mul2(f2(F, F), exy));
-    k_fzq.add(mul2(f2(F, F), f2(ez, du)));
+    k_fzq.add(f2(mul_(F, ez), mul_(F, du)));
   }
 
   __device__ __forceinline__ void flux_at(const PairArgs& a, int64_t i, const V4& Ai, const V4& Bi, const VC& Ci,
