@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
             // broadcast from shared memory, and appends the accepted ones to its
             // own list in candidate order
             const int nc = min(32, r1 - base);
-#pragma unroll 4
+#pragma unroll 8
             for (int c = 0; c < nc; ++c) {
               const V4 Sc = cand[warp][c];
               bool acc;

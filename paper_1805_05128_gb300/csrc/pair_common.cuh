@@ -468,14 +468,19 @@ struct FwdAcc {
       const double R = __dmul_rn(a.kh, __dadd_rn(Ai.w, Aj.w));
       acc = valid && P::r2_of(ex, ey, ez) < __dmul_rn(R, R);
     }
-    if constexpr (kX2 && !EXTRA) {
+    if constexpr (kX2) {
       // Branch-free: every listed entry runs the flux arithmetic, and the
       // kernel derivative is set to zero where the pair does not interact
       // (such entries lie at q >= kappa, where W' vanishes anyway; the select
       // keeps the exact pair set).  With ~86 % of the entries interacting the
       // lanes would run the flux almost always; the branches and their
-      // reconvergence cost more than the idle arithmetic.
+      // reconvergence cost more than the idle arithmetic.  The side outputs
+      // (rare: a unit boundary, a pair query) keep their branch.
       flux_x2(a, Ai, Bi, Ci, Aj, Bj, Cj, dx, dy, dz, r2, acc && r2 > T(0));
+      if constexpr (EXTRA) {
+        if (acc) dmax = Aj.w > dmax ? Aj.w : dmax;
+        if (acc && r2 > T(0)) side_outputs(a, i, ui, j);
+      }
     } else {
       if (acc) flux_at(a, i, Ai, Bi, Ci, ui, j, Aj, Bj, Cj, dx, dy, dz, r2);
     }
