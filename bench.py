@@ -260,6 +260,26 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     builds = (sim.list_builds()[0] - builds0) if args.beta > 0 else args.steps
     status = sim.read_status()
     ms = max_over_ranks(ms, dist, dev)
+
+    # ---- the same K steps captured in one CUDA graph (fewer launch gaps), replayed
+    # once untimed and once timed; the state simply advances
+    graph_ms, graph_builds = None, 0
+    if not args.no_graph:
+        from paper_1805_05128_gb300.ensemble import GraphRun
+        gr = GraphRun(sim, args.steps)
+        gr.replay()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        gb0 = sim.list_builds()[0] if args.beta > 0 else 0
+        e0.record()
+        gr.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        graph_builds = (sim.list_builds()[0] - gb0) if args.beta > 0 else args.steps
+        graph_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        status = status or sim.read_status()
+        del gr
     n_total = prob.n * world
     value = job_value(prob.n, world, args.steps, ms)
 
@@ -314,6 +334,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                         "frac": achieved / peak, "traffic": traffic,
                         "peak_note": "FP32 152 SM x 128 lanes x 2 x 2.07 GHz (derived from unit counts and clock)",
                         "pair_ms_per_launch": pair_ms_avg, "pair_share": pair_ms / ms},
+           "graph": None if graph_ms is None else {
+               "ms_per_step": graph_ms / args.steps,
+               "value": job_value(prob.n, world, args.steps, graph_ms), "list_builds": graph_builds,
+               "form": "the same number of steps captured in one CUDA graph (ensemble.GraphRun) and replayed "
+                       "after the timed eager region; no per-kernel events inside the graph"},
            "clocks": clk.summary(), "gpu_launches": launches, "device_status": status,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "steps": e2e_steps}}
@@ -669,6 +694,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the K steps")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-step, batched-ensemble and adjoint measurements")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))

@@ -389,7 +389,8 @@ int voronoi_assign_static(int64_t n, const double* x, const double* y, const dou
 /* Measurement support.  sph_profile(h, 1) starts recording CUDA events
  * around every launch of the pair kernel on the caller's stream and counts
  * every kernel launch of the library; sph_profile(h, 0) stops.  Resets the
- * records either way. */
+ * records either way.  Pair-kernel launches issued while the stream is being
+ * captured into a CUDA graph are counted as launches but not timed. */
 int sph_profile(sph_handle* h, int enable);
 
 /* Synchronise and report, since the last sph_profile/sph_profile_read: the

@@ -633,7 +633,9 @@ __global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, PermArrays
   }
 }
 
-__global__ void k_scatter_back(int64_t n, PermArrays a, const char* scratch) {
+// Writes the gathered arrays back; with perm, also makes the slot order the
+// identity (particle sl now sits in slot sl).
+__global__ void k_scatter_back(int64_t n, PermArrays a, const char* scratch, int32_t* perm) {
   int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (sl >= n) return;
   size_t off = 0;
@@ -642,6 +644,7 @@ __global__ void k_scatter_back(int64_t n, PermArrays a, const char* scratch) {
     else reinterpret_cast<uint32_t*>(a.ptr[k])[sl] = reinterpret_cast<const uint32_t*>(scratch + off)[sl];
     off += (size_t)a.bytes[k] * n;
   }
+  if (perm) perm[sl] = (int32_t)sl;
 }
 
 // ---------------------------------------------------------------------------
@@ -834,10 +837,27 @@ cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st, const 
   add(s.mat, 4); add(s.unit, 4);
   int g = grid_for(h->n, kBlock);
   k_gather<<<g, kBlock, 0, st>>>(h->n, order ? order : h->perm, a, reinterpret_cast<char*>(h->scratch));
-  k_scatter_back<<<g, kBlock, 0, st>>>(h->n, a, reinterpret_cast<const char*>(h->scratch));
+  k_scatter_back<<<g, kBlock, 0, st>>>(h->n, a, reinterpret_cast<const char*>(h->scratch), nullptr);
   h->launches += 2;
-  // particle indices changed under the slot order of the Verlet lists
-  if (h->verlet) return cudaMemsetAsync(&h->vflag[1], 0xff, sizeof(int), st);
+  if (!h->verlet) return cudaGetLastError();
+  // another order than the slot order (the unit-major evaluation order) moves
+  // particles between slots under the Verlet lists: rebuild them
+  if (order) return cudaMemsetAsync(&h->vflag[1], 0xff, sizeof(int), st);
+  // In slot order the mesh, the slots and the lists stay as they are: particle
+  // q is now the one in slot q, so the slot permutation becomes the identity
+  // and the build-time positions and sizes of the validity criterion follow
+  // their particles.
+  PermArrays b;
+  b.count = 0;
+  for (int k = 0; k < 4; ++k)
+    if (k < h->dp.dim || k == 3) {
+      b.ptr[b.count] = h->vref + (size_t)k * h->n;
+      b.bytes[b.count] = 8;
+      ++b.count;
+    }
+  k_gather<<<g, kBlock, 0, st>>>(h->n, h->perm, b, reinterpret_cast<char*>(h->scratch));
+  k_scatter_back<<<g, kBlock, 0, st>>>(h->n, b, reinterpret_cast<const char*>(h->scratch), h->perm);
+  h->launches += 2;
   return cudaGetLastError();
 }
 

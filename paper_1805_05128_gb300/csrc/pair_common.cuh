@@ -698,8 +698,14 @@ __device__ __forceinline__ void warp_counters(const PairArgs& a, bool act, unsig
 constexpr int kWarps = kPairBlock / 32;
 
 // CUDA events around a pair-kernel launch when profiling (sph_profile).
+// Launches captured into a CUDA graph are not timed: a record under capture
+// only orders the graph's nodes, and its event has no time to read.
 cudaError_t prof_record(sph_handle* h, bool start, cudaStream_t st) {
   if (!h->profiling) return cudaSuccess;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(st, &cap);
+  if (ce != cudaSuccess) return ce;
+  if (cap != cudaStreamCaptureStatusNone) return cudaSuccess;
   if (start && h->prof_used + 2 > h->prof_events.size()) {
     for (int k = 0; k < 64; ++k) {
       cudaEvent_t ev;

@@ -133,8 +133,8 @@ def test_lists_inside_a_cuda_graph_equal_eager():
 
 
 def test_lists_with_work_units_and_rebalancing():
-    """Rebalancing renumbers the particles, which invalidates the lists; the
-    run stays within the one-step tolerance and conserves mass."""
+    """Rebalancing renumbers the particles into slot order under the lists;
+    the run stays within the one-step tolerance and conserves mass."""
     from paper_1805_05128_gb300 import Simulation
     prob = synth.plate_impact(6, (16, 16, 5), a=1e-4, v=3000.0, units=8, seed=7, jitter=0.05)
     gen = synth.problem_generators(prob)
@@ -143,7 +143,7 @@ def test_lists_with_work_units_and_rebalancing():
     sim.build_cells()
     m0 = float(sim.conservation().cpu().numpy()[0][0])
     sim.step(12)
-    assert sim.list_builds()[0] >= 3          # first step, and after each of the two rebalances
+    assert sim.list_builds()[0] >= 2
     g0 = sim.numpy()
     p, _ = O.from_problem(prob)
     s = O.State(prob.dim, {k: g0[k] for k in O.State.FIELDS + O.State.DERIVED if k in g0}, None)
@@ -155,6 +155,32 @@ def test_lists_with_work_units_and_rebalancing():
     for k in ("vz", "rho", "E", "az", "drho"):
         assert _rel(g[k], getattr(s, k)) <= 1e-4, (k, _rel(g[k], getattr(s, k)))
     assert float(sim.conservation().cpu().numpy()[0][0]) == pytest.approx(m0, rel=1e-15)
+    assert sim.read_status() == 0
+    sim.close()
+
+
+def test_lists_survive_the_renumbering_of_a_rebalance():
+    """A rebalance (Alg. 1: shift the generators, reassign, renumber in cell
+    order) permutes the particles into the slot order of the current mesh,
+    so the lists, the mesh and the slots stay valid: a slow flow keeps its
+    first build through four rebalances, and every FP64 step agrees with the
+    oracle (which never renumbers) particle by particle to 1e-10."""
+    from paper_1805_05128_gb300 import Simulation
+    prob = synth.plate_impact(5, (14, 14, 4), a=1e-4, v=20.0, units=8, seed=3, jitter=0.05)
+    gen = synth.problem_generators(prob)
+    sim = Simulation(prob, precision="fp64", generators=gen, n_upd=3, cell_beta=0.4)
+    sim.assign()
+    p, s = O.from_problem(prob)
+    t = 0.0
+    for step in range(13):
+        sim.step(1)
+        t, _ = O.step(p, s, 1, rates_valid=step > 0, t=t)
+        g = sim.numpy()
+        order = np.argsort(g["id"])
+        for k in ("x", "z", "vx", "vz", "rho", "E", "az", "drho", "dE"):
+            assert _rel(g[k][order], getattr(s, k)) <= 1e-10, (step, k, _rel(g[k][order], getattr(s, k)))
+    assert not np.array_equal(np.argsort(g["id"]), np.arange(len(g["id"])))   # renumbered
+    assert sim.list_builds()[0] == 1
     assert sim.read_status() == 0
     sim.close()
 
