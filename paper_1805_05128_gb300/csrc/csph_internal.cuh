@@ -39,6 +39,7 @@ struct BlockPart {
   long long d1, d2;        // two largest particle sizes
   long long dtmin;         // min_i eta d_i / (c_i + |v_i|)
   long long viol;          // Verlet lists: max_i of the validity criterion (> 0: rebuild)
+  int dlo[3], dhi[3];      // Verlet lists: box of the displacements since the build (FP32 order keys)
 };
 
 // Material constants on the device.
@@ -85,6 +86,8 @@ struct DevParams {
   double kappa, eta, cfl, cell_beta, kh;  // kh = (0.5 kappa) eta
   const Mat* mat;                         // device table of n_mat materials
   const double* vref;                     // Verlet lists: x, y, z, d at the last build (4 arrays of n), or NULL
+  const double* vframe;                   // Verlet lists: this step's frame displacement U (3) and the
+                                          // number of steps since the build, or NULL
   int64_t n;                              // particles of the handle (stride of vref)
   double vscale;                          // mixed precision: packed volume = (m / rho) vscale (a power of two)
 };
@@ -199,7 +202,9 @@ struct sph_handle {
   int vcap = 0;                       // list capacity per particle
   uint32_t* vlist = nullptr;          // [n][vcap]: entry k of slot i at i vcap + k = (slot j << 5) | cell code
   int32_t* vcnt = nullptr;            // [n] entries of slot i
-  double* vref = nullptr;             // [4 n] x, y, z, d of each particle at the last build
+  double* vref = nullptr;             // [4 n] x, y, z, d of each particle at the last build, then
+                                      // [4] the frame of the validity criterion (U, steps since the build)
+  double* vframe = nullptr;           // = vref + 4 n
   int* vflag = nullptr;               // [0]: rebuild in this step; [1]: lists invalid; [2]: builds done
 
   // Work units as the partition of the list kernel's work (Verlet lists with

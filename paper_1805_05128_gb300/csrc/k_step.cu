@@ -26,12 +26,20 @@ __device__ __forceinline__ void top2_merge(long long& a1, long long& a2, long lo
   else { a2 = b2 > a1 ? b2 : a1; a1 = b1; }
 }
 
+// Order keys of FP32 values (integer order = numeric order), as dkey.
+__device__ __forceinline__ int fkey(float x) {
+  const int b = __float_as_int(x);
+  return b < 0 ? b ^ 0x7fffffff : b;
+}
+__device__ __forceinline__ float funkey(int k) { return __int_as_float(k < 0 ? k ^ 0x7fffffff : k); }
+
 struct Red {
   long long lo[3], hi[3], d1, d2, dtmin, viol;
+  int dlo[3], dhi[3];
 };
 
 __device__ __forceinline__ void red_init(Red& r) {
-  for (int a = 0; a < 3; ++a) { r.lo[a] = LLONG_MAX; r.hi[a] = LLONG_MIN; }
+  for (int a = 0; a < 3; ++a) { r.lo[a] = LLONG_MAX; r.hi[a] = LLONG_MIN; r.dlo[a] = INT_MAX; r.dhi[a] = INT_MIN; }
   r.d1 = 0; r.d2 = 0; r.dtmin = LLONG_MAX; r.viol = LLONG_MIN;
 }
 
@@ -39,6 +47,8 @@ __device__ __forceinline__ void red_merge(Red& a, const Red& b) {
   for (int k = 0; k < 3; ++k) {
     a.lo[k] = a.lo[k] < b.lo[k] ? a.lo[k] : b.lo[k];
     a.hi[k] = a.hi[k] > b.hi[k] ? a.hi[k] : b.hi[k];
+    a.dlo[k] = min(a.dlo[k], b.dlo[k]);
+    a.dhi[k] = max(a.dhi[k], b.dhi[k]);
   }
   top2_merge(a.d1, a.d2, b.d1, b.d2);
   a.dtmin = a.dtmin < b.dtmin ? a.dtmin : b.dtmin;
@@ -50,6 +60,8 @@ __device__ __forceinline__ Red shfl_red(const Red& r, int o) {
   for (int a = 0; a < 3; ++a) {
     q.lo[a] = __shfl_xor_sync(0xffffffffu, r.lo[a], o);
     q.hi[a] = __shfl_xor_sync(0xffffffffu, r.hi[a], o);
+    q.dlo[a] = __shfl_xor_sync(0xffffffffu, r.dlo[a], o);
+    q.dhi[a] = __shfl_xor_sync(0xffffffffu, r.dhi[a], o);
   }
   q.d1 = __shfl_xor_sync(0xffffffffu, r.d1, o);
   q.d2 = __shfl_xor_sync(0xffffffffu, r.d2, o);
@@ -89,7 +101,7 @@ __device__ long long block_min_key(long long k) {
 
 __device__ __forceinline__ void write_part(BlockPart* part, const Red& r) {
   BlockPart& b = part[blockIdx.x];
-  for (int a = 0; a < 3; ++a) { b.lo[a] = r.lo[a]; b.hi[a] = r.hi[a]; }
+  for (int a = 0; a < 3; ++a) { b.lo[a] = r.lo[a]; b.hi[a] = r.hi[a]; b.dlo[a] = r.dlo[a]; b.dhi[a] = r.dhi[a]; }
   b.d1 = r.d1; b.d2 = r.d2; b.dtmin = r.dtmin; b.viol = r.viol;
 }
 
@@ -436,15 +448,21 @@ __global__ void k_kick_drift(DevParams P, sph_state s, const int64_t* __restrict
     r.d1 = dkey(d);
     if (P.vref) {
       // Verlet-list validity: a listed superset of the pairs within kappa h_ij holds as long
-      // as |x_i - x_i^b| + kh max(0, d_i - d_i^b) <= beta kh d_i^b for every particle (b: the
-      // last build; summing the bounds of i and j covers the pair), kept with a 5 % margin
-      // (differences in FP64, the bound itself in FP32: the 5 % margin dwarfs its rounding)
+      // as |x_i - x_i^b - U| + kh max(0, d_i - d_i^b) <= beta kh d_i^b for every particle
+      // (b: the last build).  U is one displacement shared by all particles, any vector:
+      // the separation of a pair changes by (x_j - x_j^b - U) - (x_i - x_i^b - U), so
+      // summing the bounds of i and j covers the pair.  U follows the bulk motion (the
+      // midpoint of the displacement box, extrapolated from the previous step), so a body
+      // in uniform motion keeps its lists.  Kept with a 5 % margin (differences in FP64,
+      // the bound itself in FP32: the 5 % margin dwarfs its rounding).
       float dsq = 0.0f;
 #pragma unroll
       for (int a = 0; a < 3; ++a)
         if (a < dim) {
-          const float dx = (float)(x[a] - xb[a]);
+          const double dd = x[a] - xb[a];
+          const float dx = (float)(dd - P.vframe[a]);
           dsq += dx * dx;
+          r.dlo[a] = r.dhi[a] = fkey((float)dd);
         }
       const float kh = (float)P.kh;
       const float crit = sqrtf(dsq) + kh * fmaxf((float)(d - db), 0.0f) - 0.95f * (float)P.cell_beta * kh * (float)db;
@@ -752,30 +770,60 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
 
 // Verlet lists: vflag[0] = lists invalid (vflag[1]) or the validity criterion
 // of k_kick_drift failed for some particle of any instance.
-__global__ void k_verlet_flag(const BlockPart* __restrict__ part, int nblk, int* vflag) {
-  __shared__ long long sh[1024];
+// Also sets the frame displacement U of the next step's criterion: the
+// midpoint of this step's displacement box, which covers k steps since the
+// build, extrapolated to k + 1 steps; after a build, one step's worth of it
+// (the new reference is this step's state); 0 while the reference is void.
+// Any U keeps the criterion sound; a good one only makes builds rarer.
+__global__ void k_verlet_flag(const BlockPart* __restrict__ part, int nblk, int* vflag, double* vframe) {
+  __shared__ long long shv[32];
+  __shared__ int shb[32][6];
   long long m = LLONG_MIN;
-  for (int k = threadIdx.x; k < nblk; k += 4 * blockDim.x) {   // four independent loads in flight
-    long long q[4];
+  int b[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) {
+    const BlockPart& q = part[k];
+    m = q.viol > m ? q.viol : m;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int kk = k + u * (int)blockDim.x;
-      q[u] = kk < nblk ? part[kk].viol : LLONG_MIN;
+    for (int a = 0; a < 3; ++a) { b[a] = min(b[a], q.dlo[a]); b[3 + a] = max(b[3 + a], q.dhi[a]); }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long qm = __shfl_xor_sync(0xffffffffu, m, o);
+    m = qm > m ? qm : m;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      b[a] = min(b[a], __shfl_xor_sync(0xffffffffu, b[a], o));
+      b[3 + a] = max(b[3 + a], __shfl_xor_sync(0xffffffffu, b[3 + a], o));
     }
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    shv[w] = m;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) m = q[u] > m ? q[u] : m;
+    for (int a = 0; a < 6; ++a) shb[w][a] = b[a];
   }
-  sh[threadIdx.x] = m;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) sh[threadIdx.x] = sh[threadIdx.x + w] > sh[threadIdx.x] ? sh[threadIdx.x + w] : sh[threadIdx.x];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      m = shv[k] > m ? shv[k] : m;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { b[a] = min(b[a], shb[k][a]); b[3 + a] = max(b[3 + a], shb[k][3 + a]); }
+    }
+    const bool void_ref = vflag[1] != 0;
+    const bool rebuild = m > 0 || void_ref;
+    vflag[0] = rebuild ? 1 : 0;
+    const double ks = vframe[3] >= 1.0 ? vframe[3] : 1.0;   // steps covered by this step's displacements
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double mid = b[a] <= b[3 + a] ? 0.5 * ((double)funkey(b[a]) + (double)funkey(b[3 + a])) : 0.0;
+      vframe[a] = void_ref ? 0.0 : (rebuild ? mid / ks : mid * (ks + 1.0) / ks);
+    }
+    vframe[3] = rebuild ? 1.0 : ks + 1.0;
   }
-  if (threadIdx.x == 0) vflag[0] = (sh[0] > 0 || vflag[1] != 0) ? 1 : 0;
 }
 
 cudaError_t launch_verlet_flag(sph_handle* h, cudaStream_t st) {
-  k_verlet_flag<<<1, 1024, 0, st>>>(h->part, h->nblk, h->vflag);
+  k_verlet_flag<<<1, 1024, 0, st>>>(h->part, h->nblk, h->vflag, h->vframe);
   h->launches += 1;
   return cudaGetLastError();
 }
