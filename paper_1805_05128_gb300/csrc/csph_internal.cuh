@@ -306,6 +306,35 @@ __device__ __forceinline__ T kernel_dw(int kernel, T kappa, T r, T h) {
 }
 
 // --------------------------------------------------------------------------
+// Programmatic dependent launch of a step's kernels: each is launched while
+// its predecessor in the stream still runs (launch_chained), so that the
+// launch overhead overlaps the predecessor.  Every kernel launched this way
+// calls chain_entry() first: it waits for the predecessor's completion and
+// memory (which, by the same rule one level up, implies every earlier
+// kernel's), and only then lets its own successor launch.  Launched without
+// the attribute, both instructions do nothing.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void chain_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// --------------------------------------------------------------------------
 // Host helpers shared by the translation units
 // --------------------------------------------------------------------------
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
                                                  : (MODE == kModeGrad ? (MIXED ? 5 : 3)
                                                  : (MODE == kModeList ? (MIXED ? kBuildBlocks : 4) : (MIXED ? 6 : 4))))
     k_pair(PairArgs a) {
+  chain_entry();
   constexpr bool VJP = MODE == kModeVjp;
   constexpr bool LIST = MODE == kModeList;
   constexpr bool GRAD = MODE == kModeGrad;
@@ -520,8 +521,7 @@ cudaError_t launch_one(const PairArgs& args, int blocks_per_sm, cudaStream_t st)
     if (per_sm < 1) per_sm = 1;
   }
   const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
-  k_pair<MIXED, DIM, MODE, HLL, EXTRA><<<sms * b, kPairBlock, 0, st>>>(args);
-  return cudaGetLastError();
+  return launch_chained(k_pair<MIXED, DIM, MODE, HLL, EXTRA>, dim3(sms * b), dim3(kPairBlock), st, args);
 }
 
 template <bool MIXED, int MODE, bool HLL, bool EXTRA>

@@ -59,6 +59,7 @@ __device__ __forceinline__ T slot_sum(const Kahan<T>& k) {
 
 template <bool MIXED, int DIM, bool HLL = false, bool EXTRA = true, bool STAGE = false>
 __global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pair_lists(PairArgs a) {
+  chain_entry();
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
   using V4 = typename P::V4;
@@ -452,8 +453,7 @@ cudaError_t launch_lists_one(const PairArgs& args, int blocks_per_sm, cudaStream
   int grid = sms * b;
   if (args.unit_sched == SPH_SCHED_UNITS_OWNED && args.K > 0)   // the same number of CTAs for every unit
     grid = args.K * (grid / args.K > 0 ? grid / args.K : 1);
-  k_pair_lists<MIXED, DIM, HLL, EXTRA, STAGE><<<grid, kPairBlock, 0, st>>>(args);
-  return cudaGetLastError();
+  return launch_chained(k_pair_lists<MIXED, DIM, HLL, EXTRA, STAGE>, dim3(grid), dim3(kPairBlock), st, args);
 }
 
 template <bool MIXED, bool HLL, bool EXTRA, bool STAGE>

@@ -18,6 +18,13 @@ namespace {
 
 __device__ __forceinline__ double ld(const double* a, int64_t i) { return a ? a[i] : 0.0; }
 
+// Return the status of a failed launch from the enclosing launcher.
+#define CKL(call)                            \
+  do {                                       \
+    const cudaError_t ckl_e_ = (call);       \
+    if (ckl_e_ != cudaSuccess) return ckl_e_; \
+  } while (0)
+
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
 // Merge the top-2 multisets (a1 >= a2) and (b1 >= b2).
@@ -112,6 +119,7 @@ __device__ __forceinline__ void write_part(BlockPart* part, const Red& r) {
 __global__ void k_derive(DevParams P, sph_state s, const int64_t* __restrict__ blk_start,
                          const int64_t* __restrict__ blk_end, BlockPart* part, int write_derived,
                          int with_bbox) {
+  chain_entry();
   int64_t p = blk_start[blockIdx.x] + threadIdx.x;
   Red r;
   red_init(r);
@@ -152,6 +160,7 @@ __global__ void k_derive(DevParams P, sph_state s, const int64_t* __restrict__ b
 // flight per thread.
 __global__ void k_reduce_dt(const int32_t* __restrict__ inst_blk, const BlockPart* __restrict__ part, double cfl,
                             double* dt, long long* dt_key, int from_key) {
+  chain_entry();
   const int b = blockIdx.x;
   if (from_key) {   // the fused second kick's keys: already the instance minimum
     if (threadIdx.x == 0) {
@@ -183,6 +192,7 @@ __global__ void k_reduce_dt(const int32_t* __restrict__ inst_blk, const BlockPar
 // instance from its block partials, into the grid record.
 __global__ void k_reduce_inst(const int32_t* __restrict__ inst_blk, const BlockPart* __restrict__ part,
                               GridInfo* grid, const int* __restrict__ gate) {
+  chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   int b = blockIdx.x;
   Red r;
@@ -208,6 +218,7 @@ __global__ void k_reduce_inst(const int32_t* __restrict__ inst_blk, const BlockP
 __global__ void k_grid_setup(DevParams P, int n_inst, const int64_t* __restrict__ inst_off,
                              const int64_t* __restrict__ inst_cap, GridInfo* grid, int64_t* total_cells,
                              int* status, const int* __restrict__ gate) {
+  chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   if (threadIdx.x != 0) return;
   int64_t off = 0;
@@ -258,6 +269,7 @@ __global__ void k_cell_count(int dim, sph_state s, const int64_t* __restrict__ b
                              const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst, int nblk,
                              const GridInfo* __restrict__ grid, int32_t* cell_count, int32_t* cell_of,
                              int32_t* rank, int* status, const int* __restrict__ gate) {
+  chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   // a capped grid strides over the segmented blocks (cheap to launch when gated)
   for (int lb = blockIdx.x; lb < nblk; lb += gridDim.x) {
@@ -283,6 +295,7 @@ constexpr int kScanTile = 1024;
 
 __global__ void k_scan_reduce(const int32_t* __restrict__ cnt, const int64_t* __restrict__ total,
                               int32_t* sums, const int* __restrict__ gate) {
+  chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   const int64_t tot = *total;
   __shared__ int sh[kBlock];
@@ -308,6 +321,7 @@ __global__ void k_scan_reduce(const int32_t* __restrict__ cnt, const int64_t* __
 
 // Single block: exclusive scan of the tile sums in place.
 __global__ void k_scan_sums(int32_t* sums, const int64_t* __restrict__ total, const int* __restrict__ gate) {
+  chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   int64_t ntiles = (*total + kScanTile - 1) / kScanTile;
   __shared__ int carry;
@@ -335,6 +349,7 @@ __global__ void k_scan_sums(int32_t* sums, const int64_t* __restrict__ total, co
 // Per tile: exclusive scan plus tile offset; zero the counts for the next use.
 __global__ void k_scan_down(int32_t* cnt, const int64_t* __restrict__ total, const int32_t* __restrict__ sums,
                             int32_t* start, int64_t n_total, const int* __restrict__ gate) {
+  chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   const int64_t tot = *total;
   constexpr int per = kScanTile / kBlock;  // 4 cells per thread
@@ -372,6 +387,7 @@ __global__ void k_scan_down(int32_t* cnt, const int64_t* __restrict__ total, con
 
 __global__ void k_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of, const int32_t* __restrict__ rank,
                                const int32_t* __restrict__ start, int32_t* perm, const int* __restrict__ gate) {
+  chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
     perm[start[cell_of[p]] + rank[p]] = (int32_t)p;
@@ -381,6 +397,7 @@ __global__ void k_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of, c
 // not reproducible; this makes the slot order a function of the state only).
 __global__ void k_cell_sort(const int64_t* __restrict__ total, const int32_t* __restrict__ start, int32_t* perm,
                             const int* __restrict__ gate) {
+  chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   const int64_t tot = *total;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (int64_t)gridDim.x * blockDim.x) {
@@ -402,6 +419,7 @@ template <bool MIXED>
 __global__ void k_kick_drift(DevParams P, sph_state s, const int64_t* __restrict__ blk_start,
                              const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst,
                              const double* __restrict__ dt, BlockPart* part, int* status) {
+  chain_entry();
   int64_t p = blk_start[blockIdx.x] + threadIdx.x;
   Red r;
   red_init(r);
@@ -482,6 +500,7 @@ __global__ void k_kick2(DevParams P, sph_state s, const int64_t* __restrict__ bl
                         const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst,
                         const int32_t* __restrict__ inst_blk, const double* __restrict__ dt, double* t_dev,
                         BlockPart* part) {
+  chain_entry();
   const int64_t p = blk_start[blockIdx.x] + threadIdx.x;
   const int b = blk_inst[blockIdx.x];
   if (t_dev && threadIdx.x == 0 && inst_blk[b] == (int)blockIdx.x) t_dev[b] += dt[b];
@@ -535,6 +554,7 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
                        void* packA, void* packB, void* packC, double* rho_slot, int32_t* slot_cell,
                        int32_t* slot_unit, int n_units, int* status, const int32_t* __restrict__ e_of_c,
                        int32_t* perm_e, void* packAc, const int* __restrict__ gate) {
+  chain_entry();
   const int64_t sc = blk_start[blockIdx.x] + threadIdx.x;     // cell-order slot
   if (sc >= blk_end[blockIdx.x]) return;
   // the operands go to the slot's evaluation position (unit-major order of the
@@ -722,25 +742,25 @@ static int capped_grid(int want) {
 }
 
 cudaError_t launch_derive_dt(sph_handle* h, const sph_state& s, bool with_bbox, cudaStream_t st) {
-  k_derive<<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->part, with_bbox ? 1 : 0,
-                                       with_bbox ? 1 : 0);
+  CKL(launch_chained(k_derive, dim3(h->nblk), dim3(kBlock), st, h->dp, s, h->blk_start, h->blk_end, h->part, with_bbox ? 1 : 0,
+                                       with_bbox ? 1 : 0));
   h->launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_dt(sph_handle* h, cudaStream_t st, bool from_key) {
-  k_reduce_dt<<<h->n_inst, kBlock, 0, st>>>(h->inst_blk, h->part, h->dp.cfl, h->dt, h->dt_key, from_key ? 1 : 0);
+  CKL(launch_chained(k_reduce_dt, dim3(h->n_inst), dim3(kBlock), st, h->inst_blk, h->part, h->dp.cfl, h->dt, h->dt_key, from_key ? 1 : 0));
   h->launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_kick_drift(sph_handle* h, const sph_state& s, cudaStream_t st) {
   if (h->dp.precision == SPH_PREC_MIXED)
-    k_kick_drift<true><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->dt, h->part,
-                                                   h->status);
+    CKL(launch_chained(k_kick_drift<true>, dim3(h->nblk), dim3(kBlock), st, h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->dt, h->part,
+                                                   h->status));
   else
-    k_kick_drift<false><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->dt, h->part,
-                                                    h->status);
+    CKL(launch_chained(k_kick_drift<false>, dim3(h->nblk), dim3(kBlock), st, h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->dt, h->part,
+                                                    h->status));
   h->launches += 1;
   return cudaGetLastError();
 }
@@ -748,20 +768,20 @@ cudaError_t launch_kick_drift(sph_handle* h, const sph_state& s, cudaStream_t st
 // Mesh from the block partials left by k_derive(with_bbox) or k_kick_drift,
 // then the counting sort of particles into cells.
 cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st, const int* gate) {
-  k_reduce_inst<<<h->n_inst, kBlock, 0, st>>>(h->inst_blk, h->part, h->grid, gate);
-  k_grid_setup<<<1, 32, 0, st>>>(h->dp, h->n_inst, h->inst_off, h->inst_cap, h->grid, h->total_cells,
-                                 h->status, gate);
-  k_cell_count<<<capped_grid(h->nblk), kBlock, 0, st>>>(h->dp.dim, s, h->blk_start, h->blk_end, h->blk_inst,
+  CKL(launch_chained(k_reduce_inst, dim3(h->n_inst), dim3(kBlock), st, h->inst_blk, h->part, h->grid, gate));
+  CKL(launch_chained(k_grid_setup, dim3(1), dim3(32), st, h->dp, h->n_inst, h->inst_off, h->inst_cap, h->grid, h->total_cells,
+                                 h->status, gate));
+  CKL(launch_chained(k_cell_count, dim3(capped_grid(h->nblk)), dim3(kBlock), st, h->dp.dim, s, h->blk_start, h->blk_end, h->blk_inst,
                                                         h->nblk, h->grid,
-                                           h->cell_count, h->cell_of, h->rank, h->status, gate);
+                                           h->cell_count, h->cell_of, h->rank, h->status, gate));
   int tiles = capped_grid(grid_for(h->cell_cap, kScanTile));
-  k_scan_reduce<<<tiles, kBlock, 0, st>>>(h->cell_count, h->total_cells, h->scan_sums, gate);
-  k_scan_sums<<<1, 1024, 0, st>>>(h->scan_sums, h->total_cells, gate);
-  k_scan_down<<<tiles, kBlock, 0, st>>>(h->cell_count, h->total_cells, h->scan_sums, h->cell_start, h->n, gate);
-  k_cell_scatter<<<capped_grid(grid_for(h->n, kBlock)), kBlock, 0, st>>>(h->n, h->cell_of, h->rank,
-                                                                         h->cell_start, h->perm, gate);
-  k_cell_sort<<<capped_grid(grid_for(h->cell_cap, kBlock)), kBlock, 0, st>>>(h->total_cells, h->cell_start,
-                                                                             h->perm, gate);
+  CKL(launch_chained(k_scan_reduce, dim3(tiles), dim3(kBlock), st, h->cell_count, h->total_cells, h->scan_sums, gate));
+  CKL(launch_chained(k_scan_sums, dim3(1), dim3(1024), st, h->scan_sums, h->total_cells, gate));
+  CKL(launch_chained(k_scan_down, dim3(tiles), dim3(kBlock), st, h->cell_count, h->total_cells, h->scan_sums, h->cell_start, h->n, gate));
+  CKL(launch_chained(k_cell_scatter, dim3(capped_grid(grid_for(h->n, kBlock))), dim3(kBlock), st, h->n, h->cell_of, h->rank,
+                                                                         h->cell_start, h->perm, gate));
+  CKL(launch_chained(k_cell_sort, dim3(capped_grid(grid_for(h->cell_cap, kBlock))), dim3(kBlock), st, h->total_cells, h->cell_start,
+                                                                             h->perm, gate));
   h->launches += 8;
   // a mesh built outside the Verlet sequence changes the slot order under the lists
   if (!gate && h->verlet) return cudaMemsetAsync(&h->vflag[1], 0xff, sizeof(int), st);
@@ -776,6 +796,7 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
 // (the new reference is this step's state); 0 while the reference is void.
 // Any U keeps the criterion sound; a good one only makes builds rarer.
 __global__ void k_verlet_flag(const BlockPart* __restrict__ part, int nblk, int* vflag, double* vframe) {
+  chain_entry();
   __shared__ long long shv[32];
   __shared__ int shb[32][6];
   long long m = LLONG_MIN;
@@ -823,7 +844,7 @@ __global__ void k_verlet_flag(const BlockPart* __restrict__ part, int nblk, int*
 }
 
 cudaError_t launch_verlet_flag(sph_handle* h, cudaStream_t st) {
-  k_verlet_flag<<<1, 1024, 0, st>>>(h->part, h->nblk, h->vflag, h->vframe);
+  CKL(launch_chained(k_verlet_flag, dim3(1), dim3(1024), st, h->part, h->nblk, h->vflag, h->vframe));
   h->launches += 1;
   return cudaGetLastError();
 }
@@ -833,15 +854,15 @@ cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStr
   int32_t* pe = eorder ? h->perm_e : nullptr;
   void* Ac = eorder ? h->packAc : nullptr;
   if (h->dp.precision == SPH_PREC_MIXED)
-    k_pack<true><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->grid, h->dt,
+    CKL(launch_chained(k_pack<true>, dim3(h->nblk), dim3(kBlock), st, h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->grid, h->dt,
                                              predict ? 1 : 0, h->perm, h->cell_of, h->packA, h->packB, h->packC,
                                              h->rho_slot, h->slot_cell, h->slot_unit, h->K, h->status, eoc, pe, Ac,
-                                             h->vflag);
+                                             h->vflag));
   else
-    k_pack<false><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->grid, h->dt,
+    CKL(launch_chained(k_pack<false>, dim3(h->nblk), dim3(kBlock), st, h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->grid, h->dt,
                                               predict ? 1 : 0, h->perm, h->cell_of, h->packA, h->packB, h->packC,
                                               h->rho_slot, h->slot_cell, h->slot_unit, h->K, h->status, eoc, pe, Ac,
-                                              h->vflag);
+                                              h->vflag));
   h->launches += 1;
   return cudaGetLastError();
 }
@@ -861,11 +882,11 @@ cudaError_t launch_pack_fp64(sph_handle* h, const sph_state& s, bool predict, vo
 cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st, bool next_dt) {
   BlockPart* part = next_dt ? h->part : nullptr;
   if (h->dp.precision == SPH_PREC_MIXED)
-    k_kick2<true><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->inst_blk, h->dt,
-                                              t_dev, part);
+    CKL(launch_chained(k_kick2<true>, dim3(h->nblk), dim3(kBlock), st, h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->inst_blk, h->dt,
+                                              t_dev, part));
   else
-    k_kick2<false><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->inst_blk, h->dt,
-                                               t_dev, part);
+    CKL(launch_chained(k_kick2<false>, dim3(h->nblk), dim3(kBlock), st, h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->inst_blk, h->dt,
+                                               t_dev, part));
   h->launches += 1;
   return cudaGetLastError();
 }
@@ -892,9 +913,9 @@ cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st, const 
   // particles between slots under the Verlet lists: rebuild them
   if (order) return cudaMemsetAsync(&h->vflag[1], 0xff, sizeof(int), st);
   // In slot order the mesh, the slots and the lists stay as they are: particle
-  // q is now the one in slot q, so the slot permutation becomes the identity
-  // and the build-time positions and sizes of the validity criterion follow
-  // their particles.
+  // q is now the one in slot q, so the slot permutation becomes the identity,
+  // and each particle's cell and the build-time positions and sizes of the
+  // validity criterion follow their particles.
   PermArrays b;
   b.count = 0;
   for (int k = 0; k < 4; ++k)
@@ -903,6 +924,9 @@ cudaError_t launch_renumber(sph_handle* h, sph_state& s, cudaStream_t st, const 
       b.bytes[b.count] = 8;
       ++b.count;
     }
+  b.ptr[b.count] = h->cell_of;
+  b.bytes[b.count] = 4;
+  ++b.count;
   k_gather<<<g, kBlock, 0, st>>>(h->n, h->perm, b, reinterpret_cast<char*>(h->scratch));
   k_scatter_back<<<g, kBlock, 0, st>>>(h->n, b, reinterpret_cast<const char*>(h->scratch), h->perm);
   h->launches += 2;
