@@ -321,10 +321,10 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     h->vcap = (int)std::min(65536.0, std::ceil(cap / 32.0) * 32.0);
     CKI(dalloc(&h->vlist, (size_t)h->vcap * n));
     CKI(dalloc(&h->vcnt, n));
-    CKI(dalloc(&h->vref, (size_t)4 * n + 4));
-    CKI(cudaMemset(h->vref, 0, sizeof(double) * 4 * n));
+    CKI(dalloc(&h->vref, (size_t)4 * n + 6));
+    CKI(cudaMemset(h->vref, 0, sizeof(double) * (4 * n + 6)));
     h->vframe = h->vref + (size_t)4 * n;
-    const double frame0[4] = {0.0, 0.0, 0.0, 1.0};   // U = 0, one step since the (first) build
+    const double frame0[4] = {0.0, 0.0, 0.0, 1.0};   // U = 0 (also its FP32 copy), one step since the build
     CKI(cudaMemcpy(h->vframe, frame0, sizeof(frame0), cudaMemcpyHostToDevice));
     CKI(dalloc(&h->vflag, 4));
     const int flags[4] = {1, 1, 0, 0};    // lists invalid until the first build
@@ -434,7 +434,7 @@ int sph_step(sph_handle* h, sph_state* s, int n_steps, double* t_dev, void* stre
     } else {
       CK(h, launch_build_grid(h, *s, st));
     }
-    CK(h, launch_pack(h, *s, true, st, h->verlet && h->unit_sched != SPH_SCHED_GLOBAL));
+    CK(h, launch_pack(h, *s, true, st, h->verlet && h->unit_sched != SPH_SCHED_GLOBAL, h->verlet));
     // unit adjacency is needed only from the evaluation that precedes a rebalance
     h->collect_adj = !vd3 || h->steps_since_balance + 1 >= h->p.n_upd;
     const bool next_dt = k + 1 < n_steps;

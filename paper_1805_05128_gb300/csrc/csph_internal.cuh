@@ -86,8 +86,8 @@ struct DevParams {
   double kappa, eta, cfl, cell_beta, kh;  // kh = (0.5 kappa) eta
   const Mat* mat;                         // device table of n_mat materials
   const double* vref;                     // Verlet lists: x, y, z, d at the last build (4 arrays of n), or NULL
-  const double* vframe;                   // Verlet lists: this step's frame displacement U (3) and the
-                                          // number of steps since the build, or NULL
+  const double* vframe;                   // Verlet lists: this step's frame displacement U (3), the
+                                          // number of steps since the build, U as 3 floats; or NULL
   int64_t n;                              // particles of the handle (stride of vref)
   double vscale;                          // mixed precision: packed volume = (m / rho) vscale (a power of two)
 };
@@ -203,7 +203,8 @@ struct sph_handle {
   uint32_t* vlist = nullptr;          // [n][vcap]: entry k of slot i at i vcap + k = (slot j << 5) | cell code
   int32_t* vcnt = nullptr;            // [n] entries of slot i
   double* vref = nullptr;             // [4 n] x, y, z, d of each particle at the last build, then
-                                      // [4] the frame of the validity criterion (U, steps since the build)
+                                      // [6] the frame of the validity criterion: U, steps since the
+                                      // build, U in FP32 (3 floats in the last two)
   double* vframe = nullptr;           // = vref + 4 n
   int* vflag = nullptr;               // [0]: rebuild in this step; [1]: lists invalid; [2]: builds done
 
@@ -354,7 +355,10 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
 cudaError_t launch_verlet_flag(sph_handle* h, cudaStream_t st);
 // eorder: write the packs in the unit-major evaluation order of the last build (e_of_c), the
 // particle of each evaluation slot (perm_e) and, at builds, the cell-order copy packAc
-cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st, bool eorder = false);
+// list_counters: also zero the counters of the list build and list evaluation
+// that follow in the step (which then need no memsets of their own)
+cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st, bool eorder = false,
+                        bool list_counters = false);
 // next_dt: also leave the CFL block minima of the new state in h->part (the next
 // step's dt without a k_derive pass)
 cudaError_t launch_kick2(sph_handle* h, const sph_state& s, double* t_dev, cudaStream_t st, bool next_dt = false);
@@ -380,7 +384,8 @@ cudaError_t launch_pair_vjp(sph_handle* h, const sph_state& s, const void* G, co
                             cudaStream_t st, const void* A64 = nullptr, const void* B64 = nullptr,
                             const void* C64 = nullptr);
 // Verlet lists: build (k_pair over the (1 + beta) radius, returns at once unless vflag[0]) and
-// the pair evaluation over the lists
+// the pair evaluation over the lists; both only after a launch_pack with list_counters in
+// the same step, which zeroes their counters
 cudaError_t launch_list_build(sph_handle* h, const sph_state& s, cudaStream_t st);
 // kick2: also the second half kick of the step (and the instance time, and with
 // next_dt the CFL keys of the new state), fused into the rate write

@@ -592,10 +592,10 @@ cudaError_t launch_list_build(sph_handle* h, const sph_state& s, cudaStream_t st
     a.e_of_c = h->e_of_c;
     a.Ac = h->packAc;
   }
-  cudaError_t e = cudaMemsetAsync(&h->counters[5], 0, sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return e;
-  e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, kModeList>(h, a, st)
-                                        : launch_dim<false, kModeList>(h, a, st);
+  // work counter zeroed by the step's k_pack (launch_pack with list_counters)
+  a.work_counter = &h->counters[7];
+  cudaError_t e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, kModeList>(h, a, st)
+                                                    : launch_dim<false, kModeList>(h, a, st);
   h->launches += 1;
   return e;
 }

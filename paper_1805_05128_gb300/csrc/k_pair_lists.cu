@@ -504,8 +504,8 @@ cudaError_t launch_pair_lists(sph_handle* h, const sph_state& s, cudaStream_t st
   a.kx_t = t_dev;
   a.dt_key = h->dt_key;
   a.dp = h->dp;
-  cudaError_t e = cudaMemsetAsync(h->counters, 0, 3 * sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return e;
+  // pair counts and work counter zeroed by the step's k_pack (launch_pack with list_counters)
+  cudaError_t e = cudaSuccess;
   if (h->unit_sched != SPH_SCHED_GLOBAL) {
     // operands, lists and rows in the unit-major evaluation order; per-unit
     // queues and times reset for this launch (starts to the maximum, ends to 0)
@@ -519,8 +519,6 @@ cudaError_t launch_pair_lists(sph_handle* h, const sph_state& s, cudaStream_t st
     if ((e = cudaMemsetAsync(h->unit_t, 0xff, sizeof(unsigned long long) * h->K, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(h->unit_t + h->K, 0, sizeof(unsigned long long) * h->K, st)) != cudaSuccess) return e;
   }
-  e = cudaMemsetAsync(&h->counters[5], 0, sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return e;
   if ((e = prof_record(h, true, st)) != cudaSuccess) return e;
   e = h->dp.precision == SPH_PREC_MIXED ? launch_lists_dim<true>(h, a, st) : launch_lists_dim<false>(h, a, st);
   h->launches += 1;

@@ -473,14 +473,16 @@ __global__ void k_kick_drift(DevParams P, sph_state s, const int64_t* __restrict
       // midpoint of the displacement box, extrapolated from the previous step), so a body
       // in uniform motion keeps its lists.  Kept with a 5 % margin (differences in FP64,
       // the bound itself in FP32: the 5 % margin dwarfs its rounding).
+      // (The displacement and U in FP32: their rounding, ~1e-7 of each, is far
+      // inside the margin.)  The box is that of x - x^b - U.
+      const float* Uf = reinterpret_cast<const float*>(P.vframe + 4);
       float dsq = 0.0f;
 #pragma unroll
       for (int a = 0; a < 3; ++a)
         if (a < dim) {
-          const double dd = x[a] - xb[a];
-          const float dx = (float)(dd - P.vframe[a]);
+          const float dx = (float)(x[a] - xb[a]) - Uf[a];
           dsq += dx * dx;
-          r.dlo[a] = r.dhi[a] = fkey((float)dd);
+          r.dlo[a] = r.dhi[a] = fkey(dx);
         }
       const float kh = (float)P.kh;
       const float crit = sqrtf(dsq) + kh * fmaxf((float)(d - db), 0.0f) - 0.95f * (float)P.cell_beta * kh * (float)db;
@@ -553,8 +555,18 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
                        const int32_t* __restrict__ perm, const int32_t* __restrict__ cell_of,
                        void* packA, void* packB, void* packC, double* rho_slot, int32_t* slot_cell,
                        int32_t* slot_unit, int n_units, int* status, const int32_t* __restrict__ e_of_c,
-                       int32_t* perm_e, void* packAc, const int* __restrict__ gate) {
+                       int32_t* perm_e, void* packAc, const int* __restrict__ gate,
+                       unsigned long long* list_counters) {
   chain_entry();
+  // the counters of the list build and the list evaluation that follow (the
+  // evaluation's pair counts and work counter, the build's work counter)
+  if (list_counters && blockIdx.x == 0 && threadIdx.x == 0) {
+    list_counters[0] = 0ull;
+    list_counters[1] = 0ull;
+    list_counters[2] = 0ull;
+    list_counters[5] = 0ull;
+    list_counters[7] = 0ull;
+  }
   const int64_t sc = blk_start[blockIdx.x] + threadIdx.x;     // cell-order slot
   if (sc >= blk_end[blockIdx.x]) return;
   // the operands go to the slot's evaluation position (unit-major order of the
@@ -834,10 +846,14 @@ __global__ void k_verlet_flag(const BlockPart* __restrict__ part, int nblk, int*
     const bool rebuild = m > 0 || void_ref;
     vflag[0] = rebuild ? 1 : 0;
     const double ks = vframe[3] >= 1.0 ? vframe[3] : 1.0;   // steps covered by this step's displacements
+    float* Uf = reinterpret_cast<float*>(vframe + 4);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double mid = b[a] <= b[3 + a] ? 0.5 * ((double)funkey(b[a]) + (double)funkey(b[3 + a])) : 0.0;
+      // midpoint of the box of x - x^b, from that of x - x^b - U
+      const double mid = b[a] <= b[3 + a] ? 0.5 * ((double)funkey(b[a]) + (double)funkey(b[3 + a])) + vframe[a]
+                                          : vframe[a];
       vframe[a] = void_ref ? 0.0 : (rebuild ? mid / ks : mid * (ks + 1.0) / ks);
+      Uf[a] = (float)vframe[a];
     }
     vframe[3] = rebuild ? 1.0 : ks + 1.0;
   }
@@ -849,7 +865,9 @@ cudaError_t launch_verlet_flag(sph_handle* h, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st, bool eorder) {
+cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStream_t st, bool eorder,
+                        bool list_counters) {
+  unsigned long long* lc = list_counters ? h->counters : nullptr;
   const int32_t* eoc = eorder ? h->e_of_c : nullptr;
   int32_t* pe = eorder ? h->perm_e : nullptr;
   void* Ac = eorder ? h->packAc : nullptr;
@@ -857,12 +875,12 @@ cudaError_t launch_pack(sph_handle* h, const sph_state& s, bool predict, cudaStr
     CKL(launch_chained(k_pack<true>, dim3(h->nblk), dim3(kBlock), st, h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->grid, h->dt,
                                              predict ? 1 : 0, h->perm, h->cell_of, h->packA, h->packB, h->packC,
                                              h->rho_slot, h->slot_cell, h->slot_unit, h->K, h->status, eoc, pe, Ac,
-                                             h->vflag));
+                                             h->vflag, lc));
   else
     CKL(launch_chained(k_pack<false>, dim3(h->nblk), dim3(kBlock), st, h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->grid, h->dt,
                                               predict ? 1 : 0, h->perm, h->cell_of, h->packA, h->packB, h->packC,
                                               h->rho_slot, h->slot_cell, h->slot_unit, h->K, h->status, eoc, pe, Ac,
-                                              h->vflag));
+                                              h->vflag, lc));
   h->launches += 1;
   return cudaGetLastError();
 }
@@ -874,7 +892,7 @@ cudaError_t launch_pack_fp64(sph_handle* h, const sph_state& s, bool predict, vo
                              double* rho_out, cudaStream_t st) {
   k_pack<false><<<h->nblk, kBlock, 0, st>>>(h->dp, s, h->blk_start, h->blk_end, h->blk_inst, h->grid, h->dt,
                                             predict ? 1 : 0, h->perm, h->cell_of, A, B, C, rho_out, h->slot_cell,
-                                            h->slot_unit, h->K, h->status, nullptr, nullptr, nullptr, nullptr);
+                                            h->slot_unit, h->K, h->status, nullptr, nullptr, nullptr, nullptr, nullptr);
   h->launches += 1;
   return cudaGetLastError();
 }
