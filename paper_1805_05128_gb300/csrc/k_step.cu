@@ -399,15 +399,54 @@ __global__ void k_cell_sort(const int64_t* __restrict__ total, const int32_t* __
                             const int* __restrict__ gate) {
   chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
+  // One warp per cell: each lane holds up to kSortPer of the cell's particle
+  // indices and counts, by broadcasts, the cell's indices smaller than each
+  // (indices are distinct), which is its position in ascending order.  Cells
+  // above 32 kSortPer particles (never on a sane mesh: the cell code admits
+  // 2047) are sorted by one lane.
+  constexpr int kSortPer = 4;
   const int64_t tot = *total;
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (int64_t)gridDim.x * blockDim.x) {
-    int b = start[c], e = start[c + 1];
-    for (int i = b + 1; i < e; ++i) {
-      int32_t v = perm[i];
-      int j = i - 1;
-      while (j >= b && perm[j] > v) { perm[j + 1] = perm[j]; --j; }
-      perm[j + 1] = v;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = w0; c < tot; c += nw) {
+    const int b = start[c], e = start[c + 1], n = e - b;
+    if (n <= 1) continue;
+    if (n > 32 * kSortPer) {
+      if (lane == 0)
+        for (int i = b + 1; i < e; ++i) {
+          int32_t v = perm[i];
+          int j = i - 1;
+          while (j >= b && perm[j] > v) { perm[j + 1] = perm[j]; --j; }
+          perm[j + 1] = v;
+        }
+      __syncwarp();
+      continue;
     }
+    int32_t v[kSortPer];
+    int rank[kSortPer];
+#pragma unroll
+    for (int q = 0; q < kSortPer; ++q) {
+      v[q] = lane + 32 * q < n ? perm[b + lane + 32 * q] : INT_MAX;
+      rank[q] = 0;
+    }
+    const int rounds = (n + 31) >> 5;
+    for (int r = 0; r < rounds; ++r) {
+      const int cnt = min(32, n - 32 * r);
+      int32_t mine = INT_MAX;
+#pragma unroll
+      for (int q = 0; q < kSortPer; ++q)
+        if (q == r) mine = v[q];
+      for (int k = 0; k < cnt; ++k) {
+        const int32_t t = __shfl_sync(0xffffffffu, mine, k);
+#pragma unroll
+        for (int q = 0; q < kSortPer; ++q) rank[q] += t < v[q] ? 1 : 0;
+      }
+    }
+    __syncwarp();   // every index read before any is written back
+#pragma unroll
+    for (int q = 0; q < kSortPer; ++q)
+      if (lane + 32 * q < n) perm[b + rank[q]] = v[q];
   }
 }
 
@@ -792,7 +831,7 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
   CKL(launch_chained(k_scan_down, dim3(tiles), dim3(kBlock), st, h->cell_count, h->total_cells, h->scan_sums, h->cell_start, h->n, gate));
   CKL(launch_chained(k_cell_scatter, dim3(capped_grid(grid_for(h->n, kBlock))), dim3(kBlock), st, h->n, h->cell_of, h->rank,
                                                                          h->cell_start, h->perm, gate));
-  CKL(launch_chained(k_cell_sort, dim3(capped_grid(grid_for(h->cell_cap, kBlock))), dim3(kBlock), st, h->total_cells, h->cell_start,
+  CKL(launch_chained(k_cell_sort, dim3(capped_grid(grid_for(h->cell_cap * 32, kBlock))), dim3(kBlock), st, h->total_cells, h->cell_start,
                                                                              h->perm, gate));
   h->launches += 8;
   // a mesh built outside the Verlet sequence changes the slot order under the lists
