@@ -275,8 +275,10 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
 __device__ __forceinline__ void rotate3(const double ax[3], double alpha, const double v[3], double out[3]) {
   double na = sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
   if (na == 0.0) { out[0] = v[0]; out[1] = v[1]; out[2] = v[2]; return; }
-  double u[3] = {ax[0] / na, ax[1] / na, ax[2] / na};
-  double c = cos(alpha), s = sin(alpha);
+  const double ina = 1.0 / na;
+  double u[3] = {ax[0] * ina, ax[1] * ina, ax[2] * ina};
+  double c, s;
+  sincos(alpha, &s, &c);
   double uxv[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
   double udv = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
   for (int q = 0; q < 3; ++q) out[q] = v[q] * c + uxv[q] * s + u[q] * udv * (1.0 - c);
@@ -297,7 +299,23 @@ __device__ __forceinline__ void rotate3(const double ax[3], double alpha, const 
 // D^sh_kl = max(rmax_k, rmax_l) (eq. Horizon).  Loads: caller's, else half
 // the accumulated full-list pair counts.  Resets the accumulators.
 // ---------------------------------------------------------------------------
-// Unit k's update (one block per unit, the arithmetic on thread 0): the
+// Butterfly sum / max over the warp (every lane gets the result).
+__device__ __forceinline__ void warp_sum3(double* v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o);
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double q = __shfl_xor_sync(0xffffffffu, v, o);
+    v = q > v ? q : v;
+  }
+  return v;
+}
+
+// Unit k's update (one warp per unit, the terms spread over its lanes): the
 // balancing offsets of unit k and its new generator, into scratch
 // (3 coordinates, then the shift length, per unit).
 __global__ void k_balance_unit(int K, int gdim, const double* __restrict__ gen, const double* __restrict__ load_in,
@@ -316,11 +334,13 @@ __global__ void k_balance_unit(int K, int gdim, const double* __restrict__ gen, 
   for (int q = threadIdx.x; q < K * adj_words; q += blockDim.x) AB[q] = adj_bits[q];
   __syncthreads();
   const int k = blockIdx.x;
-  if (threadIdx.x != 0 || k >= K) return;
+  if (k >= K) return;
+  const int lane = threadIdx.x & 31;   // one warp per unit
   double sig = (gdim >= 2) ? sigma : 0.0;   // three-body terms in 2D, four-body terms in 3D
   // The neighbours of a unit are walked as the set bits of its bitmap row, in
-  // increasing index order: the same terms in the same order as a scan of all
-  // indices that skips the non-adjacent ones.
+  // increasing index order; the warp's lanes take every 32nd neighbour l, and
+  // every 32nd three- or four-body set in that walk, and the lanes' partial
+  // sums are added by a butterfly.
   auto dsh = [&](int r, int c) -> double {
     double a = stats[r * 5 + 4], b = stats[c * 5 + 4];
     return a > b ? a : b;
@@ -328,10 +348,12 @@ __global__ void k_balance_unit(int K, int gdim, const double* __restrict__ gen, 
   const double* gk = &G[k * 3];
   double dg2[3] = {0, 0, 0}, dg3[3] = {0, 0, 0};
   double maxd = 0.0;
+  int nth = 0;
   for (int w = 0; w < adj_words; ++w)
   for (uint32_t bits = AB[k * adj_words + w]; bits; bits &= bits - 1) {
     const int l = w * 32 + __ffs(bits) - 1;
     if (l == k || l >= K) continue;
+    if ((nth++ & 31) != lane) continue;
     double D = dsh(k, l);
     if (D > maxd) maxd = D;
     double den = L[k] + L[l];
@@ -346,6 +368,7 @@ __global__ void k_balance_unit(int K, int gdim, const double* __restrict__ gen, 
     // four-body terms: each set {k, l, m, n} of mutually adjacent units once
     // (l < m < n), a rotation of c_k on the circumsphere of the four generators
     const double half_t = 0.5 * acos(-1.0 / 3.0);
+    int nset = 0;
     for (int wl = 0; wl < adj_words; ++wl)
     for (uint32_t bl = AB[k * adj_words + wl]; bl; bl &= bl - 1) {
       const int l = wl * 32 + __ffs(bl) - 1;
@@ -362,6 +385,7 @@ __global__ void k_balance_unit(int K, int gdim, const double* __restrict__ gen, 
              bn; bn &= bn - 1) {
           const int n4 = wn * 32 + __ffs(bn) - 1;
           if (n4 == k || n4 >= K) continue;
+          if ((nset++ & 31) != lane) continue;
           const double* gl = &G[l * 3];
           const double* gm = &G[m * 3];
           const double* gn = &G[n4 * 3];
@@ -405,12 +429,15 @@ __global__ void k_balance_unit(int K, int gdim, const double* __restrict__ gen, 
         }
       }
     }
+    warp_sum3(dg3);
+    maxd = warp_max(maxd);
     double n3 = sqrt(dg3[0] * dg3[0] + dg3[1] * dg3[1] + dg3[2] * dg3[2]);
     if (n3 > maxd && n3 > 0.0) {
       double f = maxd / n3;
       for (int a = 0; a < 3; ++a) dg3[a] *= f;
     }
   } else if (sig != 0.0) {
+    int nset = 0;
     for (int wl = 0; wl < adj_words; ++wl)
     for (uint32_t bl = AB[k * adj_words + wl]; bl; bl &= bl - 1) {
       const int l = wl * 32 + __ffs(bl) - 1;
@@ -421,6 +448,7 @@ __global__ void k_balance_unit(int K, int gdim, const double* __restrict__ gen, 
            bm; bm &= bm - 1) {
         const int m = wm * 32 + __ffs(bm) - 1;
         if (m == k || m >= K) continue;
+        if ((nset++ & 31) != lane) continue;
         const double* gl = &G[l * 3];
         const double* gm = &G[m * 3];
         double ax = gl[0] - gk[0], ay = gl[1] - gk[1];
@@ -447,12 +475,16 @@ __global__ void k_balance_unit(int K, int gdim, const double* __restrict__ gen, 
         for (int a = 0; a < 3; ++a) dg3[a] += r2[a] - ck[a];
       }
     }
+    warp_sum3(dg3);
+    maxd = warp_max(maxd);
     double n3 = sqrt(dg3[0] * dg3[0] + dg3[1] * dg3[1] + dg3[2] * dg3[2]);
     if (n3 > maxd && n3 > 0.0) {
       double f = maxd / n3;
       for (int a = 0; a < 3; ++a) dg3[a] *= f;
     }
   }
+  warp_sum3(dg2);
+  if (lane != 0) return;
   double cnt = stats[k * 5 + 3];
   double dist2 = 0.0;
   for (int a = 0; a < gdim; ++a) {
