@@ -174,6 +174,7 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   dp.n = s->n;
   dp.vref = nullptr;
   dp.vframe = nullptr;
+  dp.vacc = nullptr;
   dp.vscale = 1.0;
   for (int k = 0; k < p->n_mat; ++k) {
     const sph_material& m = mats[k];
@@ -321,16 +322,20 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     h->vcap = (int)std::min(65536.0, std::ceil(cap / 32.0) * 32.0);
     CKI(dalloc(&h->vlist, (size_t)h->vcap * n));
     CKI(dalloc(&h->vcnt, n));
-    CKI(dalloc(&h->vref, (size_t)4 * n + 6));
-    CKI(cudaMemset(h->vref, 0, sizeof(double) * (4 * n + 6)));
+    CKI(dalloc(&h->vref, (size_t)4 * n + 10));
+    CKI(cudaMemset(h->vref, 0, sizeof(double) * (4 * n + 10)));
     h->vframe = h->vref + (size_t)4 * n;
     const double frame0[4] = {0.0, 0.0, 0.0, 1.0};   // U = 0 (also its FP32 copy), one step since the build
     CKI(cudaMemcpy(h->vframe, frame0, sizeof(frame0), cudaMemcpyHostToDevice));
+    h->vacc = reinterpret_cast<VAcc*>(h->vframe + 6);
+    const VAcc acc0{LLONG_MIN, {INT_MAX, INT_MAX, INT_MAX}, {INT_MIN, INT_MIN, INT_MIN}};
+    CKI(cudaMemcpy(h->vacc, &acc0, sizeof(acc0), cudaMemcpyHostToDevice));
     CKI(dalloc(&h->vflag, 4));
     const int flags[4] = {1, 1, 0, 0};    // lists invalid until the first build
     CKI(cudaMemcpy(h->vflag, flags, sizeof(flags), cudaMemcpyHostToDevice));
     dp.vref = h->vref;
     dp.vframe = h->vframe;
+    dp.vacc = h->vacc;
     // the units as the list kernel's work partition
     h->unit_sched = h->K > 0 ? p->unit_sched : SPH_SCHED_GLOBAL;
     if (h->unit_sched != SPH_SCHED_GLOBAL) {

@@ -42,6 +42,14 @@ struct BlockPart {
   int dlo[3], dhi[3];      // Verlet lists: box of the displacements since the build (FP32 order keys)
 };
 
+// Verlet lists: the grid-wide maximum of the validity criterion and the box
+// of the displacements of one kick-drift, accumulated by its blocks with
+// atomics and read (then reset) by the step's flag kernel.
+struct VAcc {
+  long long viol;          // max_i of the criterion key (> 0: rebuild)
+  int dlo[3], dhi[3];      // box of x - x_b - U (FP32 order keys)
+};
+
 // Material constants on the device.
 struct Mat {
   int eos;
@@ -88,6 +96,7 @@ struct DevParams {
   const double* vref;                     // Verlet lists: x, y, z, d at the last build (4 arrays of n), or NULL
   const double* vframe;                   // Verlet lists: this step's frame displacement U (3), the
                                           // number of steps since the build, U as 3 floats; or NULL
+  VAcc* vacc;                             // Verlet lists: the criterion's accumulators, or NULL
   int64_t n;                              // particles of the handle (stride of vref)
   double vscale;                          // mixed precision: packed volume = (m / rho) vscale (a power of two)
 };
@@ -204,8 +213,9 @@ struct sph_handle {
   int32_t* vcnt = nullptr;            // [n] entries of slot i
   double* vref = nullptr;             // [4 n] x, y, z, d of each particle at the last build, then
                                       // [6] the frame of the validity criterion: U, steps since the
-                                      // build, U in FP32 (3 floats in the last two)
+                                      // build, U in FP32 (3 floats in the last two); [4] a VAcc
   double* vframe = nullptr;           // = vref + 4 n
+  csph::VAcc* vacc = nullptr;         // = vref + 4 n + 6 (32 bytes)
   int* vflag = nullptr;               // [0]: rebuild in this step; [1]: lists invalid; [2]: builds done
 
   // Work units as the partition of the list kernel's work (Verlet lists with

@@ -530,7 +530,17 @@ __global__ void k_kick_drift(DevParams P, sph_state s, const int64_t* __restrict
     if (!finite || !finite_bits(d)) set_status(status, SPH_ERR_NONFINITE);
   }
   block_reduce(r);
-  if (threadIdx.x == 0) write_part(part, r);
+  if (threadIdx.x == 0) {
+    write_part(part, r);
+    if (P.vacc) {                  // the criterion's grid-wide maximum and displacement box
+      atomicMax(&P.vacc->viol, r.viol);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        atomicMin(&P.vacc->dlo[a], r.dlo[a]);
+        atomicMax(&P.vacc->dhi[a], r.dhi[a]);
+      }
+    }
+  }
 }
 
 // Second half kick with the rates of the predicted state; instance time.
@@ -846,60 +856,35 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
 // build, extrapolated to k + 1 steps; after a build, one step's worth of it
 // (the new reference is this step's state); 0 while the reference is void.
 // Any U keeps the criterion sound; a good one only makes builds rarer.
-__global__ void k_verlet_flag(const BlockPart* __restrict__ part, int nblk, int* vflag, double* vframe) {
+__global__ void k_verlet_flag(int* vflag, double* vframe, VAcc* vacc) {
   chain_entry();
-  __shared__ long long shv[32];
-  __shared__ int shb[32][6];
-  long long m = LLONG_MIN;
-  int b[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
-  for (int k = threadIdx.x; k < nblk; k += blockDim.x) {
-    const BlockPart& q = part[k];
-    m = q.viol > m ? q.viol : m;
+  if (threadIdx.x != 0) return;
+  const long long m = vacc->viol;
+  int b[6];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) { b[a] = min(b[a], q.dlo[a]); b[3 + a] = max(b[3 + a], q.dhi[a]); }
+  for (int a = 0; a < 3; ++a) { b[a] = vacc->dlo[a]; b[3 + a] = vacc->dhi[a]; }
+  // reset for the next kick-drift
+  vacc->viol = LLONG_MIN;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) { vacc->dlo[a] = INT_MAX; vacc->dhi[a] = INT_MIN; }
+  const bool void_ref = vflag[1] != 0;
+  const bool rebuild = m > 0 || void_ref;
+  vflag[0] = rebuild ? 1 : 0;
+  const double ks = vframe[3] >= 1.0 ? vframe[3] : 1.0;   // steps covered by this step's displacements
+  float* Uf = reinterpret_cast<float*>(vframe + 4);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    // midpoint of the box of x - x^b, from that of x - x^b - U
+    const double mid = b[a] <= b[3 + a] ? 0.5 * ((double)funkey(b[a]) + (double)funkey(b[3 + a])) + vframe[a]
+                                        : vframe[a];
+    vframe[a] = void_ref ? 0.0 : (rebuild ? mid / ks : mid * (ks + 1.0) / ks);
+    Uf[a] = (float)vframe[a];
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long qm = __shfl_xor_sync(0xffffffffu, m, o);
-    m = qm > m ? qm : m;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      b[a] = min(b[a], __shfl_xor_sync(0xffffffffu, b[a], o));
-      b[3 + a] = max(b[3 + a], __shfl_xor_sync(0xffffffffu, b[3 + a], o));
-    }
-  }
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    shv[w] = m;
-#pragma unroll
-    for (int a = 0; a < 6; ++a) shb[w][a] = b[a];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
-      m = shv[k] > m ? shv[k] : m;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) { b[a] = min(b[a], shb[k][a]); b[3 + a] = max(b[3 + a], shb[k][3 + a]); }
-    }
-    const bool void_ref = vflag[1] != 0;
-    const bool rebuild = m > 0 || void_ref;
-    vflag[0] = rebuild ? 1 : 0;
-    const double ks = vframe[3] >= 1.0 ? vframe[3] : 1.0;   // steps covered by this step's displacements
-    float* Uf = reinterpret_cast<float*>(vframe + 4);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      // midpoint of the box of x - x^b, from that of x - x^b - U
-      const double mid = b[a] <= b[3 + a] ? 0.5 * ((double)funkey(b[a]) + (double)funkey(b[3 + a])) + vframe[a]
-                                          : vframe[a];
-      vframe[a] = void_ref ? 0.0 : (rebuild ? mid / ks : mid * (ks + 1.0) / ks);
-      Uf[a] = (float)vframe[a];
-    }
-    vframe[3] = rebuild ? 1.0 : ks + 1.0;
-  }
+  vframe[3] = rebuild ? 1.0 : ks + 1.0;
 }
 
 cudaError_t launch_verlet_flag(sph_handle* h, cudaStream_t st) {
-  CKL(launch_chained(k_verlet_flag, dim3(1), dim3(1024), st, h->part, h->nblk, h->vflag, h->vframe));
+  CKL(launch_chained(k_verlet_flag, dim3(1), dim3(32), st, h->vflag, h->vframe, h->vacc));
   h->launches += 1;
   return cudaGetLastError();
 }
