@@ -58,7 +58,7 @@ __device__ __forceinline__ T slot_sum(const Kahan<T>& k) {
 }
 
 template <bool MIXED, int DIM, bool HLL = false, bool EXTRA = true, bool STAGE = false>
-__global__ void __launch_bounds__(kPairBlock, MIXED ? (EXTRA ? 6 : 7) : 4) k_pair_lists(PairArgs a) {
+__global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairArgs a) {
   chain_entry();
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
