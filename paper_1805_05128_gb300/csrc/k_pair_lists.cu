@@ -79,6 +79,9 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairAr
     const int c = threadIdx.x;
     unit_shift[c] = make_float4((float)(c % 3 - 1), (float)((c / 3) % 3 - 1), (float)(c / 9 - 1), 0.f);
   }
+  const int adj_n = EXTRA && a.collect_adj ? a.K * a.adj_words : 0;   // the block's adjacency tile
+  if constexpr (EXTRA)
+    for (int w = threadIdx.x; w < adj_n; w += blockDim.x) adj_tile()[w] = 0u;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int half = lane / kSlotLanes, hl = lane % kSlotLanes;   // the slot's group of lanes, lane in it
@@ -228,6 +231,7 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairAr
       const int ui = a.K > 0 ? a.slot_unit[ii] : 0;
       const uint32_t* __restrict__ row = a.vlist + (int64_t)ii * a.vcap;
       FwdAcc<MIXED, DIM, false, HLL, EXTRA> fw;
+      fw.adj_local = true;
       unsigned nacc = 0;                              // accepted pairs of i (the slot's total after the loop)
       int cmax = cnt;                                 // chunks run by the whole warp
 #pragma unroll
@@ -435,6 +439,13 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairAr
         atomicMin(&a.unit_t[u_cur[warp]], t_grp[warp]);
         atomicMax(&a.unit_t[a.K + u_cur[warp]], t_end);
       }
+    }
+  }
+  if constexpr (EXTRA) {                            // the block's adjacency bits into adj_bits
+    __syncthreads();
+    for (int w = threadIdx.x; w < adj_n; w += blockDim.x) {
+      const uint32_t v = adj_tile()[w];
+      if (v) atomicOr(&a.adj_bits[w], v);
     }
   }
 }

@@ -353,6 +353,14 @@ __device__ __forceinline__ double lab_power_of(const PairArgs& a, int64_t i, con
 // size, the unit adjacency and the optional pair output.  Only the
 // evaluations that feed a rebalance or a pair query need them, and leaving
 // them out of the pair loop saves ~10 % of the list kernel.
+// Per-block shared tile of the unit adjacency bits (K <= SPH_MAX_UNITS), for
+// the list evaluation with side outputs: zeroed by the kernel before its
+// work loop, merged into adj_bits after it.
+__device__ __forceinline__ uint32_t* adj_tile() {
+  __shared__ uint32_t tile[SPH_MAX_UNITS * (SPH_MAX_UNITS / 32)];
+  return tile;
+}
+
 template <bool MIXED, int DIM, bool ORDER2 = false, bool HLL = false, bool EXTRA = true>
 struct FwdAcc {
   using P = Pair<MIXED, DIM>;
@@ -365,6 +373,8 @@ struct FwdAcc {
   Kahan2 k_fxy, k_fzq;   // kX2: (a_x, a_y) and (a_z, E) sums in paired form, folded by fold()
   T dmax = T(0);
   int last_adj = -1;
+  int uj_ld = -1;       // EXTRA: unit of the current listed neighbour, loaded with its operands
+  bool adj_local = false;   // EXTRA: unit adjacency into the block's shared tile (adj_tile), not global
   V4 gPi{}, gVi[3]{};   // order 2: i's gradients (set by the caller)
 
   // Moves the paired sums into s_fx, s_fy, s_fz, s_q (call once, after the last pair).
@@ -440,6 +450,9 @@ struct FwdAcc {
     const V4 Aj = A[j];
     const V4 Bj = B[j];       // requested with A[j]: most candidates interact
     const VC Cj = C[j];
+    // the side outputs' unit of j, requested with the operands rather than
+    // inside the branch that needs it (a dependent load per entry there)
+    if constexpr (EXTRA) uj_ld = a.collect_adj ? a.slot_unit[j] : -1;
     return pair_listed_ops(a, i, Ai, Bi, Ci, ui, j, Aj, Bj, Cj, sx, sy, sz, khdi, band, nexact, valid);
   }
 
@@ -647,9 +660,19 @@ struct FwdAcc {
       }
     }
     if (a.collect_adj) {
-      const int uj = a.slot_unit[j];
+      const int uj = uj_ld >= 0 ? uj_ld : a.slot_unit[j];
       if (uj != ui && uj != last_adj) {
-        atomicOr(&a.adj_bits[ui * a.adj_words + (uj >> 5)], 1u << (uj & 31));
+        const int w = ui * a.adj_words + (uj >> 5);
+        const uint32_t bit = 1u << (uj & 31);
+        if (adj_local) {
+          // the block's tile, merged into adj_bits once at the end: global
+          // atomics on the K x K bits from every boundary entry contend on a
+          // few hundred words
+          uint32_t* tile = adj_tile();
+          if (!(tile[w] & bit)) atomicOr(&tile[w], bit);
+        } else {
+          atomicOr(&a.adj_bits[w], bit);
+        }
         last_adj = uj;
       }
     }
