@@ -45,7 +45,7 @@ void free_all(sph_handle* h) {
                   h->status, h->counters, h->scratch, h->adj_G,
                   h->adj_GR, h->adj_pair, h->adj_par, h->adj_W, h->adj_store, h->mat_dev, h->vlist, h->vcnt,
                   h->vref, h->vflag, h->grad_p, h->grad_v, h->adj64_A, h->adj64_B, h->adj64_C,
-                  h->adj64_rho, h->dt_key, h->e_of_c, h->perm_e, h->unit_eoff, h->packAc, h->unit_q, h->unit_t};
+                  h->adj64_rho, h->dt_key, h->e_of_c, h->perm_e, h->unit_eoff, h->packAc, h->unit_q, h->unit_t, h->slot_org};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -171,6 +171,11 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   dp.dim = p->dim; dp.kernel = p->kernel; dp.precision = p->precision; dp.n_mat = p->n_mat;
   dp.kappa = p->kappa; dp.eta = p->eta; dp.cfl = p->cfl; dp.cell_beta = p->cell_beta;
   dp.kh = (0.5 * p->kappa) * p->eta;
+  dp.eta_f = (float)dp.eta;
+  dp.kh_f = (float)dp.kh;
+  dp.cell_beta_f = (float)dp.cell_beta;
+  dp.vscale_f = 1.0f;
+  dp.slot_org = nullptr;
   dp.n = s->n;
   dp.vref = nullptr;
   dp.vframe = nullptr;
@@ -250,6 +255,9 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   CKI(dalloc(&h->slot_cell, n));
   CKI(dalloc(&h->slot_unit, n));
   if (p->precision == SPH_PREC_MIXED) {
+    CKI(dalloc(&h->slot_org, (size_t)3 * n));
+    CKI(cudaMemset(h->slot_org, 0, sizeof(double) * 3 * n));
+    h->dp.slot_org = h->slot_org;
     CKI(dalloc(reinterpret_cast<float4**>(&h->packA), n));
     CKI(dalloc(reinterpret_cast<float4**>(&h->packB), n));
     CKI(dalloc(reinterpret_cast<float4**>(&h->packC), n));
@@ -385,6 +393,7 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
   } else {
     dp.vscale = 1.0;
   }
+  dp.vscale_f = (float)dp.vscale;
 #undef CKI
   *out = h;
   return SPH_OK;

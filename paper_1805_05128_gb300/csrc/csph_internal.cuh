@@ -59,6 +59,10 @@ struct Mat {
   // instead of pow (FP64 pow costs ~100 operations of GB300's narrow FP64 pipe)
   double tait_B;
   int tait_n;
+  // the constants rounded to FP32 once (the FP32 sound speed of the mixed
+  // packs and of the CFL bound; a conversion per particle costs a slot of the
+  // narrow FP64 pipe)
+  float gamma_f, rho0_f, c0_f, p_inf_f, s_a_f;
 };
 
 // Host-side table entry of a material.
@@ -68,7 +72,7 @@ inline Mat make_mat(int eos, double gamma, double rho0, double c0, double p_inf,
     eos = SPH_EOS_STIFFENED;
     p_inf = rho0 * c0 * c0 / gamma;
   }
-  Mat m{eos, gamma, rho0, c0, p_inf, s_a, 0.0, 0};
+  Mat m{eos, gamma, rho0, c0, p_inf, s_a, 0.0, 0, (float)gamma, (float)rho0, (float)c0, (float)p_inf, (float)s_a};
   if (eos == SPH_EOS_TAIT) {
     m.tait_B = rho0 * c0 * c0 / gamma;
     m.tait_n = (gamma >= 1.0 && gamma <= 16.0 && gamma == (double)(int)gamma) ? (int)gamma : 0;
@@ -99,6 +103,9 @@ struct DevParams {
   VAcc* vacc;                             // Verlet lists: the criterion's accumulators, or NULL
   int64_t n;                              // particles of the handle (stride of vref)
   double vscale;                          // mixed precision: packed volume = (m / rho) vscale (a power of two)
+  float eta_f, kh_f, cell_beta_f, vscale_f;   // eta, kh, cell_beta, vscale rounded to FP32 once
+  const double* slot_org;                 // mixed precision: origin (x, y, z: 3 arrays of n) of each
+                                          // cell-order slot's cell, written at every mesh build
 };
 constexpr int kMaxMaterials = 65536;
 
@@ -143,6 +150,7 @@ struct sph_handle {
   int32_t* rank = nullptr;           // [n] arrival rank within the cell
   int32_t* perm = nullptr;           // [n] slot -> particle
   int32_t* slot_cell = nullptr;      // [n] global cell of slot s
+  double* slot_org = nullptr;        // mixed: [3 n] cell origin of each cell-order slot (k_cell_sort)
   int32_t* slot_unit = nullptr;      // [n] work unit of slot s
 
   // packed operands in slot order (FP32 or FP64 by precision)

@@ -395,8 +395,11 @@ __global__ void k_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of, c
 
 // Within each cell, order the particles by index (the atomic arrival order is
 // not reproducible; this makes the slot order a function of the state only).
+// Mixed precision: also the origin of each cell, o = x0 + c dc per axis, for
+// every slot of the cell (slot_org; k_pack takes the FP32 offsets from it).
 __global__ void k_cell_sort(const int64_t* __restrict__ total, const int32_t* __restrict__ start, int32_t* perm,
-                            const int* __restrict__ gate) {
+                            const int* __restrict__ gate, const GridInfo* __restrict__ grid, int n_inst, int dim,
+                            int64_t nslots, double* slot_org) {
   chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   // One warp per cell: each lane holds up to kSortPer of the cell's particle
@@ -411,6 +414,27 @@ __global__ void k_cell_sort(const int64_t* __restrict__ total, const int32_t* __
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = w0; c < tot; c += nw) {
     const int b = start[c], e = start[c + 1], n = e - b;
+    if (n <= 0) continue;
+    if (slot_org) {
+      int bi = 0;                                    // the cell's instance
+      if (n_inst > 1) {
+        int lo = 0, hi = n_inst;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (grid[mid].cell_off <= c) lo = mid; else hi = mid;
+        }
+        bi = lo;
+      }
+      const GridInfo& g = grid[bi];
+      const int64_t lc = c - g.cell_off;
+      const int64_t cc[3] = {lc % g.dims[0], (lc / g.dims[0]) % g.dims[1], lc / ((int64_t)g.dims[0] * g.dims[1])};
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (a < dim) {
+          const double o = __fma_rn((double)cc[a], g.dc, g.x0[a]);
+          for (int k = b + lane; k < e; k += 32) slot_org[(int64_t)a * nslots + k] = o;
+        }
+    }
     if (n <= 1) continue;
     if (n > 32 * kSortPer) {
       if (lane == 0)
@@ -523,8 +547,8 @@ __global__ void k_kick_drift(DevParams P, sph_state s, const int64_t* __restrict
           dsq += dx * dx;
           r.dlo[a] = r.dhi[a] = fkey(dx);
         }
-      const float kh = (float)P.kh;
-      const float crit = sqrtf(dsq) + kh * fmaxf((float)(d - db), 0.0f) - 0.95f * (float)P.cell_beta * kh * (float)db;
+      const float kh = P.kh_f;
+      const float crit = sqrtf(dsq) + kh * fmaxf((float)(d - db), 0.0f) - 0.95f * P.cell_beta_f * kh * (float)db;
       r.viol = dkey((double)crit);
     }
     if (!finite || !finite_bits(d)) set_status(status, SPH_ERR_NONFINITE);
@@ -598,7 +622,7 @@ __global__ void k_kick2(DevParams P, sph_state s, const int64_t* __restrict__ bl
 //   fp64 : A = {x, y, z, d} (global positions), B, C in FP64
 // ---------------------------------------------------------------------------
 template <bool MIXED>
-__global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk_start,
+__global__ void __launch_bounds__(kBlock, 4) k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk_start,
                        const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst,
                        const GridInfo* __restrict__ grid, const double* __restrict__ dt, int predict,
                        const int32_t* __restrict__ perm, const int32_t* __restrict__ cell_of,
@@ -675,18 +699,15 @@ __global__ void k_pack(DevParams P, sph_state s, const int64_t* __restrict__ blk
   slot_unit[sl] = u;
   rho_slot[sl] = rho;
   if (MIXED) {
-    const GridInfo& g = grid[b];
-    int64_t lc = gc - g.cell_off;
-    int64_t c0 = lc % g.dims[0];
-    int64_t c1 = (lc / g.dims[0]) % g.dims[1];
-    int64_t c2 = lc / ((int64_t)g.dims[0] * g.dims[1]);
-    int64_t cc[3] = {c0, c1, c2};
+    // FP32 offsets from the slot's cell origin (written at the mesh build)
     float off[3] = {0.f, 0.f, 0.f};
-    for (int a = 0; a < P.dim; ++a) off[a] = (float)(X[a] - (g.x0[a] + (double)cc[a] * g.dc));
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a < P.dim) off[a] = (float)(X[a] - P.slot_org[(int64_t)a * P.n + sc]);
     const float4 Arec = make_float4(off[0], off[1], off[2], (float)d);
     reinterpret_cast<float4*>(packA)[sl] = Arec;
     if (build) reinterpret_cast<float4*>(packAc)[sc] = Arec;
-    const float Vp = fast ? ((float)m / (float)rho) * (float)P.vscale : (float)((m / rho) * P.vscale);
+    const float Vp = fast ? ((float)m / (float)rho) * P.vscale_f : (float)((m / rho) * P.vscale);
     // FP32 velocities relative to a reference velocity of whole m/s per
     // particle (k = v truncated, |k| <= 32767): v - k is exact in FP64 and
     // small, so FP32 keeps the velocity differences between neighbours to
@@ -841,8 +862,8 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
   CKL(launch_chained(k_scan_down, dim3(tiles), dim3(kBlock), st, h->cell_count, h->total_cells, h->scan_sums, h->cell_start, h->n, gate));
   CKL(launch_chained(k_cell_scatter, dim3(capped_grid(grid_for(h->n, kBlock))), dim3(kBlock), st, h->n, h->cell_of, h->rank,
                                                                          h->cell_start, h->perm, gate));
-  CKL(launch_chained(k_cell_sort, dim3(capped_grid(grid_for(h->cell_cap * 32, kBlock))), dim3(kBlock), st, h->total_cells, h->cell_start,
-                                                                             h->perm, gate));
+  CKL(launch_chained(k_cell_sort, dim3(capped_grid(grid_for(h->cell_cap * 32, kBlock))), dim3(kBlock), st,
+                     h->total_cells, h->cell_start, h->perm, gate, h->grid, h->n_inst, h->dp.dim, h->n, h->slot_org));
   h->launches += 8;
   // a mesh built outside the Verlet sequence changes the slot order under the lists
   if (!gate && h->verlet) return cudaMemsetAsync(&h->vflag[1], 0xff, sizeof(int), st);

@@ -90,17 +90,17 @@ __device__ __forceinline__ bool finite_bits(double x) {
 // c^2 = gamma (gamma - 1)(rho e - P_inf) / rho, without the P + P_inf
 // cancellation).  For the CFL bound of a mixed-precision step only.
 __device__ __forceinline__ float sound_speed_f32(const Mat& m, float rho, float e) {
-  const float g = (float)m.gamma;
+  const float g = m.gamma_f;
   float c2;
   if (m.eos == SPH_EOS_IDEAL) {
     c2 = g * (g - 1.0f) * e;
   } else if (m.eos == SPH_EOS_STIFFENED) {
-    c2 = g * (g - 1.0f) * (rho * e - (float)m.p_inf) / rho;
+    c2 = g * (g - 1.0f) * (rho * e - m.p_inf_f) / rho;
   } else if (m.eos == SPH_EOS_TAIT) {
-    const float c0 = (float)m.c0, r = rho / (float)m.rho0;
+    const float c0 = m.c0_f, r = rho / m.rho0_f;
     c2 = c0 * c0 * (m.tait_n > 1 ? ipow(r, m.tait_n - 1) : (m.tait_n == 1 ? 1.0f : powf(r, g - 1.0f)));
   } else {
-    const float ca = (float)m.c0, sa = (float)m.s_a, r0 = (float)m.rho0;
+    const float ca = m.c0_f, sa = m.s_a_f, r0 = m.rho0_f;
     const float x = r0 / rho, u = 1.0f - x, D = 1.0f - sa * u, iD2 = 1.0f / (D * D);
     const float Pr = r0 * ca * ca * u * iD2, er = 0.5f * ca * ca * u * u * iD2;
     const float du = x / rho;
@@ -131,7 +131,7 @@ __device__ __forceinline__ long long cfl_key(const DevParams& P, double vx, doub
     const float c = sound_speed_f32(P.mat[mi], rf, (float)e);
     const float vol = (float)m / rf;
     const float d = P.dim == 1 ? vol : (P.dim == 2 ? sqrtf(vol) : cbrtf(vol));
-    return dkey((double)((float)P.eta * d / (c + sqrtf((float)v2))));
+    return dkey((double)(P.eta_f * d / (c + sqrtf((float)v2))));
   }
   double Pp, cp;
   eos(P.mat[mi], rho, e, Pp, cp);
