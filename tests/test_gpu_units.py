@@ -101,3 +101,30 @@ def test_staged_operands_give_the_same_bits(sched):
         sim.close()
     for k in ("x", "vx", "vz", "rho", "E", "ax", "drho", "dE"):
         assert np.array_equal(out[0][k], out[1][k]), k
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_list_evaluation_unit_statistics_match_oracle(precision):
+    """The unit statistics of one evaluation over the Verlet lists (the form
+    with side outputs: loads as interacting-pair counts, the adjacency
+    through each block's shared tile merged into the K x K bits) equal the
+    oracle's for the pair set of the evaluated state (Sec. 4.2-4.3)."""
+    from paper_1805_05128_gb300 import Simulation
+    prob = _plate()
+    K = prob.units
+    sim = Simulation(prob, precision=precision, generators=synth.problem_generators(prob), n_upd=0,
+                     cell_beta=0.15)
+    sim.assign()
+    sim.eval_rates()
+    sim.balance(theta=0.0, sigma=0.0, gamma_b=0.0)     # generators kept; accumulators cleared
+    sim.step(1)                                         # one list evaluation with the side outputs
+    load_g, adj_g = sim.unit_stats()
+    g = sim.numpy()
+    assert sim.read_status() == 0
+    p, _ = O.from_problem(prob)
+    s = O.State(prob.dim, {k: g[k] for k in O.State.FIELDS + O.State.DERIVED if k in g}, None)
+    pi, pj = O.pairs(p, s)                              # the evaluated positions and sizes
+    st = O.unit_stats(p, s, g["unit"], K, 2, pi, pj, 0.15)
+    assert adj_g.sum() > 0 and np.array_equal(adj_g, st["adj"])
+    assert np.array_equal(load_g, st["load"])
+    sim.close()
