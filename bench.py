@@ -348,7 +348,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": traffic,
                         "peak_note": "FP32 152 SM x 128 lanes x 2 x 2.07 GHz (derived from unit counts and clock)",
-                        "pair_ms_per_launch": pair_ms_avg, "pair_share": pair_ms / ms},
+                        "pair_ms_per_launch": pair_ms_avg, "pair_share": pair_ms / ms,
+                        "issue_active": None if traffic is None else pair_profile_value(args, "issue_active_frac"),
+                        "issue_note": "fraction of the kernel's issue slots used (ncu, the committed summary): "
+                                      "the kernel is issue-bound, the FP32 fraction counts algorithmic flops only"},
            "graph": None if graph_ms is None else {
                "ms_per_step": graph_ms / args.steps,
                "value": job_value(prob.n, world, args.steps, graph_ms), "list_builds": graph_builds,
@@ -673,10 +676,10 @@ def run_disk(dev, iters: int = 45) -> dict:
     return out
 
 
-def pair_traffic_bytes(args, profiles_dir: str | None = None):
-    """DRAM bytes per launch of the dominant kernel of the benchmark workload,
-    from the committed ncu summary of that kernel; None unless the summary was
-    taken on the current pair-kernel sources (kernel_rev) and the mixed path."""
+def pair_profile_value(args, key: str, profiles_dir: str | None = None):
+    """A figure of the committed ncu summary of the benchmark's dominant
+    kernel (`key: value` line); None unless the summary was taken on the
+    current pair-kernel sources (kernel_rev) and the mixed path."""
     import re
     name = "k_pair_lists" if args.beta > 0 else "k_pair"
     path = os.path.join(profiles_dir or os.path.join(ROOT, "profiles"), f"{name}_plate_impact_387k.md")
@@ -684,18 +687,25 @@ def pair_traffic_bytes(args, profiles_dir: str | None = None):
         return None
     text = open(path).read()
     sha = re.search(r"kernel_sha1:\s*([0-9a-f]+)", text)
-    val = re.search(r"traffic_bytes_per_launch_1125k:\s*([0-9]+)", text)
+    val = re.search(re.escape(key) + r":\s*([0-9.]+)", text)
     if not sha or not val or sha.group(1) != kernel_rev():
         return None
-    return int(val.group(1))
+    return float(val.group(1))
+
+
+def pair_traffic_bytes(args, profiles_dir: str | None = None):
+    """DRAM bytes per launch of the dominant kernel at the benchmark size,
+    from its committed ncu summary (see pair_profile_value)."""
+    v = pair_profile_value(args, "traffic_bytes_per_launch_1125k", profiles_dir)
+    return None if v is None else int(v)
 
 
 def kernel_rev() -> str:
-    """Identifier of the pair-kernel sources the stored ncu traffic belongs to
-    (the two pair translation units and the headers they share)."""
+    """Identifier of the pair-kernel sources the stored ncu figures belong to
+    (the two pair translation units and the headers they include)."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("k_pair.cu", "k_pair_lists.cu", "pair_common.cuh", "step_math.cuh"):
+    for f in ("k_pair.cu", "k_pair_lists.cu", "pair_common.cuh", "step_math.cuh", "csph_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1805_05128_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 

@@ -38,8 +38,6 @@ struct BlockPart {
   long long lo[3], hi[3];  // bounding box
   long long d1, d2;        // two largest particle sizes
   long long dtmin;         // min_i eta d_i / (c_i + |v_i|)
-  long long viol;          // Verlet lists: max_i of the validity criterion (> 0: rebuild)
-  int dlo[3], dhi[3];      // Verlet lists: box of the displacements since the build (FP32 order keys)
 };
 
 // Verlet lists: the grid-wide maximum of the validity criterion and the box

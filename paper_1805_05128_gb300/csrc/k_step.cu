@@ -108,8 +108,8 @@ __device__ long long block_min_key(long long k) {
 
 __device__ __forceinline__ void write_part(BlockPart* part, const Red& r) {
   BlockPart& b = part[blockIdx.x];
-  for (int a = 0; a < 3; ++a) { b.lo[a] = r.lo[a]; b.hi[a] = r.hi[a]; b.dlo[a] = r.dlo[a]; b.dhi[a] = r.dhi[a]; }
-  b.d1 = r.d1; b.d2 = r.d2; b.dtmin = r.dtmin; b.viol = r.viol;
+  for (int a = 0; a < 3; ++a) { b.lo[a] = r.lo[a]; b.hi[a] = r.hi[a]; }
+  b.d1 = r.d1; b.d2 = r.d2; b.dtmin = r.dtmin;
 }
 
 // ---------------------------------------------------------------------------
