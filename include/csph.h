@@ -328,10 +328,14 @@ int sph_pair_counts(sph_handle* h, int64_t* half_pairs, int64_t* candidates, int
  * Sec. 4.2, reused over several steps): *builds = number of list builds since
  * sph_init, *capacity = list entries held per particle.  sph_step keeps the
  * mesh, the slot order and the lists while every particle satisfies
- * |x - x_b| + kh max(0, d - d_b) <= 0.95 beta kh d_b (x_b, d_b at the last
- * build, kh = kappa eta / 2), which keeps every pair within kappa h_ij listed,
- * and rebuilds them otherwise (decided on the device), as well as after any
- * call that rebuilds the mesh or renumbers.  Synchronises the stream.
+ * |x - x_b - U| + kh max(0, d - d_b) <= 0.95 beta kh d_b (x_b, d_b at the
+ * last build, kh = kappa eta / 2, U one displacement shared by all particles
+ * of the handle, chosen on the device to follow the bulk motion), which keeps
+ * every pair within kappa h_ij listed, and rebuilds them otherwise (decided
+ * on the device), as well as after any call that rebuilds the mesh and after
+ * a rebalance that renumbers unit-major (SPH_SCHED_UNITS*); the renumbering
+ * into slot order of the other rebalances keeps them.  Synchronises the
+ * stream.
  * Errors: SPH_ERR_INVALID if the handle has no lists (cell_beta = 0). */
 int sph_list_builds(sph_handle* h, int64_t* builds, int32_t* capacity, void* stream);
 
