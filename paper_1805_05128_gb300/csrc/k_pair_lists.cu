@@ -57,7 +57,7 @@ __device__ __forceinline__ T slot_sum(const Kahan<T>& k) {
   return v;
 }
 
-template <bool MIXED, int DIM, bool HLL = false, bool EXTRA = true, bool STAGE = false>
+template <bool MIXED, int DIM, bool HLL = false, bool EXTRA = true, bool STAGE = false, int KERN = SPH_KERNEL_CUBIC>
 __global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairArgs a) {
   chain_entry();
   using P = Pair<MIXED, DIM>;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairAr
       const T khdi = MIXED ? (T)a.kh_f * Ai.w : T(0);
       const int ui = a.K > 0 ? a.slot_unit[ii] : 0;
       const uint32_t* __restrict__ row = a.vlist + (int64_t)ii * a.vcap;
-      FwdAcc<MIXED, DIM, false, HLL, EXTRA> fw;
+      FwdAcc<MIXED, DIM, false, HLL, EXTRA, KERN> fw;
       fw.adj_local = true;
       unsigned nacc = 0;                              // accepted pairs of i (the slot's total after the loop)
       int cmax = cnt;                                 // chunks run by the whole warp
@@ -450,31 +450,41 @@ __global__ void __launch_bounds__(kPairBlock, MIXED ? 7 : 4) k_pair_lists(PairAr
   }
 }
 
-template <bool MIXED, int DIM, bool HLL, bool EXTRA, bool STAGE>
+template <bool MIXED, int DIM, bool HLL, bool EXTRA, bool STAGE, int KERN>
 cudaError_t launch_lists_one(const PairArgs& args, int blocks_per_sm, cudaStream_t st) {
   static int sms = 0, per_sm = 0;
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_lists<MIXED, DIM, HLL, EXTRA, STAGE>, kPairBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_lists<MIXED, DIM, HLL, EXTRA, STAGE, KERN>,
+                                                  kPairBlock, 0);
     if (per_sm < 1) per_sm = 1;
   }
   const int b = (blocks_per_sm > 0 && blocks_per_sm < per_sm) ? blocks_per_sm : per_sm;
   int grid = sms * b;
   if (args.unit_sched == SPH_SCHED_UNITS_OWNED && args.K > 0)   // the same number of CTAs for every unit
     grid = args.K * (grid / args.K > 0 ? grid / args.K : 1);
-  return launch_chained(k_pair_lists<MIXED, DIM, HLL, EXTRA, STAGE>, dim3(grid), dim3(kPairBlock), st, args);
+  return launch_chained(k_pair_lists<MIXED, DIM, HLL, EXTRA, STAGE, KERN>, dim3(grid), dim3(kPairBlock), st, args);
+}
+
+// The smoothing kernel as a template parameter: one derivative compiled in
+// the pair loop instead of a run-time choice (1.5 % of the list kernel).
+template <bool MIXED, bool HLL, bool EXTRA, bool STAGE, int KERN>
+cudaError_t launch_lists_dim3k(sph_handle* h, const PairArgs& args, cudaStream_t st) {
+  const int b = h->p.pair_blocks_per_sm;
+  switch (h->dp.dim) {
+    case 1: return launch_lists_one<MIXED, 1, HLL, EXTRA, STAGE, KERN>(args, b, st);
+    case 2: return launch_lists_one<MIXED, 2, HLL, EXTRA, STAGE, KERN>(args, b, st);
+    default: return launch_lists_one<MIXED, 3, HLL, EXTRA, STAGE, KERN>(args, b, st);
+  }
 }
 
 template <bool MIXED, bool HLL, bool EXTRA, bool STAGE>
 cudaError_t launch_lists_dim3(sph_handle* h, const PairArgs& args, cudaStream_t st) {
-  const int b = h->p.pair_blocks_per_sm;
-  switch (h->dp.dim) {
-    case 1: return launch_lists_one<MIXED, 1, HLL, EXTRA, STAGE>(args, b, st);
-    case 2: return launch_lists_one<MIXED, 2, HLL, EXTRA, STAGE>(args, b, st);
-    default: return launch_lists_one<MIXED, 3, HLL, EXTRA, STAGE>(args, b, st);
-  }
+  return h->dp.kernel == SPH_KERNEL_WENDLAND_C2
+             ? launch_lists_dim3k<MIXED, HLL, EXTRA, STAGE, SPH_KERNEL_WENDLAND_C2>(h, args, st)
+             : launch_lists_dim3k<MIXED, HLL, EXTRA, STAGE, SPH_KERNEL_CUBIC>(h, args, st);
 }
 
 // Staged operands only for the mixed evaluations without side outputs (the

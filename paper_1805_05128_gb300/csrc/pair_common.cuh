@@ -223,10 +223,12 @@ __device__ __forceinline__ bool exact_accept(const PairArgs& a, int dim, int64_t
 // with the reciprocals above, times ws, a power of two folded into the
 // normalisation constant (so the result is exactly ws times the unscaled
 // value: the mixed path's W'' = W' wscale at no extra multiply).
-template <typename T, int DIM>
+template <typename T, int DIM, int KERN = -1>
 __device__ __forceinline__ T dw_fast(int kernel, T kappa, T r, T h, T ws) {
   const T pi = T(3.14159265358979323846);
-  if (kernel == SPH_KERNEL_CUBIC) {
+  // KERN >= 0: the kernel fixed at compile time (one branch compiled); -1: chosen at run time
+  const bool cubic = KERN >= 0 ? KERN == SPH_KERNEL_CUBIC : kernel == SPH_KERNEL_CUBIC;
+  if (cubic) {
     const T ih = rcp_(h);
     const T q = r * ih;
     T norm;
@@ -361,7 +363,7 @@ __device__ __forceinline__ uint32_t* adj_tile() {
   return tile;
 }
 
-template <bool MIXED, int DIM, bool ORDER2 = false, bool HLL = false, bool EXTRA = true>
+template <bool MIXED, int DIM, bool ORDER2 = false, bool HLL = false, bool EXTRA = true, int KERN = -1>
 struct FwdAcc {
   using P = Pair<MIXED, DIM>;
   using T = typename P::T;
@@ -536,7 +538,7 @@ struct FwdAcc {
       du = zp0 ? mul_(numu, izs) : mul_(0.5f, gR);
     }
     const float hij = a.eta_half_f * add_(Ai.w, Aj.w);
-    float dW = dw_fast<float, DIM>(a.kernel, a.kappa_f, r, hij, a.wscale_f);
+    float dW = dw_fast<float, DIM, KERN>(a.kernel, a.kappa_f, r, hij, a.wscale_f);
     dW = live ? dW : 0.f;
     // momentum flux along e, without its factor 2 (carried by fscale; exact)
     const float F = mul_(mul_(mul_(Bi.w, Bj.w), Ps), dW);
@@ -637,7 +639,7 @@ struct FwdAcc {
       qv = vs;
     }
     const T hij = (MIXED ? (T)a.eta_half_f : (T)a.eta_half) * add_(Ai.w, Aj.w);
-    const T dW = MIXED ? dw_fast<T, DIM>(a.kernel, (T)a.kappa_f, r, hij, (T)a.wscale_f)
+    const T dW = MIXED ? dw_fast<T, DIM, KERN>(a.kernel, (T)a.kappa_f, r, hij, (T)a.wscale_f)
                        : kernel_dw<T, DIM>(a.kernel, (T)a.kappa, r, hij);
     // momentum flux along e, without its factor 2 (carried by fscale; exact)
     const T F = mul_(mul_(mul_(Bi.w, Bj.w), Ps), dW);
