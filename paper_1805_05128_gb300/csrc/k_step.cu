@@ -479,7 +479,7 @@ __global__ void k_cell_sort(const int64_t* __restrict__ total, const int32_t* __
 // size d~ from rho~ = rho^h + dt/2 drho; bounding box and sizes for the mesh.
 // ---------------------------------------------------------------------------
 template <bool MIXED>
-__global__ void k_kick_drift(DevParams P, sph_state s, const int64_t* __restrict__ blk_start,
+__global__ void __launch_bounds__(kBlock, 4) k_kick_drift(DevParams P, sph_state s, const int64_t* __restrict__ blk_start,
                              const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst,
                              const double* __restrict__ dt, BlockPart* part, int* status) {
   chain_entry();
