@@ -330,14 +330,18 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     h->vcap = (int)std::min(65536.0, std::ceil(cap / 32.0) * 32.0);
     CKI(dalloc(&h->vlist, (size_t)h->vcap * n));
     CKI(dalloc(&h->vcnt, n));
-    CKI(dalloc(&h->vref, (size_t)4 * n + 10));
-    CKI(cudaMemset(h->vref, 0, sizeof(double) * (4 * n + 10)));
+    const size_t ni = (size_t)n_instances;
+    CKI(dalloc(&h->vref, (size_t)4 * n + 10 * ni));
+    CKI(cudaMemset(h->vref, 0, sizeof(double) * (4 * n + 10 * ni)));
+    // per instance: U = 0 (also its FP32 copy), one step since the build; empty accumulators
     h->vframe = h->vref + (size_t)4 * n;
-    const double frame0[4] = {0.0, 0.0, 0.0, 1.0};   // U = 0 (also its FP32 copy), one step since the build
-    CKI(cudaMemcpy(h->vframe, frame0, sizeof(frame0), cudaMemcpyHostToDevice));
-    h->vacc = reinterpret_cast<VAcc*>(h->vframe + 6);
+    h->vacc = reinterpret_cast<VAcc*>(h->vframe + 6 * ni);
+    std::vector<double> frame0(6 * ni, 0.0);
+    for (size_t b = 0; b < ni; ++b) frame0[6 * b + 3] = 1.0;
+    CKI(cudaMemcpy(h->vframe, frame0.data(), sizeof(double) * frame0.size(), cudaMemcpyHostToDevice));
     const VAcc acc0{LLONG_MIN, {INT_MAX, INT_MAX, INT_MAX}, {INT_MIN, INT_MIN, INT_MIN}};
-    CKI(cudaMemcpy(h->vacc, &acc0, sizeof(acc0), cudaMemcpyHostToDevice));
+    std::vector<VAcc> accs(ni, acc0);
+    CKI(cudaMemcpy(h->vacc, accs.data(), sizeof(VAcc) * ni, cudaMemcpyHostToDevice));
     CKI(dalloc(&h->vflag, 4));
     const int flags[4] = {1, 1, 0, 0};    // lists invalid until the first build
     CKI(cudaMemcpy(h->vflag, flags, sizeof(flags), cudaMemcpyHostToDevice));

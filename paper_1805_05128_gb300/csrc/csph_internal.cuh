@@ -96,9 +96,11 @@ struct DevParams {
   double kappa, eta, cfl, cell_beta, kh;  // kh = (0.5 kappa) eta
   const Mat* mat;                         // device table of n_mat materials
   const double* vref;                     // Verlet lists: x, y, z, d at the last build (4 arrays of n), or NULL
-  const double* vframe;                   // Verlet lists: this step's frame displacement U (3), the
-                                          // number of steps since the build, U as 3 floats; or NULL
-  VAcc* vacc;                             // Verlet lists: the criterion's accumulators, or NULL
+  const double* vframe;                   // Verlet lists, 6 doubles per instance: this step's frame
+                                          // displacement U (3), the number of steps since the build,
+                                          // U as 3 floats; or NULL
+  VAcc* vacc;                             // Verlet lists: the criterion's accumulators, one per
+                                          // instance, or NULL
   int64_t n;                              // particles of the handle (stride of vref)
   double vscale;                          // mixed precision: packed volume = (m / rho) vscale (a power of two)
   float eta_f, kh_f, cell_beta_f, vscale_f;   // eta, kh, cell_beta, vscale rounded to FP32 once
@@ -218,10 +220,11 @@ struct sph_handle {
   uint32_t* vlist = nullptr;          // [n][vcap]: entry k of slot i at i vcap + k = (slot j << 5) | cell code
   int32_t* vcnt = nullptr;            // [n] entries of slot i
   double* vref = nullptr;             // [4 n] x, y, z, d of each particle at the last build, then
-                                      // [6] the frame of the validity criterion: U, steps since the
-                                      // build, U in FP32 (3 floats in the last two); [4] a VAcc
+                                      // per instance: [6] the frame of the validity criterion (U,
+                                      // steps since the build, U in FP32: 3 floats in the last
+                                      // two), then per instance [4] a VAcc
   double* vframe = nullptr;           // = vref + 4 n
-  csph::VAcc* vacc = nullptr;         // = vref + 4 n + 6 (32 bytes)
+  csph::VAcc* vacc = nullptr;         // = vref + 4 n + 6 n_inst (32 bytes each)
   int* vflag = nullptr;               // [0]: rebuild in this step; [1]: lists invalid; [2]: builds done
 
   // Work units as the partition of the list kernel's work (Verlet lists with

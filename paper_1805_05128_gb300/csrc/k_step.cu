@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_kick_drift(DevParams P, sph_state
       // the bound itself in FP32: the 5 % margin dwarfs its rounding).
       // (The displacement and U in FP32: their rounding, ~1e-7 of each, is far
       // inside the margin.)  The box is that of x - x^b - U.
-      const float* Uf = reinterpret_cast<const float*>(P.vframe + 4);
+      const float* Uf = reinterpret_cast<const float*>(P.vframe + 6 * blk_inst[blockIdx.x] + 4);
       float dsq = 0.0f;
 #pragma unroll
       for (int a = 0; a < 3; ++a)
@@ -556,12 +556,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_kick_drift(DevParams P, sph_state
   block_reduce(r);
   if (threadIdx.x == 0) {
     write_part(part, r);
-    if (P.vacc) {                  // the criterion's grid-wide maximum and displacement box
-      atomicMax(&P.vacc->viol, r.viol);
+    if (P.vacc) {                  // the criterion's maximum and displacement box of the instance
+      VAcc* va = P.vacc + blk_inst[blockIdx.x];
+      atomicMax(&va->viol, r.viol);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        atomicMin(&P.vacc->dlo[a], r.dlo[a]);
-        atomicMax(&P.vacc->dhi[a], r.dhi[a]);
+        atomicMin(&va->dlo[a], r.dlo[a]);
+        atomicMax(&va->dhi[a], r.dhi[a]);
       }
     }
   }
@@ -872,40 +873,47 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
 
 // Verlet lists: vflag[0] = lists invalid (vflag[1]) or the validity criterion
 // of k_kick_drift failed for some particle of any instance.
-// Also sets the frame displacement U of the next step's criterion: the
-// midpoint of this step's displacement box, which covers k steps since the
-// build, extrapolated to k + 1 steps; after a build, one step's worth of it
-// (the new reference is this step's state); 0 while the reference is void.
-// Any U keeps the criterion sound; a good one only makes builds rarer.
-__global__ void k_verlet_flag(int* vflag, double* vframe, VAcc* vacc) {
+// Also sets, per instance (no pair joins two instances), the frame
+// displacement U of the next step's criterion: the midpoint of this step's
+// displacement box, which covers k steps since the build, extrapolated to
+// k + 1 steps; after a build, one step's worth of it (the new reference is
+// this step's state); 0 while the reference is void.  Any U keeps the
+// criterion sound; a good one only makes builds rarer.
+__global__ void k_verlet_flag(int* vflag, double* vframe, VAcc* vacc, int n_inst) {
   chain_entry();
-  if (threadIdx.x != 0) return;
-  const long long m = vacc->viol;
-  int b[6];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) { b[a] = vacc->dlo[a]; b[3 + a] = vacc->dhi[a]; }
-  // reset for the next kick-drift
-  vacc->viol = LLONG_MIN;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) { vacc->dlo[a] = INT_MAX; vacc->dhi[a] = INT_MIN; }
+  // any instance's criterion failed (one list build serves every instance)
+  int fail = 0;
+  for (int b = threadIdx.x; b < n_inst; b += blockDim.x) fail |= vacc[b].viol > 0 ? 1 : 0;
   const bool void_ref = vflag[1] != 0;
-  const bool rebuild = m > 0 || void_ref;
-  vflag[0] = rebuild ? 1 : 0;
-  const double ks = vframe[3] >= 1.0 ? vframe[3] : 1.0;   // steps covered by this step's displacements
-  float* Uf = reinterpret_cast<float*>(vframe + 4);
+  const bool rebuild = __syncthreads_or(fail) != 0 || void_ref;
+  if (threadIdx.x == 0) vflag[0] = rebuild ? 1 : 0;
+  for (int b = threadIdx.x; b < n_inst; b += blockDim.x) {
+    VAcc& va = vacc[b];
+    int bx[6];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    // midpoint of the box of x - x^b, from that of x - x^b - U
-    const double mid = b[a] <= b[3 + a] ? 0.5 * ((double)funkey(b[a]) + (double)funkey(b[3 + a])) + vframe[a]
-                                        : vframe[a];
-    vframe[a] = void_ref ? 0.0 : (rebuild ? mid / ks : mid * (ks + 1.0) / ks);
-    Uf[a] = (float)vframe[a];
+    for (int a = 0; a < 3; ++a) { bx[a] = va.dlo[a]; bx[3 + a] = va.dhi[a]; }
+    // reset for the next kick-drift
+    va.viol = LLONG_MIN;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { va.dlo[a] = INT_MAX; va.dhi[a] = INT_MIN; }
+    double* fr = vframe + 6 * b;
+    const double ks = fr[3] >= 1.0 ? fr[3] : 1.0;   // steps covered by this step's displacements
+    float* Uf = reinterpret_cast<float*>(fr + 4);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      // midpoint of the box of x - x^b, from that of x - x^b - U
+      const double mid = bx[a] <= bx[3 + a] ? 0.5 * ((double)funkey(bx[a]) + (double)funkey(bx[3 + a])) + fr[a]
+                                            : fr[a];
+      fr[a] = void_ref ? 0.0 : (rebuild ? mid / ks : mid * (ks + 1.0) / ks);
+      Uf[a] = (float)fr[a];
+    }
+    fr[3] = rebuild ? 1.0 : ks + 1.0;
   }
-  vframe[3] = rebuild ? 1.0 : ks + 1.0;
 }
 
 cudaError_t launch_verlet_flag(sph_handle* h, cudaStream_t st) {
-  CKL(launch_chained(k_verlet_flag, dim3(1), dim3(32), st, h->vflag, h->vframe, h->vacc));
+  CKL(launch_chained(k_verlet_flag, dim3(1), dim3(h->n_inst < 1024 ? 32 * ((h->n_inst + 31) / 32) : 1024), st,
+                     h->vflag, h->vframe, h->vacc, h->n_inst));
   h->launches += 1;
   return cudaGetLastError();
 }
