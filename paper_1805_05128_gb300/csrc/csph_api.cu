@@ -45,7 +45,7 @@ void free_all(sph_handle* h) {
                   h->status, h->counters, h->scratch, h->adj_G,
                   h->adj_GR, h->adj_pair, h->adj_par, h->adj_W, h->adj_store, h->mat_dev, h->vlist, h->vcnt,
                   h->vref, h->vflag, h->grad_p, h->grad_v, h->adj64_A, h->adj64_B, h->adj64_C,
-                  h->adj64_rho, h->dt_key, h->e_of_c, h->perm_e, h->unit_eoff, h->packAc, h->unit_q, h->unit_t, h->slot_org};
+                  h->adj64_rho, h->dt_key, h->e_of_c, h->perm_e, h->unit_eoff, h->packAc, h->unit_q, h->unit_t, h->slot_org, h->vinst};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -343,6 +343,11 @@ int sph_init(sph_handle** out, const sph_params* p, int n_instances, const int64
     std::vector<VAcc> accs(ni, acc0);
     CKI(cudaMemcpy(h->vacc, accs.data(), sizeof(VAcc) * ni, cudaMemcpyHostToDevice));
     CKI(dalloc(&h->vflag, 4));
+    CKI(dalloc(&h->vinst, ni));
+    {
+      std::vector<int> ones(ni, 1);
+      CKI(cudaMemcpy(h->vinst, ones.data(), sizeof(int) * ni, cudaMemcpyHostToDevice));
+    }
     const int flags[4] = {1, 1, 0, 0};    // lists invalid until the first build
     CKI(cudaMemcpy(h->vflag, flags, sizeof(flags), cudaMemcpyHostToDevice));
     dp.vref = h->vref;

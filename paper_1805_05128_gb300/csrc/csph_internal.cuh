@@ -226,6 +226,8 @@ struct sph_handle {
   double* vframe = nullptr;           // = vref + 4 n
   csph::VAcc* vacc = nullptr;         // = vref + 4 n + 6 n_inst (32 bytes each)
   int* vflag = nullptr;               // [0]: rebuild in this step; [1]: lists invalid; [2]: builds done
+  int* vinst = nullptr;               // [n_inst]: instance rebuilt in this step (its mesh, slots and
+                                      // lists; the others keep theirs)
 
   // Work units as the partition of the list kernel's work (Verlet lists with
   // n_units > 0 and unit_sched > 0): at every list build the cell-order slots

@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
     }
     b = lo;
   }
+  if (LIST && a.vinst && a.vinst[b] == 0) continue;   // the instance keeps its lists (warp-uniform)
   const GridInfo& g = a.grid[b];
   const int nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
   const int64_t lc = cell_g - g.cell_off;
@@ -594,6 +595,7 @@ cudaError_t launch_list_build(sph_handle* h, const sph_state& s, cudaStream_t st
   }
   // work counter zeroed by the step's k_pack (launch_pack with list_counters)
   a.work_counter = &h->counters[7];
+  a.vinst = h->n_inst > 1 ? h->vinst : nullptr;   // only the instances whose lists are rebuilt
   cudaError_t e = h->dp.precision == SPH_PREC_MIXED ? launch_dim<true, kModeList>(h, a, st)
                                                     : launch_dim<false, kModeList>(h, a, st);
   h->launches += 1;

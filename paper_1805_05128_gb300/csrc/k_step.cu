@@ -190,11 +190,13 @@ __global__ void k_reduce_dt(const int32_t* __restrict__ inst_blk, const BlockPar
 
 // One block per instance: the bounding box and the two largest sizes of the
 // instance from its block partials, into the grid record.
+// vinst (Verlet steps): an instance that keeps its lists keeps its mesh geometry.
 __global__ void k_reduce_inst(const int32_t* __restrict__ inst_blk, const BlockPart* __restrict__ part,
-                              GridInfo* grid, const int* __restrict__ gate) {
+                              GridInfo* grid, const int* __restrict__ gate, const int* __restrict__ vinst) {
   chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   int b = blockIdx.x;
+  if (vinst && vinst[b] == 0) return;
   Red r;
   red_init(r);
   for (int k = inst_blk[b] + threadIdx.x; k < inst_blk[b + 1]; k += blockDim.x) {
@@ -215,15 +217,22 @@ __global__ void k_reduce_inst(const int32_t* __restrict__ inst_blk, const BlockP
 // Cell mesh per instance (single block): D^c of eq. (Dcell) with the safety
 // margin, doubled until the instance's share of the cell capacity holds the
 // mesh; dims per axis; global cell offsets.  Matches the oracle bit for bit.
+// vinst (Verlet steps): an instance that keeps its lists keeps its geometry and
+// only moves to its new cell offset.
 __global__ void k_grid_setup(DevParams P, int n_inst, const int64_t* __restrict__ inst_off,
                              const int64_t* __restrict__ inst_cap, GridInfo* grid, int64_t* total_cells,
-                             int* status, const int* __restrict__ gate) {
+                             int* status, const int* __restrict__ gate, const int* __restrict__ vinst) {
   chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   if (threadIdx.x != 0) return;
   int64_t off = 0;
   for (int b = 0; b < n_inst; ++b) {
     GridInfo& g = grid[b];
+    if (vinst && vinst[b] == 0) {
+      g.cell_off = off;
+      off += g.ncells;
+      continue;
+    }
     double hi[3];
     for (int a = 0; a < 3; ++a) hi[a] = g.hi[a];
     for (int a = P.dim; a < 3; ++a) { g.x0[a] = 0.0; g.hi[a] = 0.0; hi[a] = 0.0; }
@@ -265,19 +274,28 @@ __device__ __forceinline__ int64_t local_cell(const GridInfo& g, int dim, double
   return (int64_t)c[0] + (int64_t)g.dims[0] * ((int64_t)c[1] + (int64_t)g.dims[1] * c[2]);
 }
 
+// vinst (Verlet steps): the particles of an instance that keeps its lists are
+// counted at their positions of its last build (vref), with its kept
+// geometry, which reproduces that build's cells, slots and in-cell order.
 __global__ void k_cell_count(int dim, sph_state s, const int64_t* __restrict__ blk_start,
                              const int64_t* __restrict__ blk_end, const int32_t* __restrict__ blk_inst, int nblk,
                              const GridInfo* __restrict__ grid, int32_t* cell_count, int32_t* cell_of,
-                             int32_t* rank, int* status, const int* __restrict__ gate) {
+                             int32_t* rank, int* status, const int* __restrict__ gate, const int* __restrict__ vinst,
+                             const double* __restrict__ vref, int64_t n) {
   chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   // a capped grid strides over the segmented blocks (cheap to launch when gated)
   for (int lb = blockIdx.x; lb < nblk; lb += gridDim.x) {
     const int64_t p = blk_start[lb] + threadIdx.x;
     if (p >= blk_end[lb]) continue;
-    const GridInfo& g = grid[blk_inst[lb]];
+    const int b = blk_inst[lb];
+    const GridInfo& g = grid[b];
+    const bool kept = vinst && vinst[b] == 0;
+    const double px = kept ? vref[p] : s.x[p];
+    const double py = dim >= 2 ? (kept ? vref[n + p] : s.y[p]) : 0.0;
+    const double pz = dim >= 3 ? (kept ? vref[2 * n + p] : s.z[p]) : 0.0;
     int32_t c[3];
-    int64_t lc = local_cell(g, dim, s.x[p], dim >= 2 ? s.y[p] : 0.0, dim >= 3 ? s.z[p] : 0.0, c);
+    int64_t lc = local_cell(g, dim, px, py, pz, c);
     bool ok = true;
     for (int a = 0; a < 3; ++a) ok = ok && c[a] >= 0 && c[a] < g.dims[a];
     if (!ok) {  // only a non-finite position can leave the mesh: latch it, stay in bounds
@@ -385,12 +403,25 @@ __global__ void k_scan_down(int32_t* cnt, const int64_t* __restrict__ total, con
   }
 }
 
+// vinst (Verlet steps): the slots of an instance that keeps its lists keep
+// their particles (its cells' starts come out as before), so its particles
+// are not scattered, and its cells are not sorted below.
 __global__ void k_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of, const int32_t* __restrict__ rank,
-                               const int32_t* __restrict__ start, int32_t* perm, const int* __restrict__ gate) {
+                               const int32_t* __restrict__ start, int32_t* perm, const int* __restrict__ gate,
+                               const int* __restrict__ vinst, const int64_t* __restrict__ inst_off, int n_inst) {
   chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    if (vinst) {
+      int lo = 0, hi = n_inst;                       // the particle's instance
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (inst_off[mid] <= p) lo = mid; else hi = mid;
+      }
+      if (vinst[lo] == 0) continue;
+    }
     perm[start[cell_of[p]] + rank[p]] = (int32_t)p;
+  }
 }
 
 // Within each cell, order the particles by index (the atomic arrival order is
@@ -399,7 +430,7 @@ __global__ void k_cell_scatter(int64_t n, const int32_t* __restrict__ cell_of, c
 // every slot of the cell (slot_org; k_pack takes the FP32 offsets from it).
 __global__ void k_cell_sort(const int64_t* __restrict__ total, const int32_t* __restrict__ start, int32_t* perm,
                             const int* __restrict__ gate, const GridInfo* __restrict__ grid, int n_inst, int dim,
-                            int64_t nslots, double* slot_org) {
+                            int64_t nslots, double* slot_org, const int* __restrict__ vinst) {
   chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
   // One warp per cell: each lane holds up to kSortPer of the cell's particle
@@ -415,16 +446,17 @@ __global__ void k_cell_sort(const int64_t* __restrict__ total, const int32_t* __
   for (int64_t c = w0; c < tot; c += nw) {
     const int b = start[c], e = start[c + 1], n = e - b;
     if (n <= 0) continue;
-    if (slot_org) {
-      int bi = 0;                                    // the cell's instance
-      if (n_inst > 1) {
-        int lo = 0, hi = n_inst;
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (grid[mid].cell_off <= c) lo = mid; else hi = mid;
-        }
-        bi = lo;
+    int bi = 0;                                      // the cell's instance
+    if (n_inst > 1 && (slot_org || vinst)) {
+      int lo = 0, hi = n_inst;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (grid[mid].cell_off <= c) lo = mid; else hi = mid;
       }
+      bi = lo;
+    }
+    if (vinst && vinst[bi] == 0) continue;          // kept: slots, order and origins as they are
+    if (slot_org) {
       const GridInfo& g = grid[bi];
       const int64_t lc = c - g.cell_off;
       const int64_t cc[3] = {lc % g.dims[0], (lc / g.dims[0]) % g.dims[1], lc / ((int64_t)g.dims[0] * g.dims[1])};
@@ -851,20 +883,24 @@ cudaError_t launch_kick_drift(sph_handle* h, const sph_state& s, cudaStream_t st
 // Mesh from the block partials left by k_derive(with_bbox) or k_kick_drift,
 // then the counting sort of particles into cells.
 cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st, const int* gate) {
-  CKL(launch_chained(k_reduce_inst, dim3(h->n_inst), dim3(kBlock), st, h->inst_blk, h->part, h->grid, gate));
-  CKL(launch_chained(k_grid_setup, dim3(1), dim3(32), st, h->dp, h->n_inst, h->inst_off, h->inst_cap, h->grid, h->total_cells,
-                                 h->status, gate));
-  CKL(launch_chained(k_cell_count, dim3(capped_grid(h->nblk)), dim3(kBlock), st, h->dp.dim, s, h->blk_start, h->blk_end, h->blk_inst,
-                                                        h->nblk, h->grid,
-                                           h->cell_count, h->cell_of, h->rank, h->status, gate));
+  // per-instance rebuilds only inside the Verlet sequence (gated) of a batched
+  // handle; any other build is global (one instance: the same thing)
+  const int* vinst = gate && h->n_inst > 1 ? h->vinst : nullptr;
+  CKL(launch_chained(k_reduce_inst, dim3(h->n_inst), dim3(kBlock), st, h->inst_blk, h->part, h->grid, gate, vinst));
+  CKL(launch_chained(k_grid_setup, dim3(1), dim3(32), st, h->dp, h->n_inst, h->inst_off, h->inst_cap, h->grid,
+                     h->total_cells, h->status, gate, vinst));
+  CKL(launch_chained(k_cell_count, dim3(capped_grid(h->nblk)), dim3(kBlock), st, h->dp.dim, s, h->blk_start,
+                     h->blk_end, h->blk_inst, h->nblk, h->grid, h->cell_count, h->cell_of, h->rank, h->status, gate,
+                     vinst, (const double*)h->vref, h->n));
   int tiles = capped_grid(grid_for(h->cell_cap, kScanTile));
   CKL(launch_chained(k_scan_reduce, dim3(tiles), dim3(kBlock), st, h->cell_count, h->total_cells, h->scan_sums, gate));
   CKL(launch_chained(k_scan_sums, dim3(1), dim3(1024), st, h->scan_sums, h->total_cells, gate));
   CKL(launch_chained(k_scan_down, dim3(tiles), dim3(kBlock), st, h->cell_count, h->total_cells, h->scan_sums, h->cell_start, h->n, gate));
-  CKL(launch_chained(k_cell_scatter, dim3(capped_grid(grid_for(h->n, kBlock))), dim3(kBlock), st, h->n, h->cell_of, h->rank,
-                                                                         h->cell_start, h->perm, gate));
+  CKL(launch_chained(k_cell_scatter, dim3(capped_grid(grid_for(h->n, kBlock))), dim3(kBlock), st, h->n, h->cell_of,
+                     h->rank, h->cell_start, h->perm, gate, vinst, h->inst_off, h->n_inst));
   CKL(launch_chained(k_cell_sort, dim3(capped_grid(grid_for(h->cell_cap * 32, kBlock))), dim3(kBlock), st,
-                     h->total_cells, h->cell_start, h->perm, gate, h->grid, h->n_inst, h->dp.dim, h->n, h->slot_org));
+                     h->total_cells, h->cell_start, h->perm, gate, h->grid, h->n_inst, h->dp.dim, h->n, h->slot_org,
+                     vinst));
   h->launches += 8;
   // a mesh built outside the Verlet sequence changes the slot order under the lists
   if (!gate && h->verlet) return cudaMemsetAsync(&h->vflag[1], 0xff, sizeof(int), st);
@@ -879,15 +915,19 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
 // k + 1 steps; after a build, one step's worth of it (the new reference is
 // this step's state); 0 while the reference is void.  Any U keeps the
 // criterion sound; a good one only makes builds rarer.
-__global__ void k_verlet_flag(int* vflag, double* vframe, VAcc* vacc, int n_inst) {
+__global__ void k_verlet_flag(int* vflag, double* vframe, VAcc* vacc, int n_inst, int* vinst, int together) {
   chain_entry();
-  // any instance's criterion failed (one list build serves every instance)
+  // each instance whose criterion failed is rebuilt (its mesh, slots and lists;
+  // the other instances keep theirs), or all of them when the lists are void or
+  // the instances share an evaluation order (together)
   int fail = 0;
   for (int b = threadIdx.x; b < n_inst; b += blockDim.x) fail |= vacc[b].viol > 0 ? 1 : 0;
   const bool void_ref = vflag[1] != 0;
-  const bool rebuild = __syncthreads_or(fail) != 0 || void_ref;
-  if (threadIdx.x == 0) vflag[0] = rebuild ? 1 : 0;
+  const bool any = __syncthreads_or(fail) != 0 || void_ref;
+  if (threadIdx.x == 0) vflag[0] = any ? 1 : 0;
   for (int b = threadIdx.x; b < n_inst; b += blockDim.x) {
+    const bool rebuild = void_ref || (together ? any : vacc[b].viol > 0);
+    vinst[b] = rebuild ? 1 : 0;
     VAcc& va = vacc[b];
     int bx[6];
 #pragma unroll
@@ -913,7 +953,7 @@ __global__ void k_verlet_flag(int* vflag, double* vframe, VAcc* vacc, int n_inst
 
 cudaError_t launch_verlet_flag(sph_handle* h, cudaStream_t st) {
   CKL(launch_chained(k_verlet_flag, dim3(1), dim3(h->n_inst < 1024 ? 32 * ((h->n_inst + 31) / 32) : 1024), st,
-                     h->vflag, h->vframe, h->vacc, h->n_inst));
+                     h->vflag, h->vframe, h->vacc, h->n_inst, h->vinst, h->unit_sched != SPH_SCHED_GLOBAL ? 1 : 0));
   h->launches += 1;
   return cudaGetLastError();
 }

@@ -41,6 +41,7 @@ struct PairArgs {
   unsigned long long* counters;
   int* status;
   unsigned long long* work_counter;   // next cell for the persistent warps (zeroed per launch)
+  const int* vinst;                    // list build: the instances rebuilt in this step, or NULL (all)
   int collect_adj;   // record unit adjacency in this evaluation
   int load_timed;    // unit loads in SM cycles (SPH_LOAD_TIME) instead of pair counts
   int32_t* pair_i;   // optional unordered pair output (particle indices, i < j)
@@ -767,6 +768,7 @@ PairArgs make_args(sph_handle* h, const sph_state& s) {
   a.adj_words = (h->K + 31) / 32;
   a.counters = h->counters;
   a.work_counter = &h->counters[5];
+  a.vinst = nullptr;
   a.status = h->status;
   a.collect_adj = (h->K > 0 && h->collect_adj) ? 1 : 0;
   a.load_timed = h->load_timed ? 1 : 0;
