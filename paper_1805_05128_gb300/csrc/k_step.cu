@@ -214,9 +214,10 @@ __global__ void k_reduce_inst(const int32_t* __restrict__ inst_blk, const BlockP
   }
 }
 
-// Cell mesh per instance (single block): D^c of eq. (Dcell) with the safety
-// margin, doubled until the instance's share of the cell capacity holds the
-// mesh; dims per axis; global cell offsets.  Matches the oracle bit for bit.
+// Cell mesh per instance (one block, a thread per instance): D^c of eq.
+// (Dcell) with the safety margin, doubled until the instance's share of the
+// cell capacity holds the mesh; dims per axis; then the global cell offsets
+// in instance order.  Matches the oracle bit for bit.
 // vinst (Verlet steps): an instance that keeps its lists keeps its geometry and
 // only moves to its new cell offset.
 __global__ void k_grid_setup(DevParams P, int n_inst, const int64_t* __restrict__ inst_off,
@@ -224,15 +225,10 @@ __global__ void k_grid_setup(DevParams P, int n_inst, const int64_t* __restrict_
                              int* status, const int* __restrict__ gate, const int* __restrict__ vinst) {
   chain_entry();
   if (gate && gate[0] == 0) return;   // Verlet mode: mesh kept from the last build
-  if (threadIdx.x != 0) return;
-  int64_t off = 0;
-  for (int b = 0; b < n_inst; ++b) {
+  // the instances' meshes, one thread per instance
+  for (int b = threadIdx.x; b < n_inst; b += blockDim.x) {
     GridInfo& g = grid[b];
-    if (vinst && vinst[b] == 0) {
-      g.cell_off = off;
-      off += g.ncells;
-      continue;
-    }
+    if (vinst && vinst[b] == 0) continue;
     double hi[3];
     for (int a = 0; a < 3; ++a) hi[a] = g.hi[a];
     for (int a = P.dim; a < 3; ++a) { g.x0[a] = 0.0; g.hi[a] = 0.0; hi[a] = 0.0; }
@@ -259,11 +255,43 @@ __global__ void k_grid_setup(DevParams P, int n_inst, const int64_t* __restrict_
     g.inv_dc = inv;
     for (int a = 0; a < 3; ++a) g.dims[a] = (int32_t)dims[a];
     g.ncells = tot;
-    g.cell_off = off;
     g.dc_f = (float)dc;
-    off += tot;
   }
-  *total_cells = off;
+  __syncthreads();
+  if (n_inst == 1) {
+    if (threadIdx.x == 0) {
+      grid[0].cell_off = 0;
+      *total_cells = grid[0].ncells;
+    }
+    return;
+  }
+  // global cell offsets in instance order (a kept instance only moves): an
+  // exclusive scan of the cell counts over the block (warp scans, then the
+  // warps' totals), a chunk of instances at a time
+  __shared__ long long wsum[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  long long carry = 0;
+  for (int base = 0; base < n_inst; base += blockDim.x) {
+    const int b = base + (int)threadIdx.x;
+    const long long v = b < n_inst ? (long long)grid[b].ncells : 0;
+    long long x = v;                                   // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    long long before = 0, chunk = 0;                   // the earlier warps' totals, the chunk's total
+    for (int k = 0; k < nw; ++k) {
+      if (k < w) before += wsum[k];
+      chunk += wsum[k];
+    }
+    if (b < n_inst) grid[b].cell_off = carry + before + x - v;
+    carry += chunk;
+    __syncthreads();                                   // wsum is rewritten by the next chunk
+  }
+  if (threadIdx.x == 0) *total_cells = carry;
 }
 
 __device__ __forceinline__ int64_t local_cell(const GridInfo& g, int dim, double x, double y, double z,
@@ -887,8 +915,8 @@ cudaError_t launch_build_grid(sph_handle* h, const sph_state& s, cudaStream_t st
   // handle; any other build is global (one instance: the same thing)
   const int* vinst = gate && h->n_inst > 1 ? h->vinst : nullptr;
   CKL(launch_chained(k_reduce_inst, dim3(h->n_inst), dim3(kBlock), st, h->inst_blk, h->part, h->grid, gate, vinst));
-  CKL(launch_chained(k_grid_setup, dim3(1), dim3(32), st, h->dp, h->n_inst, h->inst_off, h->inst_cap, h->grid,
-                     h->total_cells, h->status, gate, vinst));
+  CKL(launch_chained(k_grid_setup, dim3(1), dim3(h->n_inst < 1024 ? 32 * ((h->n_inst + 31) / 32) : 1024), st,
+                     h->dp, h->n_inst, h->inst_off, h->inst_cap, h->grid, h->total_cells, h->status, gate, vinst));
   CKL(launch_chained(k_cell_count, dim3(capped_grid(h->nblk)), dim3(kBlock), st, h->dp.dim, s, h->blk_start,
                      h->blk_end, h->blk_inst, h->nblk, h->grid, h->cell_count, h->cell_of, h->rank, h->status, gate,
                      vinst, (const double*)h->vref, h->n));
