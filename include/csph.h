@@ -332,9 +332,12 @@ int sph_pair_counts(sph_handle* h, int64_t* half_pairs, int64_t* candidates, int
  * last build, kh = kappa eta / 2, U one displacement shared by all particles
  * of the handle, chosen on the device to follow the bulk motion), which keeps
  * every pair within kappa h_ij listed, and rebuilds them otherwise (decided
- * on the device), as well as after any call that rebuilds the mesh and after
- * a rebalance that renumbers unit-major (SPH_SCHED_UNITS*); the renumbering
- * into slot order of the other rebalances keeps them.  Synchronises the
+ * on the device, per instance: an instance whose criterion fails rebuilds
+ * its mesh, slots and lists, the others keep theirs), as well as after any
+ * call that rebuilds the mesh and after a rebalance that renumbers
+ * unit-major (SPH_SCHED_UNITS*, which also rebuilds every instance at
+ * once); the renumbering into slot order of the other rebalances keeps
+ * them.  *builds counts the steps with a rebuild.  Synchronises the
  * stream.
  * Errors: SPH_ERR_INVALID if the handle has no lists (cell_beta = 0). */
 int sph_list_builds(sph_handle* h, int64_t* builds, int32_t* capacity, void* stream);
