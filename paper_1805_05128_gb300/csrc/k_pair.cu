@@ -142,6 +142,18 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
     }
     int cnt = 0, vc = 0;
     unsigned nfull = 0, ncand = 0, nexact = 0;
+    // list build: the home group's bounding box and largest kh d, a warp-wide cull of candidates
+    float bxl = 0.f, bxh = 0.f, byl = 0.f, byh = 0.f, bzl = 0.f, bzh = 0.f, bkh = 0.f;
+    if constexpr (LIST && MIXED) {
+      bxl = (float)Ai.x; bxh = bxl; byl = (float)Ai.y; byh = byl; bzl = (float)Ai.z; bzh = bzl; bkh = (float)khdi;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        bxl = fminf(bxl, __shfl_xor_sync(0xffffffffu, bxl, o)); bxh = fmaxf(bxh, __shfl_xor_sync(0xffffffffu, bxh, o));
+        byl = fminf(byl, __shfl_xor_sync(0xffffffffu, byl, o)); byh = fmaxf(byh, __shfl_xor_sync(0xffffffffu, byh, o));
+        bzl = fminf(bzl, __shfl_xor_sync(0xffffffffu, bzl, o)); bzh = fmaxf(bzh, __shfl_xor_sync(0xffffffffu, bzh, o));
+        bkh = fmaxf(bkh, __shfl_xor_sync(0xffffffffu, bkh, o));
+      }
+    }
     const int ui = a.K > 0 ? a.slot_unit[ii] : 0;
     const V4 Bi = B[ii];
     const VC Ci = C[ii];
@@ -380,13 +392,30 @@ __global__ void __launch_bounds__(kPairBlock, (MODE == kModeVjp || MODE == kMode
             ent = ((uint32_t)(rc + ox + 1) << 11) | (uint32_t)(off & 2047);
           }
           if constexpr (LIST) {
-            cand[warp][lane] = S;
-            cand_ent[warp][lane] = (uint16_t)ent;
+            int nc = min(32, r1 - base);
+            if constexpr (MIXED) {
+              // keep only the candidates within reach of the home group's box
+              // (a superset: every rounding below is monotone in the distance)
+              const float ex = fmaxf(0.f, fmaxf((float)S.x - bxh, bxl - (float)S.x));
+              const float ey = DIM >= 2 ? fmaxf(0.f, fmaxf((float)S.y - byh, byl - (float)S.y)) : 0.f;
+              const float ez = DIM >= 3 ? fmaxf(0.f, fmaxf((float)S.z - bzh, bzl - (float)S.z)) : 0.f;
+              const float Rm = fmaf(a.kh_f, (float)S.w, bkh);
+              const bool keep = jv && fmaf(-Rm, Rm, P::r2_of(ex, ey, ez)) < band;
+              const unsigned km = __ballot_sync(0xffffffffu, keep);
+              if (keep) {
+                const int q = __popc(km & lt);
+                cand[warp][q] = S;
+                cand_ent[warp][q] = (uint16_t)ent;
+              }
+              nc = __popc(km);
+            } else {
+              cand[warp][lane] = S;
+              cand_ent[warp][lane] = (uint16_t)ent;
+            }
             __syncwarp();
             // each lane tests its home particle against the chunk's candidates,
             // broadcast from shared memory, and appends the accepted ones to its
             // own list in candidate order
-            const int nc = min(32, r1 - base);
 #pragma unroll 8
             for (int c = 0; c < nc; ++c) {
               const V4 Sc = cand[warp][c];
