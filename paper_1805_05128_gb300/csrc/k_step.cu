@@ -603,13 +603,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_kick_drift(DevParams P, sph_state
 #pragma unroll
       for (int a = 0; a < 3; ++a)
         if (a < dim) {
-          const float dx = (float)(x[a] - xb[a]) - Uf[a];
+          const float dx = f32_rn(x[a] - xb[a]) - Uf[a];
           dsq += dx * dx;
           r.dlo[a] = r.dhi[a] = fkey(dx);
         }
       const float kh = P.kh_f;
-      const float crit = sqrtf(dsq) + kh * fmaxf((float)(d - db), 0.0f) - 0.95f * P.cell_beta_f * kh * (float)db;
-      r.viol = dkey((double)crit);
+      const float crit = sqrtf(dsq) + kh * fmaxf(f32_rn(d - db), 0.0f) - 0.95f * P.cell_beta_f * kh * f32_rn(db);
+      r.viol = dkey(f64_of(crit));
     }
     if (!finite || !finite_bits(d)) set_status(status, SPH_ERR_NONFINITE);
   }
@@ -747,8 +747,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_pack(DevParams P, sph_state s, co
     // differences of two large terms, the expressions of eos()), c in FP32
     if (mt.eos == SPH_EOS_TAIT) Pp = mt.tait_B * (ipow(rho / mt.rho0, mt.tait_n) - 1.0);
     else Pp = (mt.gamma - 1.0) * rho * e - (mt.eos == SPH_EOS_STIFFENED ? mt.gamma * mt.p_inf : 0.0);
-    cf = sound_speed_f32(mt, (float)rho, (float)e);
-    cp = (double)cf;
+    cf = sound_speed_f32(mt, f32_rn(rho), f32_rn(e));
+    cp = f64_of(cf);
   } else {
     eos(mt, rho, e, Pp, cp);
     cf = (float)cp;
@@ -764,11 +764,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_pack(DevParams P, sph_state s, co
     float off[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      if (a < P.dim) off[a] = (float)(X[a] - P.slot_org[(int64_t)a * P.n + sc]);
-    const float4 Arec = make_float4(off[0], off[1], off[2], (float)d);
+      if (a < P.dim) off[a] = f32_rn(X[a] - P.slot_org[(int64_t)a * P.n + sc]);
+    const float4 Arec = make_float4(off[0], off[1], off[2], f32_rn(d));
     reinterpret_cast<float4*>(packA)[sl] = Arec;
     if (build) reinterpret_cast<float4*>(packAc)[sc] = Arec;
-    const float Vp = fast ? ((float)m / (float)rho) * P.vscale_f : (float)((m / rho) * P.vscale);
+    const float Vp = fast ? (f32_rn(m) / f32_rn(rho)) * P.vscale_f : (float)((m / rho) * P.vscale);
     // FP32 velocities relative to a reference velocity of whole m/s per
     // particle (k = v truncated, |k| <= 32767): v - k is exact in FP64 and
     // small, so FP32 keeps the velocity differences between neighbours to
@@ -779,10 +779,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_pack(DevParams P, sph_state s, co
     float vr[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      if (a < P.dim) vr[a] = (float)(v[a] - trunc_ref(v[a], k[a]));
+      if (a < P.dim) vr[a] = f32_rn(v[a] - trunc_ref(v[a], k[a]));
     const uint32_t kxy = (uint32_t)(k[0] + 32768) | ((uint32_t)(k[1] + 32768) << 16);
     reinterpret_cast<float4*>(packB)[sl] = make_float4(vr[0], vr[1], vr[2], Vp);
-    reinterpret_cast<float4*>(packC)[sl] = make_float4((float)Pp, fast ? (float)rho * cf : (float)(rho * cp),
+    reinterpret_cast<float4*>(packC)[sl] = make_float4(f32_rn(Pp), fast ? f32_rn(rho) * cf : (float)(rho * cp),
                                                        __uint_as_float(kxy), (float)k[2]);
   } else {
     reinterpret_cast<D4*>(packA)[sl] = D4{X[0], X[1], X[2], d};

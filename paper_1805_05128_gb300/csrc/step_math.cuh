@@ -4,6 +4,8 @@
 // key of a particle.
 #pragma once
 
+#include <cstring>
+
 #include "csph_internal.cuh"
 
 namespace csph {
@@ -17,6 +19,76 @@ __device__ __forceinline__ long long dkey(double x) {
 }
 __device__ __forceinline__ double dunkey(long long k) {
   return __longlong_as_double(k < 0 ? k ^ 0x7fffffffffffffffLL : k);
+}
+
+// Conversions between FP64 and FP32 on the integer ALU.  The F2F
+// conversions run on the narrow FP64 pipe, about as many of them as FP64
+// additions and multiplies in the per-particle kernels of a mixed step.
+// f32_rn(x) is x rounded to the nearest FP32 value, ties to even (IEEE 754
+// roundTiesToEven), built from x's bits: the exponent rebiased from 1023 to
+// 127, the 52-bit fraction cut to 23 bits and rounded on the 29 bits dropped;
+// a carry out of the fraction moves into the exponent (up to infinity, which
+// is the rounded value there).  Zeros keep their sign; other values outside
+// FP32's normal range (subnormal results, infinities, NaN) take the F2F
+// conversion.
+__host__ __device__ __forceinline__ float f32_rn(double x) {
+#ifdef __CUDA_ARCH__
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+#else
+  unsigned long long bb;
+  memcpy(&bb, &x, 8);
+  const unsigned hi = (unsigned)(bb >> 32), lo = (unsigned)bb;
+#endif
+  const unsigned h = hi & 0x7fffffffu;
+  unsigned r;
+  if (h - (897u << 20) < ((1151u - 897u) << 20)) {         // 2^-126 <= |x| < 2^128
+    r = ((h - (896u << 20)) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+  } else if ((h | lo) == 0u) {
+    r = 0u;
+  } else {
+    return (float)x;
+  }
+  r |= hi & 0x80000000u;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(r);
+#else
+  float f;
+  memcpy(&f, &r, 4);
+  return f;
+#endif
+}
+
+// f64_of(f) is f as an FP64 value (exact): the exponent rebiased, the
+// fraction moved up by 29 bits; zeros keep their sign, subnormals,
+// infinities and NaN take the F2F conversion.
+__host__ __device__ __forceinline__ double f64_of(float f) {
+#ifdef __CUDA_ARCH__
+  const unsigned u = __float_as_uint(f);
+#else
+  unsigned u;
+  memcpy(&u, &f, 4);
+#endif
+  const unsigned a = u & 0x7fffffffu;
+  unsigned hi, lo;
+  if (a - 0x00800000u < 0x7f800000u - 0x00800000u) {
+    hi = ((a >> 3) + (896u << 20)) | (u & 0x80000000u);
+    lo = a << 29;
+  } else if (a == 0u) {
+    hi = u;
+    lo = 0u;
+  } else {
+    return (double)f;
+  }
+#ifdef __CUDA_ARCH__
+  return __hiloint2double((int)hi, (int)lo);
+#else
+  const unsigned long long bb = ((unsigned long long)hi << 32) | lo;
+  double d;
+  memcpy(&d, &bb, 8);
+  return d;
+#endif
 }
 
 // Reference velocity of a mixed pack: t = trunc(v) with |t| <= 32767, built
@@ -66,9 +138,9 @@ __device__ __forceinline__ double size_of(int dim, double m, double rho) {
 // conversions are what bound the per-particle kernels on GB300.  Volumes
 // outside FP32's normal range take the FP64 path.
 __device__ __forceinline__ double size_of_mixed(int dim, double m, double rho) {
-  const float vf = __fdiv_rn((float)m, (float)rho);
+  const float vf = __fdiv_rn(f32_rn(m), f32_rn(rho));
   if (!(vf > 1e-36f && vf < 1e36f)) return size_of(dim, m, rho);
-  return (double)(dim == 1 ? vf : (dim == 2 ? sqrtf(vf) : cbrtf(vf)));
+  return f64_of(dim == 1 ? vf : (dim == 2 ? sqrtf(vf) : cbrtf(vf)));
 }
 
 // Half kick / drift y + a x: the oracle's correctly rounded product and sum

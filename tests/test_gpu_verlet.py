@@ -256,3 +256,44 @@ def test_list_query_needs_lists():
     with pytest.raises(CsphError):
         sim.list_builds()
     sim.close()
+
+
+def test_mixed_lists_with_uneven_particle_sizes():
+    """A jittered cloud whose particle sizes d = (m/rho)^(1/3) spread over a
+    factor of two and whose velocities are random: the list build's
+    candidate cull works with the largest size of each home group, so uneven
+    sizes test that it keeps every pair within (1 + beta) kappa h_ij.  Each
+    mixed step over the lists against one oracle step (exact pair set) from
+    the same state."""
+    import dataclasses
+    a, rho0, nx, ny, nz = 1e-4, 2700.0, 14, 14, 6
+    n = nx * ny * nz
+    k = np.arange(n)
+    u = synth.uniform(41, 7 * n).reshape(7, n)
+    x = (k % nx + 0.25 * (u[0] - 0.5)) * a
+    y = ((k // nx) % ny + 0.25 * (u[1] - 0.5)) * a
+    z = (k // (nx * ny) + 0.25 * (u[2] - 0.5)) * a
+    m = rho0 * a ** 3 * 8.0 ** (u[3] - 0.5)
+    v = 100.0 * (u[4:7] - 0.5)
+    mat = synth.stiffened(rho0, 5300.0, 2.0)
+    e0 = 2.0 * mat.p_inf / rho0
+    arrays = dict(x=x, y=y, z=z, vx=v[0].copy(), vy=v[1].copy(), vz=v[2].copy(), rho=np.full(n, rho0),
+                  E=e0 + 0.5 * np.sum(v * v, axis=0), m=m)
+    base = synth.plate_impact(2, (2, 2, 2), a=a, units=0)
+    prob = dataclasses.replace(base, name="uneven_cloud", arrays=arrays, materials=[mat], units=0)
+    sim = _sim(prob, "mixed", beta=0.15)
+    sim.step(1)
+    for step in range(6):
+        g0 = sim.numpy()
+        p, _ = O.from_problem(prob)
+        s = O.State(prob.dim, {k: g0[k] for k in O.State.FIELDS + O.State.DERIVED if k in g0}, prob.mat)
+        dt = torch.zeros(1, dtype=torch.float64, device=sim.device)
+        sim.step(1)
+        sim.last_dt(dt)
+        O.step_replay(p, s, [float(dt[0])], rates_valid=True)
+        g = sim.numpy()
+        for f in ("vx", "vy", "vz", "rho", "E", "drho", "ax", "ay", "az", "dE"):
+            assert _rel(g[f], getattr(s, f)) <= 1e-4, (step, f, _rel(g[f], getattr(s, f)))
+    assert sim.list_builds()[0] >= 1
+    assert sim.read_status() == 0
+    sim.close()
