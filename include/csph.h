@@ -386,9 +386,8 @@ int sph_pair_list(sph_handle* h, sph_state* s, int64_t cap, int32_t* pi_out, int
  * it; each call resets what it needs, so consecutive calls on one stream are
  * independent.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current and keeps it for
- * the life of the process; make that first call before any stream capture.
- * After cudaDeviceReset the kept address is stale: do not call this entry
- * point on a device that has been reset. */
+ * the life of the process.  After cudaDeviceReset the kept address is
+ * stale: do not call this entry point on a device that has been reset. */
 int voronoi_assign_static(int64_t n, const double* x, const double* y, const double* z, const double* gen,
                           int K, int dim, int32_t* unit_out, int32_t* unit_offsets, int32_t* unit_list,
                           void* stream);
